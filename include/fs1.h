@@ -1,0 +1,156 @@
+/*
+ * fs1.h -- C ABI of the GB300 (sm_103a) FS-1 solver.
+ *
+ * FS-1 (Liao, Chen, Wang, Bai, Jin, Wu, "Fast Sinkhorn I: an O(N) algorithm for
+ * the Wasserstein-1 metric") runs the Sinkhorn iteration of Section 2,
+ * eq. "update_sinkhorn", for the entropic Wasserstein-1 problem on a uniform
+ * grid (eq. "disc entropy problem"; 2D: eq. "2d disc entropy problem"), with
+ * every kernel product K x replaced by the forward and backward first-order
+ * recurrences of Section 3, eq. "recursion" (Section 4, eq. "2d recursion" in
+ * 2D).  The problem statement follows Algorithm 1 / Algorithm 2: inputs are
+ * two histograms a, b (the paper's u, v), the grid spacing h, eps, tol and
+ * itr_max; the output is W_eps, the transport cost sum_ij u_i K_ij C_ij v_j of
+ * the final iterate (the value Algorithm 1 returns).
+ *
+ * Conventions
+ *   - All functions return an fs1_status; none aborts or throws.
+ *   - Pointers in fs1_problem are DEVICE pointers unless the problem's
+ *     `location` is FS1_MEM_HOST, in which case the library stages them to
+ *     the device itself (an allocation and two copies per call).
+ *   - Calls are ordered on the handle's CUDA stream (fs1_config.stream; NULL =
+ *     the legacy default stream).  fs1_w1 and fs1_solve_batch synchronise that
+ *     stream before returning, so their host outputs are valid on return.
+ *   - A handle is not thread-safe; use one handle per host thread.
+ *   - W1 values and marginal errors are always FP64.
+ */
+#ifndef FS1_H
+#define FS1_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum fs1_status {
+  FS1_OK = 0,
+  FS1_EINVAL = 1,       /* bad size, spacing, eps, tol, pointer, dtype; negative or
+                           non-finite mass; total masses differing by more than
+                           1e-6 relative; a configuration the kernels do not cover */
+  FS1_ENOMEM = 2,       /* device allocation failed or the HBM budget is exceeded */
+  FS1_ENUMERIC = 3,     /* a non-finite marginal error: the iteration overflowed (the
+                           paper's "terminates abnormally", Section 5.2); info.iters
+                           holds the iteration at which it was detected */
+  FS1_ETIMEOUT = 4,     /* a bounded device-side wait (team barrier) gave up; the
+                           kernel returned without hanging the GPU */
+  FS1_ENOTCONV = 5,     /* itr_max reached with err > tol.  A warning: w1 is valid */
+  FS1_ECUDA = 6,        /* a CUDA runtime call failed */
+  FS1_EUNSUPPORTED = 7  /* a valid request this build does not implement */
+} fs1_status;
+
+enum fs1_variant {
+  FS1_VARIANT_PLAIN = 0, /* Algorithm 1 / 2 as written: linear u, v, no stabilisation */
+  FS1_VARIANT_LOG = 1    /* log-domain stabilised (Remarks in Sections 2 and 3):
+                            the scalings are kept as FP32 mantissas times per-thread
+                            power-of-two frames that absorb their magnitude every
+                            half-step, and the chunk carries are combined with a
+                            max-shifted (exponent-aligned) sum */
+};
+
+enum fs1_precision { FS1_FP64 = 0, FS1_FP32 = 1 };
+enum fs1_location { FS1_MEM_DEVICE = 0, FS1_MEM_HOST = 1 };
+
+typedef struct fs1_config {
+  int variant;          /* enum fs1_variant (default FS1_VARIANT_LOG) */
+  int precision;        /* enum fs1_precision of the iteration arithmetic
+                           (default FS1_FP32; FS1_VARIANT_PLAIN also takes FS1_FP64) */
+  int check_every;      /* marginal-error test every k iterations; 1 = the paper's
+                           rule (default 1; only 1 is implemented) */
+  int team_size;        /* CTAs that share one pair; 0 = pick from the size */
+  long long spin_cap;   /* polls of a team barrier before FS1_ETIMEOUT (default 1<<22) */
+  size_t hbm_budget;    /* bytes of device workspace the handle may hold; 0 = no limit */
+  void* stream;         /* cudaStream_t the handle works on (NULL = default stream) */
+} fs1_config;
+
+typedef struct fs1_problem {
+  int ndim;             /* 1 (Algorithm 1) or 2 (Algorithm 2) */
+  int dtype;            /* enum fs1_precision of a and b */
+  int location;         /* enum fs1_location of a, b and the optional arrays */
+  int reserved;
+  int64_t n[2];         /* n[0]: points along the fast (contiguous) axis; n[1]: along
+                           the slow axis (1 in 1D).  2D arrays are n[1] rows of n[0]
+                           contiguous values: the paper's column-major flattening with
+                           its first index (spacing h[0]) running fastest */
+  double h[2];          /* grid spacings (h[1] unused in 1D) */
+  double eps;           /* entropic regularisation, > 0 */
+  double tol;           /* stop when the column-marginal L1 error <= tol (>= 0) */
+  int64_t itr_max;      /* iteration cap (>= 0) */
+  const void* a;        /* histogram a (the paper's u): n[0]*n[1] values >= 0, sum > 0 */
+  const void* b;        /* histogram b (the paper's v); same total mass as a */
+  double* f_out;        /* optional: log u of the final iterate (FP64, n values) */
+  double* g_out;        /* optional: log v of the final iterate */
+  const double* f_init; /* optional warm start: log u, log v of an earlier run's final */
+  const double* g_init; /*   iterate (both or neither); resumes bit-identically */
+} fs1_problem;
+
+typedef struct fs1_info {
+  int status;           /* fs1_status of this problem */
+  int variant;
+  int precision;
+  int team_size;        /* CTAs that shared the pair */
+  int64_t iters;        /* completed Sinkhorn iterations l */
+  double marginal_err;  /* || diag(v) K^T u - b ||_1 of the returned iterate (FP64) */
+  double w1;            /* transport cost <P, C> of the returned iterate (FP64) */
+  float ms;             /* device time of the solve (ms) */
+  float reserved;
+} fs1_info;
+
+typedef struct fs1_handle fs1_handle;
+
+/* Fill *cfg with the defaults listed above. */
+fs1_status fs1_config_default(fs1_config* cfg);
+
+/* Create a handle on the current CUDA device.  cfg may be NULL (defaults).
+ * The handle owns its device workspace (team exchange slots, barrier counters,
+ * result and descriptor arrays); it grows on demand within hbm_budget. */
+fs1_status fs1_create(const fs1_config* cfg, fs1_handle** out);
+
+/* Solve one problem (Algorithm 1 in 1D, Algorithm 2 in 2D).
+ * w1_out: host double, may be NULL.  info_out: host, may be NULL.
+ * Returns the problem's status (FS1_ENOTCONV is a warning; w1 is valid). */
+fs1_status fs1_w1(fs1_handle* h, const fs1_problem* prob, double* w1_out, fs1_info* info_out);
+
+/* Solve `count` independent problems in as few persistent launches as the mix
+ * of sizes allows (one per group of problems that share a variant, dimension
+ * and team size).  w1_out (count doubles) and infos (count entries) are host
+ * arrays and may be NULL.  Returns the worst status over the batch. */
+fs1_status fs1_solve_batch(fs1_handle* h, const fs1_problem* probs, int64_t count,
+                           double* w1_out, fs1_info* infos);
+
+/* Apply the Gibbs kernel once with the GPU recurrences, in the log domain:
+ * out_k = log sum_j exp(-|k-j| h / eps + in_j) over a 1D grid of n points
+ * (the sweeps of eq. "recursion" with the stabilised arithmetic of the handle's
+ * variant).  in/out: device FP64 arrays of n values (-inf allowed in `in`).
+ * Exposed for testing the scan primitive on its own. */
+fs1_status fs1_kernel_apply_log(fs1_handle* h, const double* in, double* out, int64_t n,
+                                double hx, double eps);
+
+/* Release the handle and its device memory. */
+void fs1_destroy(fs1_handle* h);
+
+/* Human-readable name of a status code (static string). */
+const char* fs1_status_string(fs1_status s);
+
+/* Library version string. */
+const char* fs1_version(void);
+
+/* Number of CUDA kernels this library has launched in the calling process
+ * (all handles, all devices).  Used to report launch counts of a timed region. */
+int64_t fs1_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FS1_H */

@@ -1,0 +1,69 @@
+// fs1_internal.h -- structures shared by the host runtime and the kernels.
+// Not part of the public C-ABI (include/fs1.h).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+namespace fs1 {
+
+// Per-pair input of a solve launch (device memory).
+struct PairDesc {
+  const void* a;          // histogram a (dtype of the launch), n[0]*n[1] values
+  const void* b;          // histogram b
+  int64_t n;              // number of grid points (1D: N; 2D: n_fast*n_slow)
+  int64_t n_fast;         // 2D: fast-axis length; 1D: n
+  int64_t n_slow;         // 2D: slow-axis length; 1D: 1
+  double h_fast, h_slow;  // grid spacings
+  double eps, tol;
+  int64_t itr_max;
+  double* f_out;          // optional log potentials out (FP64), may be null
+  double* g_out;
+  const double* f_init;   // optional warm start (FP64 log potentials), may be null
+  const double* g_init;
+};
+
+// Per-pair result (device memory).
+struct PairResult {
+  double w;       // transport cost <P, C> of the final iterate
+  double err;     // marginal L1 error of the final iterate
+  int64_t iters;  // completed iterations
+  int status;     // fs1_status value
+  int pad;
+};
+
+// Exchange slot of one CTA of a team (one per CTA and buffer parity).
+struct alignas(16) Slot {
+  unsigned char raw[64];
+};
+
+struct TeamLaunch {
+  const PairDesc* pairs;
+  PairResult* results;
+  const int* order;                // pair order (cost-sorted); may be null
+  int num_pairs;
+  int team_size;                   // T: CTAs per team
+  int num_teams;
+  int in_f32;                      // 1: a, b are float; 0: double
+  Slot* slots;                     // [num_teams][2][team_size]
+  unsigned long long* counters;    // [num_teams] barrier counters (zeroed per launch)
+  int* abort_flags;                // [num_teams] (zeroed per launch)
+  long long spin_cap;              // bounded-wait polls before giving up
+};
+
+enum KernelKind {
+  KK_PLAIN_F64 = 0,   // plain FS-1 (Algorithm 1 as written), FP64
+  KK_PLAIN_F32 = 1,   // plain FS-1, FP32 (no stabilisation)
+  KK_LOG_F32 = 2,     // stabilised FS-1: FP32 mantissas in extended range
+};
+
+// Host-side launch helpers (fs1_solve1d.cu).
+int team_threads();
+int team_elems_max(int kind);
+size_t team_smem_bytes(int kind);
+// Largest elements-per-thread the stabilised variant allows for c = h/eps.
+int elems_cap_for(int kind, double c);
+// Launch the 1D team kernel; cooperative when team_size > 1.
+int launch_team_1d(int kind, const TeamLaunch& L, void* stream);
+int max_coresident_ctas(int kind);
+
+}  // namespace fs1

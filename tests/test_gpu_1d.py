@@ -1,0 +1,236 @@
+"""GPU parity of the 1D FS-1 path against the CPU FP64 oracle, through the C ABI.
+
+Tolerances (relative W1, at the GPU's reported iteration count):
+  FP64 plain variant: 1e-6;  FP32 stabilised variant: 1e-4.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import cref, dense, recurrence
+from paper_2202_10042_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-6
+TOL32 = 1e-4
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    return torch
+
+
+@pytest.fixture(scope="module")
+def fs1mod(torch_cuda):
+    from paper_2202_10042_gb300 import fs1
+    fs1.load()
+    return fs1
+
+
+def _dev(torch, x, dtype=None):
+    return torch.tensor(np.asarray(x), dtype=dtype or torch.float64, device="cuda")
+
+
+def _solve(fs1, torch, variant, prec, pairs, team_size=0, **kw):
+    s = fs1.Solver(variant, prec, team_size=team_size, **kw)
+    probs, keep = [], []
+    for (a, b, h, eps, tol, itr) in pairs:
+        ta, tb = _dev(torch, a), _dev(torch, b)
+        keep += [ta, tb]
+        probs.append(fs1.Solver.problem(ta, tb, h, eps, tol, itr))
+    st, w, infos = s.solve(probs)
+    s.close()
+    return st, w, infos
+
+
+def _rel(x, y):
+    return abs(x - y) / abs(y)
+
+
+# ---------------------------------------------------------------------------
+# the scan primitive: one kernel application in the log domain
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 2, 31, 512, 513, 8197, 100003])
+@pytest.mark.parametrize("c", [1e-3, 0.05, 1.3])
+def test_kernel_apply_log(fs1mod, torch_cuda, n, c):
+    torch = torch_cuda
+    rng = np.random.default_rng(n)
+    # smooth potential with a c-Lipschitz part and a few -inf entries
+    f = np.cumsum(rng.uniform(-c, c, n)) + rng.normal(0, 1.0, n)
+    if n > 10:
+        f[rng.integers(0, n, 3)] = -np.inf
+    h = 1.0 / max(n, 1)
+    eps = h / c
+    fin = _dev(torch, f)
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    s = fs1mod.Solver("log", "fp32")
+    st = fs1mod.fs1_kernel_apply_log(s.h, fin.data_ptr(), out.data_ptr(), n, h, eps)
+    s.close()
+    assert st == fs1mod.FS1_OK
+    got = out.cpu().numpy()
+    # reference: the oracle's log-domain recurrences (FP64)
+    R, S = recurrence.lse_matvec(f, h / eps)
+    ref = np.logaddexp(R, S)
+    ok = np.isfinite(ref)
+    assert np.all(np.isfinite(got[ok]))
+    assert np.max(np.abs(got[ok] - ref[ok])) < 2e-5 + 1e-6 * np.sqrt(n)
+
+
+# ---------------------------------------------------------------------------
+# full solves
+# ---------------------------------------------------------------------------
+
+def test_workload1_plain_fp64(fs1mod, torch_cuda):
+    """Workload 1 at full size: N = 1000, eps = 1e-2, 1000 iterations, FP64."""
+    p = inputs.workload1(0)
+    ref = cref.solve(p.a, p.b, p.h[0], p.eps, p.tol, p.itr_max, tau=math.inf)
+    st, w, infos = _solve(fs1mod, torch_cuda, "plain", "fp64",
+                          [(p.a, p.b, p.h[0], p.eps, p.tol, p.itr_max)])
+    assert infos[0].status in (fs1mod.FS1_OK, fs1mod.FS1_ENOTCONV)
+    assert infos[0].iters == ref.iters == 1000
+    assert _rel(w[0], ref.w) <= TOL64
+    assert abs(infos[0].marginal_err - ref.err) <= 1e-9 + 1e-6 * ref.err
+
+
+@pytest.mark.parametrize("team", [0, 2, 3])
+def test_workload1_batch_plain_fp64_and_log(fs1mod, torch_cuda, team):
+    pairs = []
+    for i in range(6):
+        p = inputs.workload1(i, itr_max=300)
+        pairs.append((p.a, p.b, p.h[0], p.eps, p.tol, p.itr_max))
+    refs = cref.solve_many(pairs, tau=math.inf)
+    for variant, prec, tol in (("plain", "fp64", TOL64), ("log", "fp32", TOL32)):
+        st, w, infos = _solve(fs1mod, torch_cuda, variant, prec, pairs, team_size=team)
+        for i, r in enumerate(refs):
+            assert infos[i].iters == r.iters
+            assert _rel(w[i], r.w) <= tol, (variant, i, w[i], r.w)
+
+
+@pytest.mark.parametrize("n,eps", [(777, 3e-3), (20000, 1e-3), (131072 + 13, 2e-4)])
+def test_log_fp32_against_stabilised_oracle(fs1mod, torch_cuda, n, eps):
+    """Sizes that span several warps, CTAs (team barrier) and a ragged tail."""
+    p = inputs.workload2(7, n=n, eps=eps, itr_max=200)
+    ref = cref.solve(p.a, p.b, p.h[0], p.eps, p.tol, p.itr_max, tau=1e10)
+    st, w, infos = _solve(fs1mod, torch_cuda, "log", "fp32",
+                          [(p.a, p.b, p.h[0], p.eps, p.tol, p.itr_max)])
+    assert infos[0].status in (fs1mod.FS1_OK, fs1mod.FS1_ENOTCONV)
+    assert infos[0].iters == ref.iters
+    assert _rel(w[0], ref.w) <= TOL32
+    assert abs(infos[0].marginal_err - ref.err) <= 1e-3 * ref.err + 1e-6
+
+
+def test_potentials_and_row_marginal(fs1mod, torch_cuda):
+    torch = torch_cuda
+    p = inputs.workload2(3, n=5000, eps=2e-3, itr_max=120)
+    ta, tb = _dev(torch, p.a), _dev(torch, p.b)
+    f = torch.empty(p.a.size, dtype=torch.float64, device="cuda")
+    g = torch.empty_like(f)
+    s = fs1mod.Solver("log", "fp32")
+    st, w, infos = s.solve([fs1mod.Solver.problem(ta, tb, p.h[0], p.eps, p.tol, p.itr_max,
+                                                   f_out=f, g_out=g)])
+    s.close()
+    ref = cref.solve(p.a, p.b, p.h[0], p.eps, p.tol, p.itr_max, tau=1e10, potentials=True)
+    fg, gg = f.cpu().numpy(), g.cpu().numpy()
+    # gauge: (f + k, g - k) is the same plan
+    k = np.median(fg - ref.f)
+    assert np.max(np.abs(fg - k - ref.f)) < 5e-3
+    assert np.max(np.abs(gg + k - ref.g)) < 5e-3
+    # after the u-update the row marginal is exact: u (K v) = a
+    ref_kv = np.log(cref.matvec(np.exp(gg - gg.max()), p.h[0], p.eps)) + gg.max()
+    row = np.exp(fg + ref_kv)
+    assert np.max(np.abs(row - p.a) / p.a) < 1e-4
+
+
+def test_stop_rule_matches_oracle(fs1mod, torch_cuda):
+    pairs, refs = [], []
+    for i in range(4):
+        p = inputs.workload3(i, n_range=(300, 3000), eps_range=(2e-2, 1e-1), tol=1e-5)
+        pairs.append((p.a, p.b, p.h[0], p.eps, p.tol, p.itr_max))
+    st, w, infos = _solve(fs1mod, torch_cuda, "log", "fp32", pairs)
+    for i, (a, b, h, eps, tol, itr) in enumerate(pairs):
+        assert infos[i].status == fs1mod.FS1_OK
+        assert infos[i].marginal_err <= tol
+        # the oracle at the GPU's iteration count
+        r = cref.solve(a, b, h, eps, 0.0, infos[i].iters, tau=1e10)
+        assert _rel(w[i], r.w) <= TOL32
+        # and the oracle's own stop is within one iteration
+        ro = cref.solve(a, b, h, eps, tol, itr, tau=1e10)
+        assert abs(ro.iters - infos[i].iters) <= 1
+
+
+def test_plain_fp32_terminates_abnormally_log_does_not(fs1mod, torch_cuda):
+    """Section 5.2: without stabilisation the iteration overflows at small eps."""
+    n = 1000
+    x = (np.arange(n) + 0.5) / n
+    a = np.exp(-0.5 * ((x - 0.2) / 0.03) ** 2) + 1e-3; a /= a.sum()
+    b = np.exp(-0.5 * ((x - 0.8) / 0.03) ** 2) + 1e-3; b /= b.sum()
+    pr = [(a, b, 1 / n, 1e-3, 1e-9, 2000)]
+    st, w, infos = _solve(fs1mod, torch_cuda, "plain", "fp32", pr)
+    assert infos[0].status == fs1mod.FS1_ENUMERIC and 0 < infos[0].iters < 2000
+    st, w, infos = _solve(fs1mod, torch_cuda, "log", "fp32", pr)
+    assert infos[0].status in (fs1mod.FS1_OK, fs1mod.FS1_ENOTCONV) and math.isfinite(w[0])
+    ref = cref.solve(a, b, 1 / n, 1e-3, 1e-9, 2000, tau=1e10)
+    assert infos[0].iters == ref.iters
+    assert _rel(w[0], ref.w) <= TOL32
+
+
+def test_invalid_inputs(fs1mod, torch_cuda):
+    n = 64
+    a, b = inputs.random_pair_1d(0, n)
+    bad_neg = a.copy(); bad_neg[3] = -1e-3
+    bad_mass = b * 1.01
+    st, w, infos = _solve(fs1mod, torch_cuda, "log", "fp32",
+                          [(bad_neg, b, 1 / n, 0.01, 0, 10), (a, bad_mass, 1 / n, 0.01, 0, 10),
+                           (a, b, 1 / n, 0.01, 0, 10), (a, b, 1 / n, -1.0, 0, 10)])
+    assert [i.status for i in infos] == [fs1mod.FS1_EINVAL, fs1mod.FS1_EINVAL,
+                                         fs1mod.FS1_ENOTCONV, fs1mod.FS1_EINVAL]
+
+
+def test_host_location_equals_device(fs1mod, torch_cuda):
+    torch = torch_cuda
+    p = inputs.workload1(5, itr_max=100)
+    s = fs1mod.Solver("log", "fp32")
+    ha = torch.tensor(p.a, dtype=torch.float64)
+    hb = torch.tensor(p.b, dtype=torch.float64)
+    da, db = ha.cuda(), hb.cuda()
+    st1, w1, i1 = s.solve([fs1mod.Solver.problem(ha, hb, p.h[0], p.eps, p.tol, p.itr_max)])
+    st2, w2, i2 = s.solve([fs1mod.Solver.problem(da, db, p.h[0], p.eps, p.tol, p.itr_max)])
+    s.close()
+    assert w1[0] == w2[0] and i1[0].iters == i2[0].iters
+
+
+def test_warm_start_resume_bit_identical(fs1mod, torch_cuda):
+    torch = torch_cuda
+    p = inputs.workload2(11, n=40000, eps=1e-3, itr_max=60)
+    ta, tb = _dev(torch, p.a), _dev(torch, p.b)
+    s = fs1mod.Solver("log", "fp32")
+    st, w_full, i_full = s.solve([fs1mod.Solver.problem(ta, tb, p.h[0], p.eps, 0.0, 60)])
+    f = torch.empty(p.a.size, dtype=torch.float64, device="cuda")
+    g = torch.empty_like(f)
+    s.solve([fs1mod.Solver.problem(ta, tb, p.h[0], p.eps, 0.0, 25, f_out=f, g_out=g)])
+    st, w_res, i_res = s.solve([fs1mod.Solver.problem(ta, tb, p.h[0], p.eps, 0.0, 35,
+                                                       f_init=f, g_init=g)])
+    s.close()
+    assert i_res[0].iters == 35
+    assert w_res[0] == w_full[0]
+    assert i_res[0].marginal_err == i_full[0].marginal_err
+
+
+def test_workload2_full_size_sampled(fs1mod, torch_cuda):
+    """Workload 2 at its full size (N = 2^20, eps = 1e-4) in the launch
+    configuration the benchmark times, with the iteration cap cut to 100 so that
+    the FP64 oracle finishes in seconds."""
+    ps = [inputs.workload2(i, itr_max=100) for i in (0, 17)]
+    pairs = [(p.a, p.b, p.h[0], p.eps, p.tol, p.itr_max) for p in ps]
+    refs = cref.solve_many(pairs, tau=1e10)
+    st, w, infos = _solve(fs1mod, torch_cuda, "log", "fp32", pairs)
+    for i, r in enumerate(refs):
+        assert infos[i].iters == r.iters == 100
+        assert _rel(w[i], r.w) <= TOL32
+        assert abs(infos[i].marginal_err - r.err) <= 1e-3 * r.err
