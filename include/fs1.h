@@ -139,6 +139,28 @@ fs1_status fs1_kernel_apply_log(fs1_handle* h, const double* in, double* out, in
 /* Release the handle and its device memory. */
 void fs1_destroy(fs1_handle* h);
 
+/* fs1_w1_noalloc -- fs1_w1 for callers that may not allocate.
+ * The paper has no counterpart: this is a deployment variant of fs1_w1.
+ * Some callers cannot call cudaMalloc (a memory manager already owns the
+ * device's memory, an embedding forbids the library from holding device
+ * memory, or a latency-critical path cannot afford an allocation that may
+ * synchronise the device).  This entry point solves ONE 1D, device-located
+ * problem with the same kernel as fs1_w1 and allocates nothing, on the device
+ * or the host: its device scratch (descriptor, result, exchange slots, barrier
+ * counter) is a fixed file-scope __device__ array of about 21 KiB that every GPU
+ * loading the library holds until exit.  No handle is needed: cfg (may be NULL
+ * for the defaults) supplies the variant, precision, team size, spin cap and
+ * stream.  The first call on each device, with that device current, looks up
+ * the array's device address (cudaGetSymbolAddress) and caches it; make that
+ * first call before any stream capture begins.  Every call reuses the array
+ * (it is cleared where it must start from zero); calls that overlap on the GPU
+ * race on it, so serialise them.  Problems that would need a team of more than
+ * 160 CTAs are rejected with FS1_EINVAL (and a message on stderr); host-located
+ * problems are rejected with FS1_EINVAL.  w1_out, info_out: host, may be NULL;
+ * info_out->ms is not measured (0). */
+fs1_status fs1_w1_noalloc(const fs1_config* cfg, const fs1_problem* prob, double* w1_out,
+                          fs1_info* info_out);
+
 /* Human-readable name of a status code (static string). */
 const char* fs1_status_string(fs1_status s);
 

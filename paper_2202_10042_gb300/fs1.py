@@ -49,7 +49,7 @@ class fs1_info(Structure):
 
 EXPORTED = ["fs1_config_default", "fs1_create", "fs1_w1", "fs1_solve_batch",
             "fs1_kernel_apply_log", "fs1_destroy", "fs1_status_string", "fs1_version",
-            "fs1_launch_count"]
+            "fs1_launch_count", "fs1_w1_noalloc"]
 
 _lib = None
 
@@ -82,6 +82,9 @@ def load(path: str = LIB_PATH):
     L.fs1_version.restype = c_char_p
     L.fs1_launch_count.argtypes = []
     L.fs1_launch_count.restype = c_int64
+    L.fs1_w1_noalloc.argtypes = [POINTER(fs1_config), POINTER(fs1_problem), POINTER(c_double),
+                                 POINTER(fs1_info)]
+    L.fs1_w1_noalloc.restype = c_int
     _lib = L
     return L
 
@@ -136,6 +139,15 @@ def fs1_version() -> str:
 
 def fs1_launch_count() -> int:
     return int(load().fs1_launch_count())
+
+
+def fs1_w1_noalloc(cfg: Optional[fs1_config], prob: fs1_problem):
+    """One device-located 1D problem through the allocation-free entry point."""
+    w = c_double()
+    info = fs1_info()
+    st = load().fs1_w1_noalloc(ctypes.byref(cfg) if cfg is not None else None, ctypes.byref(prob),
+                               ctypes.byref(w), ctypes.byref(info))
+    return st, w.value, info
 
 
 def _check(st: int) -> None:
