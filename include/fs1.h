@@ -147,7 +147,7 @@ void fs1_destroy(fs1_handle* h);
  * synchronise the device).  This entry point solves ONE 1D, device-located
  * problem with the same kernel as fs1_w1 and allocates nothing, on the device
  * or the host: its device scratch (descriptor, result, exchange slots, barrier
- * counter) is a fixed file-scope __device__ array of about 21 KiB that every GPU
+ * counter) is a fixed file-scope __device__ array of about 81 KiB that every GPU
  * loading the library holds until exit.  No handle is needed: cfg (may be NULL
  * for the defaults) supplies the variant, precision, team size, spin cap and
  * stream.  The first call on each device, with that device current, looks up

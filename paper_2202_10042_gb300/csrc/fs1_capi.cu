@@ -175,6 +175,7 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
   const size_t o_res = off;  off = align_up(off + sizeof(PairResult) * count, 256);
   const size_t o_val = off;  off = align_up(off + sizeof(ValOut) * count, 256);
   const size_t o_slot = off; off = align_up(off + sizeof(Slot) * (size_t)teams * 2 * T, 256);
+  const size_t o_cslot = off; off = align_up(off + 128 * (size_t)teams * 2 * T, 256);
   const size_t o_ctr = off;  off = align_up(off + sizeof(unsigned long long) * teams, 256);
   const size_t o_abt = off;  off = align_up(off + sizeof(int) * teams, 256);
   if ((st = ensure_ws(h, off)) != FS1_OK) return st;
@@ -208,6 +209,8 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
   if ((e = cudaMemcpyAsync(ws + o_res, init.data(), sizeof(PairResult) * count, cudaMemcpyHostToDevice,
                            h->stream)) != cudaSuccess)
     return cuda_fail(e, "result init");
+  cudaMemsetAsync(ws + o_slot, 0, sizeof(Slot) * (size_t)teams * 2 * T, h->stream);
+  cudaMemsetAsync(ws + o_cslot, 0, 128 * (size_t)teams * 2 * T, h->stream);
   cudaMemsetAsync(ws + o_ctr, 0, sizeof(unsigned long long) * teams, h->stream);
   cudaMemsetAsync(ws + o_abt, 0, sizeof(int) * teams, h->stream);
 
@@ -254,6 +257,7 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
   L.num_teams = teams;
   L.in_f32 = in_f32;
   L.slots = (Slot*)(ws + o_slot);
+  L.cslots = (unsigned long long*)(ws + o_cslot);
   L.counters = (unsigned long long*)(ws + o_ctr);
   L.abort_flags = (int*)(ws + o_abt);
   L.spin_cap = h->cfg.spin_cap;

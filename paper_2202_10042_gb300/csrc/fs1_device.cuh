@@ -57,18 +57,21 @@ __device__ __forceinline__ float c_zero(float) { return 0.f; }
 __device__ __forceinline__ double c_zero(double) { return 0.0; }
 
 __device__ __forceinline__ XF c_add(XF a, XF b) {
-  if (a.e < b.e) { XF t = a; a = b; b = t; }
-  int d = b.e - a.e;
-  float m = a.m + b.m * pow2f(d < -200 ? -200 : d);
-  return xf_norm(m, a.e);
+  const bool sw = a.e < b.e;
+  const float am = sw ? b.m : a.m, bm = sw ? a.m : b.m;
+  const int ae = sw ? b.e : a.e, be = sw ? a.e : b.e;
+  return xf_norm(fmaf(bm, pow2f(be - ae), am), ae);
 }
 __device__ __forceinline__ float c_add(float a, float b) { return a + b; }
 __device__ __forceinline__ double c_add(double a, double b) { return a + b; }
 
+// Products of normalised mantissas stay in [0.25, 1): no renormalisation is
+// needed before the next c_add (which normalises), and exponents remain a
+// bound within two bits.
 __device__ __forceinline__ XF c_mul(XF a, XF b) {
   int e = a.e + b.e;
   e = e < kZeroExp ? kZeroExp : e;
-  return xf_norm(a.m * b.m, e);
+  return XF{a.m * b.m, e};
 }
 __device__ __forceinline__ float c_mul(float a, float b) { return a * b; }
 __device__ __forceinline__ double c_mul(double a, double b) { return a * b; }
@@ -137,6 +140,10 @@ struct OpPlain {
   static __device__ __forceinline__ T zero() { return c_zero(C{}); }
   static __device__ __forceinline__ T fwd(T l, T r, C d, float) { return c_add(c_mul(l, d), r); }
   static __device__ __forceinline__ T bwd(T l, T r, C d, float) { return c_add(l, c_mul(r, d)); }
+  // an aggregate carried across L empty points (d = lam^L): its contribution
+  // to a point L beyond its end
+  static __device__ __forceinline__ T prop(T x, C d, float) { return c_mul(x, d); }
+  static __device__ __forceinline__ T add(T x, T y) { return c_add(x, y); }
   static __device__ __forceinline__ T up(T a, int o) { return shfl_up(a, o); }
   static __device__ __forceinline__ T down(T a, int o) { return shfl_down(a, o); }
   static __device__ __forceinline__ T idx(T a, int l) { return shfl_idx(a, l); }
@@ -158,6 +165,10 @@ struct OpDist {
     // P = d Pl + Pr ; A = d (Al + L Pl) + Ar
     return T{c_add(c_mul(l.p, d), r.p), c_add(c_mul(c_add(l.a, c_scale(l.p, L)), d), r.a)};
   }
+  static __device__ __forceinline__ T prop(T x, C d, float L) {
+    return T{c_mul(x.p, d), c_mul(c_add(x.a, c_scale(x.p, L)), d)};
+  }
+  static __device__ __forceinline__ T add(T x, T y) { return T{c_add(x.p, y.p), c_add(x.a, y.a)}; }
   static __device__ __forceinline__ T bwd(T l, T r, C d, float L) {
     // Q = Ql + d Qr ; B = Bl + d (Br + L Qr)
     return T{c_add(l.p, c_mul(r.p, d)), c_add(l.a, c_mul(c_add(r.a, c_scale(r.p, L)), d))};
@@ -166,6 +177,55 @@ struct OpDist {
   static __device__ __forceinline__ T down(T a, int o) { return T{shfl_down(a.p, o), shfl_down(a.a, o)}; }
   static __device__ __forceinline__ T idx(T a, int l) { return T{shfl_idx(a.p, l), shfl_idx(a.a, l)}; }
 };
+
+// ---------------------------------------------------------------------------
+// warp-wide sums of carries (one term per lane; zero terms allowed)
+// ---------------------------------------------------------------------------
+// Extended range: align every term to the warp's largest exponent (exact
+// power-of-two shifts; terms 2^-126 below the largest vanish) and add in FP32.
+__device__ __forceinline__ XF warp_sum_c(XF t) {
+  const int e = __reduce_max_sync(0xffffffffu, t.m != 0.f ? t.e : kZeroExp);
+  float v = t.m * pow2f(t.e - e);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return xf_norm(v, e);
+}
+__device__ __forceinline__ float warp_sum_c(float t) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  return t;
+}
+__device__ __forceinline__ double warp_sum_c(double t) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  return t;
+}
+template <class C>
+__device__ __forceinline__ PairC<C> warp_sum_c(PairC<C> t) {
+  return PairC<C>{warp_sum_c(t.p), warp_sum_c(t.a)};
+}
+
+// compensated FP32 (double-float) sum across the warp; identical in every lane
+__device__ __forceinline__ void warp_sum_df(float& hi, float& lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    const float s = hi + h2;   // TwoSum(hi, h2)
+    const float bp = s - hi;
+    const float er = (hi - (s - bp)) + (h2 - bp);
+    hi = s;
+    lo = lo + l2 + er;
+  }
+}
+// local compensated accumulation: (hi, lo) += (h2, l2)
+__device__ __forceinline__ void df_add(float& hi, float& lo, float h2, float l2) {
+  const float s = hi + h2;
+  const float bp = s - hi;
+  const float er = (hi - (s - bp)) + (h2 - bp);
+  hi = s;
+  lo = lo + l2 + er;
+}
 
 // ---------------------------------------------------------------------------
 // memory-model helpers for the team exchange
@@ -177,6 +237,17 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
 }
 __device__ __forceinline__ void red_release_add(unsigned long long* p, unsigned long long v) {
   asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+// 64-bit words of the team exchange: each carries a 32-bit payload and the
+// 32-bit epoch tag of the exchange that wrote it, so a reader validates every
+// word on its own and needs no separate flag or barrier round trip.
+__device__ __forceinline__ void st_relaxed_v2(unsigned long long* p, unsigned long long a,
+                                              unsigned long long b) {
+  asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+}
+__device__ __forceinline__ void ld_relaxed_v2(const unsigned long long* p, unsigned long long& a,
+                                              unsigned long long& b) {
+  asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
 }
 __device__ __forceinline__ int ld_relaxed(const int* p) {
   int v;

@@ -31,9 +31,11 @@ struct PairResult {
   int pad;
 };
 
-// Exchange slot of one CTA of a team (one per CTA and buffer parity).
+// Exchange slot of one CTA of a team (one per CTA and buffer parity): up to
+// 16 64-bit words, each a 32-bit payload tagged with the exchange epoch.  Slots
+// must be zeroed before every launch.
 struct alignas(16) Slot {
-  unsigned char raw[64];
+  unsigned char raw[128];
 };
 
 struct TeamLaunch {
@@ -44,8 +46,10 @@ struct TeamLaunch {
   int team_size;                   // T: CTAs per team
   int num_teams;
   int in_f32;                      // 1: a, b are float; 0: double
-  Slot* slots;                     // [num_teams][2][team_size]
-  unsigned long long* counters;    // [num_teams] barrier counters (zeroed per launch)
+  Slot* slots;                     // [num_teams][2][team_size] generic slots
+  unsigned long long* cslots;      // [num_teams][2][team_size][16] compact slots
+                                   // (stabilised path); zeroed per launch
+  unsigned long long* counters;    // [num_teams] reserved (zeroed per launch)
   int* abort_flags;                // [num_teams] (zeroed per launch)
   long long spin_cap;              // bounded-wait polls before giving up
 };

@@ -6,13 +6,13 @@
 // not pay for an allocation (which may synchronise the device).  For them this
 // entry point runs the same 1D team kernel as fs1_w1, but every byte of device
 // scratch it needs (the pair descriptor, the result record, the mass-check
-// record, the team exchange slots, the barrier counter and the abort flag)
+// record, the two sets of team exchange slots, the counter and the abort flag)
 // lives in one file-scope __device__ array of fixed size.  The caller passes
 // device-resident inputs and host outputs; nothing is allocated on the device
 // or the host.
 //
 // Notes for users
-//   - The array (kScratchBytes, about 21 KiB) is part of the library image:
+//   - The array (kScratchBytes, about 81 KiB) is part of the library image:
 //     every GPU that loads the library holds it until the process exits.
 //   - Host code may not use the array's name as a device address (on the host
 //     it names a host-side stand-in).  The first call on each device, with that
@@ -54,7 +54,8 @@ constexpr size_t kOffVal = kOffRes + al(sizeof(PairResult));
 constexpr size_t kOffCtr = kOffVal + al(sizeof(NaValOut));
 constexpr size_t kOffAbort = kOffCtr + al(sizeof(unsigned long long));
 constexpr size_t kOffSlots = kOffAbort + al(sizeof(int));
-constexpr size_t kScratchBytes = kOffSlots + al(sizeof(Slot) * 2 * (size_t)kMaxTeam);
+constexpr size_t kOffCSlots = kOffSlots + al(sizeof(Slot) * 2 * (size_t)kMaxTeam);
+constexpr size_t kScratchBytes = kOffCSlots + al(128 * 2 * (size_t)kMaxTeam);
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
@@ -185,7 +186,8 @@ extern "C" fs1_status fs1_w1_noalloc(const fs1_config* cfg_in, const fs1_problem
       (e = cudaMemcpyAsync(sc + kOffRes, &r0, sizeof r0, cudaMemcpyHostToDevice, stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(sc + kOffCtr, 0, sizeof(unsigned long long), stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(sc + kOffAbort, 0, sizeof(int), stream)) != cudaSuccess ||
-      (e = cudaMemsetAsync(sc + kOffSlots, 0, sizeof(Slot) * 2 * (size_t)T, stream)) != cudaSuccess) {
+      (e = cudaMemsetAsync(sc + kOffSlots, 0, sizeof(Slot) * 2 * (size_t)T, stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(sc + kOffCSlots, 0, 128 * 2 * (size_t)T, stream)) != cudaSuccess) {
     fprintf(stderr, "fs1_w1_noalloc: %s\n", cudaGetErrorString(e));
     return FS1_ECUDA;
   }
@@ -221,6 +223,7 @@ extern "C" fs1_status fs1_w1_noalloc(const fs1_config* cfg_in, const fs1_problem
   L.num_teams = 1;
   L.in_f32 = in_f32;
   L.slots = (Slot*)(sc + kOffSlots);
+  L.cslots = (unsigned long long*)(sc + kOffCSlots);
   L.counters = (unsigned long long*)(sc + kOffCtr);
   L.abort_flags = (int*)(sc + kOffAbort);
   L.spin_cap = spin_cap;

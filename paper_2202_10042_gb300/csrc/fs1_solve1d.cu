@@ -8,16 +8,20 @@
 // Each half-step of Algorithm 1 (the r/s sweeps on phi with the psi update,
 // then the p/q sweeps on psi with the phi update) is a bidirectional chunked
 // parallel scan of the recurrences of Section 3, eq. "recursion":
-//   thread   : the recurrences run serially over the thread's E points;
-//   warp     : Kogge-Stone over the 32 thread aggregates (shuffles);
-//   CTA      : the same over the warp aggregates (shared memory);
-//   team     : every CTA publishes its aggregates to a global slot, passes one
-//              bounded team barrier, and scans the T published aggregates.
-// The aggregates of the half-step's output are formed while the output is
-// produced, so one team barrier per half-step is the only global sync.  The
-// marginal error of the while condition of Algorithm 1 (FP64 reduction of FP32
-// terms) rides on the same barrier, and every CTA takes the stop decision from
-// the same FP64 sum.
+//   thread : the recurrences run serially over the thread's E points;
+//   warp   : Kogge-Stone over the 32 thread aggregates (shuffles), in plain
+//            FP32 inside one per-warp frame when the warp's values span a
+//            narrow exponent range, in extended range otherwise;
+//   CTA    : warp 0 scans the 16 warp aggregates;
+//   team   : warp 0 publishes the CTA aggregates and the error partial as
+//            epoch-tagged 64-bit words, polls the T published slots (every
+//            word validates itself, so one L2 round trip suffices) and scans
+//            them.  This is the only global synchronisation of a half-step.
+// The aggregates of a half-step's output are formed while the output is
+// produced.  The marginal error of the while condition of Algorithm 1 (FP32
+// terms, compensated FP32 sums inside a warp, FP64 across warps and CTAs)
+// rides on the same exchange, and every CTA takes the stop decision from the
+// same FP64 sum.
 //
 // Variants (template parameters):
 //   V = double, C = double : plain FS-1 (Algorithm 1 as written), FP64.
@@ -30,11 +34,12 @@
 //                            extended-range values combined by exponent
 //                            alignment (a max-shifted log-sum-exp in base 2).
 // At the end the transport cost sum_ij u_i K_ij |i-j| h v_j is formed in O(N)
-// with the distance-weighted recurrences (OpDist) and reduced in FP64.
+// with distance-weighted recurrences (OpDist) and reduced in FP64.
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdio>
+#include <type_traits>
 
 #include "fs1.h"
 #include "fs1_device.cuh"
@@ -44,243 +49,374 @@ namespace fs1 {
 
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
+constexpr int kSlotWords = 16;      // 64-bit words per exchange slot (payload <= 10)
 
 template <class C>
 struct DecayTables {
-  C dt[33];   // lam^{Eeff j}: thread offsets inside a warp
-  C dw[33];   // lam^{32 Eeff j}: warp offsets inside a CTA
-  C dS;       // lam^{S}: one CTA slice
-  C dq[5];    // lam^{S q 2^i}: lane groups of the team scan
+  C dt[33];        // lam^{Eeff j}: thread offsets inside a warp
+  C dw[33];        // lam^{32 Eeff j}: warp offsets inside a CTA
+  C dT[257];       // lam^{S j}: CTA offsets inside a team (S = points per CTA)
+  float dtf[33];   // lam^{Eeff j} in FP32 for the narrow warp scan
+  int narrow;      // 1 if c * 32 * Eeff <= 40 (a warp's decay fits one FP32 frame)
 };
 
-template <class OpT>
-struct HierState {
-  OpT excl_f, excl_b;     // within the warp
-  OpT wexcl_f, wexcl_b;   // warp within the CTA
-  OpT cta_f, cta_b;       // CTA totals
+constexpr int kMaxTeamCtas = 256;   // the team reduction serves up to 256 CTAs
+
+template <class T>
+struct SlotPayload {
+  T f, b;
+  float eh, el;    // error partial as a compensated FP32 pair
 };
 
-// word-wise L1-bypassing load / store of a trivially copyable value
+// per-CTA shared state of an exchange; warp aggregates are double-buffered by
+// exchange parity so that a fast warp can publish the next exchange while a
+// slow one still reads the current one
 template <class T>
-__device__ __forceinline__ T load_cg(const void* p) {
-  static_assert(sizeof(T) % 4 == 0, "");
-  T v;
-  unsigned* w = reinterpret_cast<unsigned*>(&v);
-#pragma unroll
-  for (int i = 0; i < (int)(sizeof(T) / 4); ++i) w[i] = __ldcg(reinterpret_cast<const unsigned*>(p) + i);
-  return v;
-}
-template <class T>
-__device__ __forceinline__ void store_cg(void* p, const T& v) {
-  const unsigned* w = reinterpret_cast<const unsigned*>(&v);
-#pragma unroll
-  for (int i = 0; i < (int)(sizeof(T) / 4); ++i) __stcg(reinterpret_cast<unsigned*>(p) + i, w[i]);
+struct XchgSmem {
+  T wf[2][kWarps], wb[2][kWarps];
+  float eh[2][kWarps], el[2][kWarps];
+  T pf[kWarps], pb[kWarps];             // partial team carries (one per warp)
+  float ph[kWarps], pl[kWarps];
+  int ok;
+  SlotPayload<T> stage[kMaxTeamCtas];   // validated team slots
+};
+
+// split an error partial into a compensated FP32 pair
+__device__ __forceinline__ void to_df(float x, float& hi, float& lo) { hi = x; lo = 0.f; }
+__device__ __forceinline__ void to_df(double x, float& hi, float& lo) {
+  hi = (float)x;
+  lo = (float)(x - (double)hi);
 }
 
 // ---------------------------------------------------------------------------
-// team barrier: bounded, abortable.  Returns false when it gave up.
+// exchange slots: payload words tagged with the exchange epoch
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool team_barrier(unsigned long long* ctr, unsigned long long target,
-                                             int* abort_flag, long long cap, int* sm_ok) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    red_release_add(ctr, 1ull);
-    int ok = 1;
-    long long spins = 0;
-    while (ld_acquire(ctr) < target) {
-      if (++spins > cap || ld_relaxed(abort_flag)) {
-        ok = 0;
-        atomicExch(abort_flag, 1);
-        break;
-      }
-      if (spins > 64) __nanosleep(64);
-    }
-    *sm_ok = ok;
+template <class T>
+__device__ __forceinline__ void slot_publish(Slot* s, const T& f, const T& b, float eh, float el, unsigned tag) {
+  SlotPayload<T> pl{f, b, eh, el};
+  constexpr int nw = (int)(sizeof(SlotPayload<T>) / 4);
+  static_assert(nw <= kSlotWords, "slot too small");
+  const unsigned* w = reinterpret_cast<const unsigned*>(&pl);
+  unsigned long long* dst = reinterpret_cast<unsigned long long*>(s->raw);
+  const unsigned long long t = (unsigned long long)tag << 32;
+#pragma unroll
+  for (int i = 0; i < nw; i += 2) {
+    const unsigned long long w0 = t | w[i];
+    const unsigned long long w1 = t | (i + 1 < nw ? w[i + 1] : 0u);
+    st_relaxed_v2(dst + i, w0, w1);
   }
-  __syncthreads();
-  return *sm_ok != 0;
+}
+
+// returns true when every word carries `tag`
+template <class T>
+__device__ __forceinline__ bool slot_try_read(const Slot* s, unsigned tag, SlotPayload<T>& out) {
+  constexpr int nw = (int)(sizeof(SlotPayload<T>) / 4);
+  unsigned* w = reinterpret_cast<unsigned*>(&out);
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(s->raw);
+  bool ok = true;
+#pragma unroll
+  for (int i = 0; i < nw; i += 2) {
+    unsigned long long w0, w1;
+    ld_relaxed_v2(src + i, w0, w1);
+    ok &= (unsigned)(w0 >> 32) == tag;
+    ok &= (unsigned)(w1 >> 32) == tag;
+    w[i] = (unsigned)w0;
+    if (i + 1 < nw) w[i + 1] = (unsigned)w1;
+  }
+  return ok;
 }
 
 // ---------------------------------------------------------------------------
-// hierarchical scan, phase A: warp and CTA levels (before the team barrier)
+// warp-level scans of the thread aggregates (phase A)
 // ---------------------------------------------------------------------------
+// generic: inclusive forward / backward Kogge-Stone with the operator
 template <class Op, class C>
-__device__ __forceinline__ void scan_local(typename Op::T af, typename Op::T ab, int Eeff,
-                                           const DecayTables<C>& tb, typename Op::T* sm_wf,
-                                           typename Op::T* sm_wb, HierState<typename Op::T>& st) {
+__device__ __forceinline__ void warp_scan_generic(typename Op::T af, typename Op::T ab, int Eeff,
+                                                  const DecayTables<C>& tb, typename Op::T& excl_f,
+                                                  typename Op::T& excl_b, typename Op::T& wtot_f,
+                                                  typename Op::T& wtot_b) {
+  using T = typename Op::T;
+  const int lane = threadIdx.x & 31;
+  T x = af, z = ab;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T y = Op::up(x, o);
+    const T w = Op::down(z, o);
+    if (lane >= o) x = Op::fwd(y, x, tb.dt[o], (float)(Eeff * o));
+    if (lane + o < 32) z = Op::bwd(z, w, tb.dt[o], (float)(Eeff * o));
+  }
+  const T ex = Op::up(x, 1);
+  const T eb = Op::down(z, 1);
+  excl_f = lane == 0 ? Op::zero() : ex;
+  excl_b = lane == 31 ? Op::zero() : eb;
+  wtot_f = Op::idx(x, 31);
+  wtot_b = Op::idx(z, 0);
+}
+
+// narrow stabilised path: one FP32 frame per warp (exact power-of-two shifts)
+__device__ __forceinline__ bool warp_scan_narrow(XF af, XF ab, const DecayTables<XF>& tb, XF& excl_f,
+                                                 XF& excl_b, XF& wtot_f, XF& wtot_b) {
+  const int lane = threadIdx.x & 31;
+  const int emax = __reduce_max_sync(0xffffffffu, max(af.e, ab.e));
+  const int lo_f = af.m != 0.f ? af.e : INT_MAX;
+  const int lo_b = ab.m != 0.f ? ab.e : INT_MAX;
+  const int emin = __reduce_min_sync(0xffffffffu, min(lo_f, lo_b));
+  if (!tb.narrow || (emin != INT_MAX && emax - emin > 50)) return false;
+  float x = af.m * pow2f(af.e - emax);
+  float z = ab.m * pow2f(ab.e - emax);
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float y = __shfl_up_sync(0xffffffffu, x, o);
+    const float w = __shfl_down_sync(0xffffffffu, z, o);
+    if (lane >= o) x = fmaf(tb.dtf[o], y, x);
+    if (lane + o < 32) z = fmaf(tb.dtf[o], w, z);
+  }
+  const float ex = __shfl_up_sync(0xffffffffu, x, 1);
+  const float eb = __shfl_down_sync(0xffffffffu, z, 1);
+  excl_f = xf_norm(lane == 0 ? 0.f : ex, emax);
+  excl_b = xf_norm(lane == 31 ? 0.f : eb, emax);
+  wtot_f = xf_norm(__shfl_sync(0xffffffffu, x, 31), emax);
+  wtot_b = xf_norm(__shfl_sync(0xffffffffu, z, 0), emax);
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// compact exchange slots of the stabilised path: two 64-bit words, read with
+// one 16-byte load.  Every slot sits alone in its own 128-byte line, so
+// each line is polled once per CTA per round (dense slots would put several
+// pollers of one CTA on the same line, and that line's L2 slice is the
+// bottleneck of the exchange).  Bits of a word: payload [0, 56), epoch tag
+// [56, 64); a word left from an earlier exchange of the same parity is at
+// least two epochs old, so its tag differs.
+//   w0: frac(f) 23 | exp(f) 16 | exp(b) 16
+//   w1: frac(b) 23 | error partial (FP32 without its sign) 31
+// Exponents must fit 16 bits; pairs whose potentials could exceed that use
+// the generic slots (decided per pair from c N).
+// ---------------------------------------------------------------------------
+constexpr int kCompactWords = 16;   // one 128-byte line per compact slot
+constexpr int kExpNone = -32768;
+
+__device__ __forceinline__ void xf_bits(XF x, unsigned& frac, unsigned& e16) {
+  const XF n = xf_norm(x.m, x.e);   // mantissa in [0.5, 1): 23 fraction bits
+  frac = __float_as_uint(n.m) & 0x7FFFFFu;
+  e16 = n.m != 0.f ? ((unsigned)n.e & 0xFFFFu) : ((unsigned)kExpNone & 0xFFFFu);
+}
+__device__ __forceinline__ XF xf_unbits(unsigned frac, unsigned e16) {
+  const int e = (int)(short)(e16 & 0xFFFFu);
+  if (e == kExpNone) return XF{0.f, kZeroExp};
+  return XF{__uint_as_float(frac | (126u << 23)), e};
+}
+
+// publish / poll a CTA's slot: compact words for XF carries when `compact`,
+// tagged 32-bit chunks (generic slots) otherwise
+template <class T>
+__device__ __forceinline__ void publish(const TeamLaunch& L, int team, int rank, unsigned epoch, bool compact,
+                                        const T& f, const T& b, float eh, float el) {
+  const int T_ = L.team_size;
+  if constexpr (std::is_same<T, XF>::value) {
+    if (compact) {
+      unsigned long long* w = L.cslots + (((size_t)team * 2 + (epoch & 1)) * T_ + rank) * kCompactWords;
+      unsigned ff, fe, bf, be;
+      xf_bits(f, ff, fe);
+      xf_bits(b, bf, be);
+      const unsigned long long tag = (unsigned long long)(epoch & 0xFFu) << 56;
+      const float ev = eh + el;
+      const unsigned long long w0 = tag | ff | ((unsigned long long)fe << 23) | ((unsigned long long)be << 39);
+      const unsigned long long w1 =
+          tag | bf | ((unsigned long long)(__float_as_uint(ev) & 0x7FFFFFFFu) << 23);
+      st_relaxed_v2(w, w0, w1);
+      return;
+    }
+  }
+  Slot* s = L.slots + ((size_t)team * 2 + (epoch & 1)) * T_ + rank;
+  slot_publish<T>(s, f, b, eh, el, epoch);
+}
+template <class T>
+__device__ __forceinline__ bool try_read(const TeamLaunch& L, int team, int j, unsigned epoch, bool compact,
+                                         SlotPayload<T>& out) {
+  const int T_ = L.team_size;
+  if constexpr (std::is_same<T, XF>::value) {
+    if (compact) {
+      const unsigned long long* w = L.cslots + (((size_t)team * 2 + (epoch & 1)) * T_ + j) * kCompactWords;
+      unsigned long long w0, w1;
+      ld_relaxed_v2(w, w0, w1);
+      const unsigned tg = epoch & 0xFFu;
+      if ((unsigned)(w0 >> 56) != tg || (unsigned)(w1 >> 56) != tg) return false;
+      out.f = xf_unbits((unsigned)(w0 & 0x7FFFFFu), (unsigned)(w0 >> 23));
+      out.b = xf_unbits((unsigned)(w1 & 0x7FFFFFu), (unsigned)(w0 >> 39));
+      out.eh = __uint_as_float((unsigned)(w1 >> 23) & 0x7FFFFFFFu);
+      out.el = 0.f;
+      return true;
+    }
+  }
+  const Slot* s = L.slots + ((size_t)team * 2 + (epoch & 1)) * T_ + j;
+  return slot_try_read<T>(s, epoch, out);
+}
+
+// sums over the 16 lanes of each half-warp
+__device__ __forceinline__ XF hw_sum(XF t) {
+  int e = t.m != 0.f ? t.e : kZeroExp;
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+  float v = t.m * pow2f(t.e - e);
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return xf_norm(v, e);
+}
+__device__ __forceinline__ float hw_sum(float t) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  return t;
+}
+__device__ __forceinline__ double hw_sum(double t) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  return t;
+}
+template <class C>
+__device__ __forceinline__ PairC<C> hw_sum(PairC<C> t) {
+  return PairC<C>{hw_sum(t.p), hw_sum(t.a)};
+}
+__device__ __forceinline__ void hw_sum_df(float& hi, float& lo) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    df_add(hi, lo, h2, l2);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// one exchange.  Every thread ends with its carries: the forward value at the
+// point before its first point and the backward value at its last point.
+//   A  warp: Kogge-Stone of the thread aggregates; warp totals to shared
+//      memory (double-buffered); the error partial as a compensated pair.
+//   B  every warp forms its own CTA-local carry as one decay-weighted sum of
+//      the other warps' totals (lam^{32 Eeff k} table), with no serial
+//      CTA-level scan; warp 0 also forms the CTA totals and publishes them.
+//   C  (teams) every thread tid < T polls slot tid; after a block barrier the
+//      16 warps each reduce 16 staged slots into partial team carries of this
+//      CTA (decay-weighted by the lam^{S k} table), and after a second block
+//      barrier every warp sums the 16 partials.
+// The stop decision is taken by every warp from the same compensated FP32 sum,
+// so all warps and all CTAs agree.  Returns false when a bounded wait gave
+// up.  decision: 0 continue, 1 error <= tol, 2 error not finite.
+// ---------------------------------------------------------------------------
+template <class Op, class C, class EV>
+__device__ __forceinline__ bool exchange(const TeamLaunch& L, int team, int rank, unsigned& epoch,
+                                         unsigned& xc, typename Op::T af, typename Op::T ab, EV err_part,
+                                         int Eeff, const DecayTables<C>& tb, XchgSmem<typename Op::T>& X,
+                                         typename Op::T& cf, typename Op::T& cb, float tol_h, float tol_l,
+                                         int& decision, float* err_h, float* err_l, bool compact = false) {
   using T = typename Op::T;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T x = af;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    T y = Op::up(x, o);
-    if (lane >= o) x = Op::fwd(y, x, tb.dt[o], (float)(Eeff * o));
+  const int T_ = L.team_size;
+  const int par = (int)(xc++ & 1u);
+  // ---- A
+  float eh, el;
+  to_df(err_part, eh, el);
+  warp_sum_df(eh, el);
+  T excl_f, excl_b, wt_f, wt_b;
+  bool done = false;
+  if constexpr (std::is_same<T, XF>::value) done = warp_scan_narrow(af, ab, tb, excl_f, excl_b, wt_f, wt_b);
+  if (!done) warp_scan_generic<Op, C>(af, ab, Eeff, tb, excl_f, excl_b, wt_f, wt_b);
+  if (lane == 0) {
+    X.wf[par][warp] = wt_f;
+    X.wb[par][warp] = wt_b;
+    X.eh[par][warp] = eh;
+    X.el[par][warp] = el;
   }
-  T ex = Op::up(x, 1);
-  st.excl_f = lane == 0 ? Op::zero() : ex;
-  if (lane == 31) sm_wf[warp] = x;
-  T z = ab;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    T y = Op::down(z, o);
-    if (lane + o < 32) z = Op::bwd(z, y, tb.dt[o], (float)(Eeff * o));
-  }
-  T eb = Op::down(z, 1);
-  st.excl_b = lane == 31 ? Op::zero() : eb;
-  if (lane == 0) sm_wb[warp] = z;
   __syncthreads();
-  // CTA level, redundantly in every warp (no second block barrier needed)
-  T wx = lane < kWarps ? sm_wf[lane] : Op::zero();
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    T y = Op::up(wx, o);
-    if (lane >= o) wx = Op::fwd(y, wx, tb.dw[o], (float)(32 * Eeff * o));
-  }
-  T pf = Op::idx(wx, warp > 0 ? warp - 1 : 0);
-  st.wexcl_f = warp == 0 ? Op::zero() : pf;
-  st.cta_f = Op::idx(wx, kWarps - 1);
-  T wz = lane < kWarps ? sm_wb[lane] : Op::zero();
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    T y = Op::down(wz, o);
-    if (lane + o < 32) wz = Op::bwd(wz, y, tb.dw[o], (float)(32 * Eeff * o));
-  }
-  T pb = Op::idx(wz, warp + 1 < kWarps ? warp + 1 : 0);
-  st.wexcl_b = warp == kWarps - 1 ? Op::zero() : pb;
-  st.cta_b = Op::idx(wz, 0);
-}
-
-// phase C: the thread's carries from the team carries of its CTA
-template <class Op, class C>
-__device__ __forceinline__ void scan_carries(const HierState<typename Op::T>& st, typename Op::T tcf,
-                                             typename Op::T tcb, int Eeff, const DecayTables<C>& tb,
-                                             typename Op::T& cf, typename Op::T& cb) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  auto wcf = Op::fwd(tcf, st.wexcl_f, tb.dw[warp], (float)(32 * Eeff * warp));
-  cf = Op::fwd(wcf, st.excl_f, tb.dt[lane], (float)(Eeff * lane));
-  const int wr = kWarps - 1 - warp;
-  auto wcb = Op::bwd(st.wexcl_b, tcb, tb.dw[wr], (float)(32 * Eeff * wr));
-  cb = Op::bwd(st.excl_b, wcb, tb.dt[31 - lane], (float)(Eeff * (31 - lane)));
-}
-
-// slot byte offsets
-constexpr int kSlotF = 0, kSlotB = 16, kSlotErr = 32;
-
-// team level (warp 0): scan the T published CTA aggregates, return this CTA's
-// exclusive carries and the FP64 sum of the published error partials.
-template <class Op, class C>
-__device__ __forceinline__ void scan_team(const Slot* slots, int T, int rank, const DecayTables<C>& tb,
-                                          int S, typename Op::T& tcf, typename Op::T& tcb,
-                                          double& err_sum) {
-  using OT = typename Op::T;
-  const int lane = threadIdx.x & 31;
-  const int q = (T + 31) >> 5;
-  const int j0 = lane * q, j1 = min(T, j0 + q);
-  OT af = Op::zero(), ab = Op::zero();
-  double es = 0.0;
-  for (int j = j0; j < j1; ++j) {
-    af = Op::fwd(af, load_cg<OT>(slots[j].raw + kSlotF), tb.dS, (float)S);
-    es += load_cg<double>(slots[j].raw + kSlotErr);
-  }
-  for (int j = j1 - 1; j >= j0; --j) ab = Op::bwd(load_cg<OT>(slots[j].raw + kSlotB), ab, tb.dS, (float)S);
-  // lane-level scans
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    const int o = 1 << i;
-    OT y = Op::up(af, o);
-    if (lane >= o) af = Op::fwd(y, af, tb.dq[i], (float)S * (float)(q * o));
-  }
-#pragma unroll
-  for (int i = 0; i < 5; ++i) {
-    const int o = 1 << i;
-    OT y = Op::down(ab, o);
-    if (lane + o < 32) ab = Op::bwd(ab, y, tb.dq[i], (float)S * (float)(q * o));
-  }
-  OT exf = Op::up(af, 1);
-  if (lane == 0) exf = Op::zero();
-  OT exb = Op::down(ab, 1);
-  if (lane == 31) exb = Op::zero();
-  const int owner = rank / q;
-  OT rf = exf, rb = exb;
-  if (lane == owner) {
-    for (int j = owner * q; j < rank; ++j) rf = Op::fwd(rf, load_cg<OT>(slots[j].raw + kSlotF), tb.dS, (float)S);
-    for (int j = min(T, owner * q + q) - 1; j > rank; --j)
-      rb = Op::bwd(load_cg<OT>(slots[j].raw + kSlotB), rb, tb.dS, (float)S);
-  }
-  tcf = Op::idx(rf, owner);
-  tcb = Op::idx(rb, owner);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) es += __shfl_xor_sync(0xffffffffu, es, o);
-  err_sum = es;
-}
-
-// ---------------------------------------------------------------------------
-// one exchange round: local scan, publish, team barrier, team scan, carries
-// ---------------------------------------------------------------------------
-template <class Op, class C>
-struct Exchange {
-  typename Op::T* sm_wf;
-  typename Op::T* sm_wb;
-  double* sm_err;      // [kWarps]
-  typename Op::T* sm_tc;  // [2]: team carries
-  double* sm_errsum;
-  int* sm_ok;
-};
-
-template <class Op, class C>
-__device__ __forceinline__ bool exchange(const TeamLaunch& L, int team, int rank, unsigned long long& nbar,
-                                         typename Op::T af, typename Op::T ab, double err_part, int Eeff,
-                                         const DecayTables<C>& tb, const Exchange<Op, C>& X,
-                                         typename Op::T& cf, typename Op::T& cb, double& err_total) {
-  using OT = typename Op::T;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // CTA error partial: fixed-order FP64 reduction
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) err_part += __shfl_xor_sync(0xffffffffu, err_part, o);
-  if (lane == 0) X.sm_err[warp] = err_part;
-  HierState<OT> st;
-  scan_local<Op, C>(af, ab, Eeff, tb, X.sm_wf, X.sm_wb, st);   // contains __syncthreads
-  const int T = L.team_size;
-  const int S = kThreads * Eeff;
-  bool ok = true;
-  if (T == 1) {
-    if (threadIdx.x == 0) {
-      double e = 0.0;
-      for (int w = 0; w < kWarps; ++w) e += X.sm_err[w];
-      *X.sm_errsum = e;
+  // ---- B: CTA-local carries of this warp, CTA error sum (every warp)
+  const float Wf = (float)(32 * Eeff);
+  T tf = Op::zero(), tbk = Op::zero();
+  if (lane < warp) tf = Op::prop(X.wf[par][lane], tb.dw[warp - 1 - lane], Wf * (float)(warp - 1 - lane));
+  if (lane > warp && lane < kWarps)
+    tbk = Op::prop(X.wb[par][lane], tb.dw[lane - warp - 1], Wf * (float)(lane - warp - 1));
+  const T pf = warp_sum_c(tf);
+  const T pb = warp_sum_c(tbk);
+  float th = lane < kWarps ? X.eh[par][lane] : 0.f;
+  float tl = lane < kWarps ? X.el[par][lane] : 0.f;
+  warp_sum_df(th, tl);
+  T tcf = Op::zero(), tcb = Op::zero();
+  if (T_ > 1) {
+    ++epoch;
+    if (warp == 0) {
+      // CTA totals, published by lane 0
+      T xf = Op::zero(), xb = Op::zero();
+      if (lane < kWarps) {
+        xf = Op::prop(X.wf[par][lane], tb.dw[kWarps - 1 - lane], Wf * (float)(kWarps - 1 - lane));
+        xb = Op::prop(X.wb[par][lane], tb.dw[lane], Wf * (float)lane);
+      }
+      const T ctf = warp_sum_c(xf);
+      const T ctb = warp_sum_c(xb);
+      if (lane == 0) publish<T>(L, team, rank, epoch, compact, ctf, ctb, th, tl);
+    }
+    // ---- C: every thread with tid < T polls slot tid (independent loads)
+    if ((int)threadIdx.x < T_) {
+      SlotPayload<T> p;
+      long long spins = 0;
+      bool good = true;
+      while (!try_read<T>(L, team, threadIdx.x, epoch, compact, p)) {
+        if (++spins > L.spin_cap || ((spins & 63) == 0 && ld_relaxed(L.abort_flags + team))) {
+          good = false;
+          break;
+        }
+        // the pollers have no other work: spin, and sleep only when a
+        // wait runs long (a sleep's wake-up is much coarser than an L2 trip)
+        if (spins > 8192) __nanosleep(256);
+      }
+      if (good) {
+        X.stage[threadIdx.x] = p;
+      } else {
+        atomicExch(L.abort_flags + team, 1);
+        atomicExch(&X.ok, 0);
+      }
     }
     __syncthreads();
-    err_total = *X.sm_errsum;
-    scan_carries<Op, C>(st, Op::zero(), Op::zero(), Eeff, tb, cf, cb);
-    return true;
-  }
-  ++nbar;
-  Slot* slots = L.slots + ((size_t)team * 2 + (nbar & 1)) * T;
-  if (threadIdx.x == 0) {
-    double e = 0.0;
-    for (int w = 0; w < kWarps; ++w) e += X.sm_err[w];
-    Slot* s = slots + rank;
-    store_cg<OT>(s->raw + kSlotF, st.cta_f);
-    store_cg<OT>(s->raw + kSlotB, st.cta_b);
-    store_cg<double>(s->raw + kSlotErr, e);
-  }
-  ok = team_barrier(L.counters + team, nbar * (unsigned long long)T, L.abort_flags + team, L.spin_cap,
-                    X.sm_ok);
-  if (!ok) return false;
-  if (warp == 0) {
-    OT tcf, tcb;
-    double es;
-    scan_team<Op, C>(slots, T, rank, tb, S, tcf, tcb, es);
-    if (lane == 0) {
-      X.sm_tc[0] = tcf;
-      X.sm_tc[1] = tcb;
-      *X.sm_errsum = es;
+    if (!X.ok) return false;
+    // partial team carries: warp w reduces slots 16 w .. 16 w + 15; lanes
+    // 0-15 the forward terms, lanes 16-31 the backward terms
+    const float Sf = (float)(kThreads * Eeff);
+    const int j = 16 * warp + (lane & 15);
+    T term = Op::zero();
+    float ph = 0.f, pl = 0.f;
+    if (j < T_) {
+      const int k = lane < 16 ? rank - 1 - j : j - rank - 1;
+      if (k >= 0) term = Op::prop(lane < 16 ? X.stage[j].f : X.stage[j].b, tb.dT[k], Sf * (float)k);
+      if (lane < 16) {
+        ph = X.stage[j].eh;
+        pl = X.stage[j].el;
+      }
     }
+    const T part = hw_sum(term);
+    hw_sum_df(ph, pl);
+    if (lane == 0) {
+      X.pf[warp] = part;
+      X.ph[warp] = ph;
+      X.pl[warp] = pl;
+    }
+    if (lane == 16) X.pb[warp] = part;
+    __syncthreads();
+    const T q = lane < 16 ? X.pf[lane] : X.pb[lane - 16];
+    const T tot = hw_sum(q);
+    tcf = Op::idx(tot, 0);
+    tcb = Op::idx(tot, 16);
+    th = lane < 16 ? X.ph[lane] : 0.f;
+    tl = lane < 16 ? X.pl[lane] : 0.f;
+    warp_sum_df(th, tl);
   }
-  __syncthreads();
-  err_total = *X.sm_errsum;
-  scan_carries<Op, C>(st, X.sm_tc[0], X.sm_tc[1], Eeff, tb, cf, cb);
+  // ---- decision (compensated FP32, identical in every warp) and carries
+  decision = !(isfinite(th) && isfinite(tl)) ? 2 : (((th - tol_h) + (tl - tol_l)) <= 0.f ? 1 : 0);
+  if (err_h) {
+    *err_h = th;
+    *err_l = tl;
+  }
+  const T wcf = Op::fwd(tcf, pf, tb.dw[warp], Wf * (float)warp);
+  cf = Op::fwd(wcf, excl_f, tb.dt[lane], (float)(Eeff * lane));
+  const int wr = kWarps - 1 - warp;
+  const T wcb = Op::bwd(pb, tcb, tb.dw[wr], Wf * (float)wr);
+  cb = Op::bwd(excl_b, wcb, tb.dt[31 - lane], (float)(Eeff * (31 - lane)));
   return true;
 }
 
@@ -297,7 +433,7 @@ __device__ __forceinline__ V load_mass(const void* p, int64_t i, int in_f32) {
 
 template <class V, class C, int E>
 __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int mode) {
-  constexpr bool EXT = sizeof(C) != sizeof(V) || !std::is_same<C, V>::value;
+  constexpr bool EXT = std::is_same<C, XF>::value;
   using OpP = OpPlain<C>;
   using OpD = OpDist<C>;
   using PT = typename OpP::T;
@@ -308,20 +444,21 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
   V* sm_b = sm_a + E * kThreads;
 
   __shared__ DecayTables<C> tb;
-  __shared__ DT sm_wf[kWarps], sm_wb[kWarps], sm_tc[2];
-  __shared__ double sm_err[kWarps], sm_errsum;
-  __shared__ int sm_ok;
-
-  Exchange<OpP, C> XP{reinterpret_cast<PT*>(sm_wf), reinterpret_cast<PT*>(sm_wb), sm_err,
-                      reinterpret_cast<PT*>(sm_tc), &sm_errsum, &sm_ok};
-  Exchange<OpD, C> XD{sm_wf, sm_wb, sm_err, sm_tc, &sm_errsum, &sm_ok};
+  // separate exchange state per element type (no aliasing between them)
+  __shared__ XchgSmem<DT> XD;
+  __shared__ XchgSmem<PT> XP;
 
   const int T = L.team_size;
   const int team = blockIdx.x / T;
   const int rank = blockIdx.x % T;
   const int tid = threadIdx.x;
   if (team >= L.num_teams) return;
-  unsigned long long nbar = 0;
+  unsigned epoch = 0, xc = 0;
+  if (tid == 0) {
+    XD.ok = 1;
+    XP.ok = 1;
+  }
+  __syncthreads();
 
   for (int pi = team; pi < L.num_pairs; pi += L.num_teams) {
     const int pid = L.order ? L.order[pi] : pi;
@@ -333,16 +470,23 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
     const int S = kThreads * Eeff;
     const int64_t s0 = (int64_t)rank * S;
     const int64_t g0 = s0 + (int64_t)tid * Eeff;   // first grid point of this thread
-    int ne = (int)max((int64_t)0, min((int64_t)Eeff, N - g0));
+    const int ne = (int)max((int64_t)0, min((int64_t)Eeff, N - g0));
+    // compact exchange slots need every exponent within 16 bits: the
+    // potentials span at most about c N nats plus the mass range
+    const bool compact = EXT && (c * (double)N + 200.0) * 1.4426950408889634 < 30000.0;
 
     // decay tables (FP64 exponent arithmetic, once per pair)
-    if (tid < 33) tb.dt[tid] = c_decay((double)Eeff * tid, c, C{});
-    else if (tid < 66) tb.dw[tid - 33] = c_decay(32.0 * Eeff * (tid - 33), c, C{});
-    else if (tid == 66) tb.dS = c_decay((double)S, c, C{});
-    else if (tid >= 67 && tid < 72) {
-      const int q = (T + 31) >> 5;
-      tb.dq[tid - 67] = c_decay((double)S * q * (double)(1 << (tid - 67)), c, C{});
+    for (int i = tid; i < 33 + 33 + 257; i += kThreads) {
+      if (i < 33) {
+        tb.dt[i] = c_decay((double)Eeff * i, c, C{});
+        tb.dtf[i] = (float)exp(-(double)Eeff * i * c);
+      } else if (i < 66) {
+        tb.dw[i - 33] = c_decay(32.0 * Eeff * (i - 33), c, C{});
+      } else {
+        tb.dT[i - 66] = c_decay((double)S * (i - 66), c, C{});
+      }
     }
+    if (tid == 0) tb.narrow = (c * 32.0 * Eeff <= 40.0) ? 1 : 0;
     // masses into shared memory, [k][thread] layout
     for (int i = tid; i < S; i += kThreads) {
       const int64_t gi = s0 + i;
@@ -356,21 +500,22 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
       sm_b[kk * kThreads + tt] = vb;
     }
 
-    // state: u (xu, frame fu), v (xv, frame fv); hx = frame + exponent of max
-    V xu[E], xv[E], xn[E], t[E];
+    // state: u (xu, frame fu), v (xv, frame fv); h* = frame + exponent of max
+    V xu[E], xv[E], xn[E];
     int fu = 0, fv = 0, hu = kZeroExp, hv = kZeroExp;
     {
       const V init = (V)(1.0 / (double)N);
-      const double* fi = mode == 1 ? P.f_init : P.f_init;
-      if (fi != nullptr) {
+      if (P.f_init != nullptr) {
         // warm start (or the kernel-apply mode): log values -> frame + mantissas
         double fmax = -INFINITY;
         for (int k = 0; k < E; ++k)
-          if (k < ne) fmax = fmax > fi[g0 + k] ? fmax : fi[g0 + k];
+          if (k < ne) fmax = fmax > P.f_init[g0 + k] ? fmax : P.f_init[g0 + k];
         if (EXT) fu = isfinite(fmax) ? (int)floor(fmax * 1.4426950408889634) : 0;
+#pragma unroll
         for (int k = 0; k < E; ++k)
-          xu[k] = (k < ne) ? (V)exp2(fi[g0 + k] * 1.4426950408889634 - (double)fu) : (V)0;
+          xu[k] = (k < ne) ? (V)exp2(P.f_init[g0 + k] * 1.4426950408889634 - (double)fu) : (V)0;
       } else {
+#pragma unroll
         for (int k = 0; k < E; ++k) xu[k] = (k < ne) ? init : (V)0;
       }
       if (P.g_init != nullptr && mode == 0) {
@@ -378,13 +523,19 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
         for (int k = 0; k < E; ++k)
           if (k < ne) gmax = gmax > P.g_init[g0 + k] ? gmax : P.g_init[g0 + k];
         if (EXT) fv = isfinite(gmax) ? (int)floor(gmax * 1.4426950408889634) : 0;
+#pragma unroll
         for (int k = 0; k < E; ++k)
           xv[k] = (k < ne) ? (V)exp2(P.g_init[g0 + k] * 1.4426950408889634 - (double)fv) : (V)0;
       } else {
+#pragma unroll
         for (int k = 0; k < E; ++k) xv[k] = (k < ne) ? init : (V)0;
       }
       V mu = 0, mv = 0;
-      for (int k = 0; k < E; ++k) { mu = xu[k] > mu ? xu[k] : mu; mv = xv[k] > mv ? xv[k] : mv; }
+#pragma unroll
+      for (int k = 0; k < E; ++k) {
+        mu = xu[k] > mu ? xu[k] : mu;
+        mv = xv[k] > mv ? xv[k] : mv;
+      }
       if (EXT) {
         hu = mu > 0 ? fu + fexp((float)mu) : kZeroExp;
         hv = mv > 0 ? fv + fexp((float)mv) : kZeroExp;
@@ -394,71 +545,71 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
 
     // aggregates of the initial u
     PT cf, cb;
-    double err = 0.0;
     {
       V r = 0, s = 0;
+#pragma unroll
       for (int k = 0; k < E; ++k)
         if (k < Eeff) r = lam * r + xu[k];
+#pragma unroll
       for (int k = E - 1; k >= 0; --k)
         if (k < Eeff) s = lam * (s + xu[k]);
-      if (!exchange<OpP, C>(L, team, rank, nbar, c_from(r, fu, C{}), c_from(s, fu, C{}), 0.0, Eeff, tb,
-                            XP, cf, cb, err))
+      int dec;
+      if (!exchange<OpP, C>(L, team, rank, epoch, xc, c_from(r, fu, C{}), c_from(s, fu, C{}), (V)0, Eeff, tb, XP,
+                            cf, cb, 0.f, 0.f, dec, nullptr, nullptr, compact))
         goto timed_out;
     }
 
     {
       int64_t ell = 0;
       int status = FS1_OK;
-      double err_last = 0.0;
+      float eh_last = 0.f, el_last = 0.f;
+      const float tol_h = (float)P.tol;
+      const float tol_l = (float)(P.tol - (double)tol_h);
       for (;;) {
         // ---------------- v-half: y = K^T u, v_new = b / y, marginal error
         {
-          int F = 0;
-          if (EXT) {
-            F = max(hu + 5, max(c_exp(cf), c_exp(cb)) + 2);
-          }
+          const int F = EXT ? max(hu + 5, max(c_exp(cf), c_exp(cb)) + 2) : 0;
           const V sc = EXT ? (V)pow2f(fu - F) : (V)1;
-          V s = (V)c_to(cb, F);
-#pragma unroll
-          for (int k = E - 1; k >= 0; --k)
-            if (k < Eeff) {
-              t[k] = s;
-              s = lam * (s + xu[k] * sc);
-            }
           const V sc2 = EXT ? (V)pow2f(fv + F) : (V)1;
-          V r = (V)c_to(cf, F), r2 = 0, ab = 0, pw = lam, zmax = 0;
-          float ep = 0.f;
+          // forward recurrence with the carry folded in: xn[k] = r_k
+          V r = (V)c_to(cf, F);
 #pragma unroll
           for (int k = 0; k < E; ++k)
             if (k < Eeff) {
               r = lam * r + xu[k] * sc;
-              const V y = r + t[k];
+              xn[k] = r;
+            }
+          // backward recurrence; output, error term and output aggregates
+          V s = (V)c_to(cb, F), af = 0, ab = 0, pw = 1, zmax = 0, ep = 0;
+#pragma unroll
+          for (int k = E - 1; k >= 0; --k)
+            if (k < Eeff) {
+              const V y = xn[k] + s;
               const V m = sm_b[k * kThreads + tid];
               V z = (k < ne) ? vdiv(m, y) : (V)0;
-              if (mode == 1) z = y;   // kernel-apply mode: keep K^T u itself
-              if (k < ne) ep += (float)fabs(xv[k] * y * sc2 - m);
+              if (mode == 1) z = (k < ne) ? y : (V)0;   // kernel-apply mode: keep K^T u
+              if (k < ne) ep += fabs(xv[k] * y * sc2 - m);
               xn[k] = z;
               zmax = z > zmax ? z : zmax;
-              r2 = lam * r2 + z;
-              ab = ab + pw * z;
+              af = af + pw * z;
               pw = pw * lam;
+              ab = lam * (ab + z);
+              s = lam * (s + xu[k] * sc);
             }
           const int fz = EXT ? -F : 0;
-          const int fzo = (mode == 1) ? F : fz;  // frame of y itself in apply mode
           if (mode == 1) {
-            // write log(K^T u) and finish this pair
             if (P.g_out != nullptr)
+#pragma unroll
               for (int k = 0; k < E; ++k)
-                if (k < ne) P.g_out[g0 + k] = log((double)xn[k]) + (double)fzo * 0.6931471805599453;
+                if (k < ne) P.g_out[g0 + k] = log((double)xn[k]) + (double)F * 0.6931471805599453;
             break;
           }
-          double et;
-          if (!exchange<OpP, C>(L, team, rank, nbar, c_from(r2, fz, C{}), c_from(ab, fz, C{}), (double)ep,
-                                Eeff, tb, XP, cf, cb, et))
+          int dec;
+          if (!exchange<OpP, C>(L, team, rank, epoch, xc, c_from(af, fz, C{}), c_from(ab, fz, C{}), ep, Eeff, tb, XP,
+                                cf, cb, tol_h, tol_l, dec, &eh_last, &el_last, compact))
             goto timed_out;
-          err_last = et;
-          if (!isfinite(et)) { status = FS1_ENUMERIC; break; }
-          if (ell >= P.itr_max || et <= P.tol) break;
+          if (dec == 2) { status = FS1_ENUMERIC; break; }
+          if (ell >= P.itr_max || dec == 1) break;
           // accept v_new
 #pragma unroll
           for (int k = 0; k < E; ++k) xv[k] = xn[k];
@@ -467,53 +618,57 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
         }
         // ---------------- u-half: y = K v, u = a / y
         {
-          int F = 0;
-          if (EXT) F = max(hv + 5, max(c_exp(cf), c_exp(cb)) + 2);
+          const int F = EXT ? max(hv + 5, max(c_exp(cf), c_exp(cb)) + 2) : 0;
           const V sc = EXT ? (V)pow2f(fv - F) : (V)1;
-          V s = (V)c_to(cb, F);
-#pragma unroll
-          for (int k = E - 1; k >= 0; --k)
-            if (k < Eeff) {
-              t[k] = s;
-              s = lam * (s + xv[k] * sc);
-            }
-          V r = (V)c_to(cf, F), r2 = 0, ab = 0, pw = lam, zmax = 0;
+          V r = (V)c_to(cf, F);
 #pragma unroll
           for (int k = 0; k < E; ++k)
             if (k < Eeff) {
               r = lam * r + xv[k] * sc;
-              const V y = r + t[k];
+              xu[k] = r;
+            }
+          V s = (V)c_to(cb, F), af = 0, ab = 0, pw = 1, zmax = 0;
+#pragma unroll
+          for (int k = E - 1; k >= 0; --k)
+            if (k < Eeff) {
+              const V y = xu[k] + s;
               const V m = sm_a[k * kThreads + tid];
               const V z = (k < ne) ? vdiv(m, y) : (V)0;
               xu[k] = z;
               zmax = z > zmax ? z : zmax;
-              r2 = lam * r2 + z;
-              ab = ab + pw * z;
+              af = af + pw * z;
               pw = pw * lam;
+              ab = lam * (ab + z);
+              s = lam * (s + xv[k] * sc);
             }
           const int fz = EXT ? -F : 0;
           fu = fz;
           hu = (EXT && zmax > 0) ? fz + fexp((float)zmax) : kZeroExp;
-          double dummy;
-          if (!exchange<OpP, C>(L, team, rank, nbar, c_from(r2, fz, C{}), c_from(ab, fz, C{}), 0.0, Eeff, tb,
-                                XP, cf, cb, dummy))
+          int dec;
+          if (!exchange<OpP, C>(L, team, rank, epoch, xc, c_from(af, fz, C{}), c_from(ab, fz, C{}), (V)0, Eeff, tb,
+                                XP, cf, cb, 0.f, 0.f, dec, nullptr, nullptr, compact))
             goto timed_out;
         }
         ++ell;
       }
-      if (mode == 1) continue;
+      if (mode == 1) {
+        __syncthreads();
+        continue;
+      }
 
       // ---------------- transport cost: sum_k u_k (A_k + B_k) h, A/B the
       // distance-weighted forward / backward sums of v (O(N) recurrences)
       double wpart = 0.0;
       if (status == FS1_OK) {
         V p = 0, A = 0;
+#pragma unroll
         for (int k = 0; k < E; ++k)
           if (k < Eeff) {
             A = lam * (A + p);
             p = lam * p + xv[k];
           }
         V s = 0, B = 0;
+#pragma unroll
         for (int k = E - 1; k >= 0; --k)
           if (k < Eeff) {
             B = lam * (B + s + xv[k]);
@@ -522,8 +677,10 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
         DT af{c_from(p, fv, C{}), c_from(A, fv, C{})};
         DT ab{c_from(s, fv, C{}), c_from(B, fv, C{})};
         DT dcf, dcb;
-        double dummy;
-        if (!exchange<OpD, C>(L, team, rank, nbar, af, ab, 0.0, Eeff, tb, XD, dcf, dcb, dummy)) goto timed_out;
+        int dec;
+        if (!exchange<OpD, C>(L, team, rank, epoch, xc, af, ab, (V)0, Eeff, tb, XD, dcf, dcb, 0.f, 0.f, dec, nullptr,
+                              nullptr))
+          goto timed_out;
         int F = 0;
         if (EXT) {
           F = max(max(c_exp(dcf.p), c_exp(dcf.a)), max(c_exp(dcb.p), c_exp(dcb.a))) + 2;
@@ -531,24 +688,28 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
         }
         const V sc = EXT ? (V)pow2f(fv - F) : (V)1;
         V ss = (V)c_to(dcb.p, F), BB = (V)c_to(dcb.a, F);
+#pragma unroll
         for (int k = E - 1; k >= 0; --k)
           if (k < Eeff) {
-            t[k] = BB;
+            xn[k] = BB;
             BB = lam * (BB + ss + xv[k] * sc);
             ss = lam * (ss + xv[k] * sc);
           }
         V pp = (V)c_to(dcf.p, F), AA = (V)c_to(dcf.a, F);
+#pragma unroll
         for (int k = 0; k < E; ++k)
           if (k < Eeff) {
             AA = lam * (AA + pp);
             pp = lam * pp + xv[k] * sc;
-            if (k < ne) wpart += ldexp((double)xu[k] * (double)(AA + t[k]), fu + F);
+            if (k < ne) wpart += ldexp((double)xu[k] * (double)(AA + xn[k]), fu + F);
           }
         wpart *= P.h_fast;
-        double wtot;
+        float wh = 0.f, wl = 0.f;
         PT z0 = OpP::zero(), c0, c1;
-        if (!exchange<OpP, C>(L, team, rank, nbar, z0, z0, wpart, Eeff, tb, XP, c0, c1, wtot)) goto timed_out;
-        wpart = wtot;
+        if (!exchange<OpP, C>(L, team, rank, epoch, xc, z0, z0, wpart, Eeff, tb, XP, c0, c1, 0.f, 0.f, dec, &wh,
+                              &wl))
+          goto timed_out;
+        wpart = (double)wh + (double)wl;
       }
       // optional potentials out
       if (P.f_out != nullptr)
@@ -558,12 +719,13 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
         for (int k = 0; k < E; ++k)
           if (k < ne) P.g_out[g0 + k] = log((double)xv[k]) + (double)fv * 0.6931471805599453;
       if (rank == 0 && tid == 0) {
+        const double err_last = (double)eh_last + (double)el_last;
         PairResult R;
         R.w = status == FS1_OK ? wpart : NAN;
         R.err = err_last;
         R.iters = ell;
         R.status = status;
-        if (status == FS1_OK && err_last > P.tol) R.status = FS1_ENOTCONV;
+        if (status == FS1_OK && !(err_last <= P.tol)) R.status = FS1_ENOTCONV;
         R.pad = 0;
         L.results[pid] = R;
       }
@@ -620,6 +782,7 @@ int launch_team_1d(int kind, const TeamLaunch& L, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   const int mode = (kind >> 8) & 0xff;
   kind &= 0xff;
+  if (L.team_size > kMaxTeamCtas) return FS1_EINVAL;
   cudaError_t e;
   switch (kind) {
     case KK_PLAIN_F64: e = launch_kind<double, double, 4>(L, mode, st); break;
