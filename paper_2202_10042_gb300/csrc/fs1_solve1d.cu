@@ -442,6 +442,7 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* sm_a = reinterpret_cast<V*>(smem_raw);
   V* sm_b = sm_a + E * kThreads;
+  V* sm_v = sm_b + E * kThreads;   // the accepted v (for the marginal error; temp in the cost phase)
 
   __shared__ DecayTables<C> tb;
   // separate exchange state per element type (no aliasing between them)
@@ -500,14 +501,17 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
       sm_b[kk * kThreads + tt] = vb;
     }
 
-    // state: u (xu, frame fu), v (xv, frame fv); h* = frame + exponent of max
-    V xu[E], xv[E], xn[E];
+    // state: u in registers (xu, frame fu); v in registers (xn, frame fv)
+    // with a copy of the accepted v in shared memory (sm_v) for the marginal
+    // error; h* = frame + exponent of the largest value
+    V xu[E], xn[E];
     int fu = 0, fv = 0, hu = kZeroExp, hv = kZeroExp;
     {
       const V init = (V)(1.0 / (double)N);
       if (P.f_init != nullptr) {
         // warm start (or the kernel-apply mode): log values -> frame + mantissas
         double fmax = -INFINITY;
+#pragma unroll
         for (int k = 0; k < E; ++k)
           if (k < ne) fmax = fmax > P.f_init[g0 + k] ? fmax : P.f_init[g0 + k];
         if (EXT) fu = isfinite(fmax) ? (int)floor(fmax * 1.4426950408889634) : 0;
@@ -520,21 +524,23 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
       }
       if (P.g_init != nullptr && mode == 0) {
         double gmax = -INFINITY;
+#pragma unroll
         for (int k = 0; k < E; ++k)
           if (k < ne) gmax = gmax > P.g_init[g0 + k] ? gmax : P.g_init[g0 + k];
         if (EXT) fv = isfinite(gmax) ? (int)floor(gmax * 1.4426950408889634) : 0;
 #pragma unroll
         for (int k = 0; k < E; ++k)
-          xv[k] = (k < ne) ? (V)exp2(P.g_init[g0 + k] * 1.4426950408889634 - (double)fv) : (V)0;
+          xn[k] = (k < ne) ? (V)exp2(P.g_init[g0 + k] * 1.4426950408889634 - (double)fv) : (V)0;
       } else {
 #pragma unroll
-        for (int k = 0; k < E; ++k) xv[k] = (k < ne) ? init : (V)0;
+        for (int k = 0; k < E; ++k) xn[k] = (k < ne) ? init : (V)0;
       }
       V mu = 0, mv = 0;
 #pragma unroll
       for (int k = 0; k < E; ++k) {
         mu = xu[k] > mu ? xu[k] : mu;
-        mv = xv[k] > mv ? xv[k] : mv;
+        mv = xn[k] > mv ? xn[k] : mv;
+        sm_v[k * kThreads + tid] = xn[k];
       }
       if (EXT) {
         hu = mu > 0 ? fu + fexp((float)mu) : kZeroExp;
@@ -588,7 +594,7 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
               const V m = sm_b[k * kThreads + tid];
               V z = (k < ne) ? vdiv(m, y) : (V)0;
               if (mode == 1) z = (k < ne) ? y : (V)0;   // kernel-apply mode: keep K^T u
-              if (k < ne) ep += fabs(xv[k] * y * sc2 - m);
+              if (k < ne) ep += fabs(sm_v[k * kThreads + tid] * y * sc2 - m);
               xn[k] = z;
               zmax = z > zmax ? z : zmax;
               af = af + pw * z;
@@ -608,11 +614,16 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
           if (!exchange<OpP, C>(L, team, rank, epoch, xc, c_from(af, fz, C{}), c_from(ab, fz, C{}), ep, Eeff, tb, XP,
                                 cf, cb, tol_h, tol_l, dec, &eh_last, &el_last, compact))
             goto timed_out;
-          if (dec == 2) { status = FS1_ENUMERIC; break; }
-          if (ell >= P.itr_max || dec == 1) break;
+          if (dec != 0 || ell >= P.itr_max) {
+            if (dec == 2) status = FS1_ENUMERIC;
+            // the returned iterate keeps the accepted v
+#pragma unroll
+            for (int k = 0; k < E; ++k) xn[k] = sm_v[k * kThreads + tid];
+            break;
+          }
           // accept v_new
 #pragma unroll
-          for (int k = 0; k < E; ++k) xv[k] = xn[k];
+          for (int k = 0; k < E; ++k) sm_v[k * kThreads + tid] = xn[k];
           fv = fz;
           hv = (EXT && zmax > 0) ? fz + fexp((float)zmax) : kZeroExp;
         }
@@ -624,7 +635,7 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
 #pragma unroll
           for (int k = 0; k < E; ++k)
             if (k < Eeff) {
-              r = lam * r + xv[k] * sc;
+              r = lam * r + xn[k] * sc;
               xu[k] = r;
             }
           V s = (V)c_to(cb, F), af = 0, ab = 0, pw = 1, zmax = 0;
@@ -639,7 +650,7 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
               af = af + pw * z;
               pw = pw * lam;
               ab = lam * (ab + z);
-              s = lam * (s + xv[k] * sc);
+              s = lam * (s + xn[k] * sc);
             }
           const int fz = EXT ? -F : 0;
           fu = fz;
@@ -665,14 +676,14 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
         for (int k = 0; k < E; ++k)
           if (k < Eeff) {
             A = lam * (A + p);
-            p = lam * p + xv[k];
+            p = lam * p + xn[k];
           }
         V s = 0, B = 0;
 #pragma unroll
         for (int k = E - 1; k >= 0; --k)
           if (k < Eeff) {
-            B = lam * (B + s + xv[k]);
-            s = lam * (s + xv[k]);
+            B = lam * (B + s + xn[k]);
+            s = lam * (s + xn[k]);
           }
         DT af{c_from(p, fv, C{}), c_from(A, fv, C{})};
         DT ab{c_from(s, fv, C{}), c_from(B, fv, C{})};
@@ -691,17 +702,17 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
 #pragma unroll
         for (int k = E - 1; k >= 0; --k)
           if (k < Eeff) {
-            xn[k] = BB;
-            BB = lam * (BB + ss + xv[k] * sc);
-            ss = lam * (ss + xv[k] * sc);
+            sm_v[k * kThreads + tid] = BB;   // temp: backward distance sums
+            BB = lam * (BB + ss + xn[k] * sc);
+            ss = lam * (ss + xn[k] * sc);
           }
         V pp = (V)c_to(dcf.p, F), AA = (V)c_to(dcf.a, F);
 #pragma unroll
         for (int k = 0; k < E; ++k)
           if (k < Eeff) {
             AA = lam * (AA + pp);
-            pp = lam * pp + xv[k] * sc;
-            if (k < ne) wpart += ldexp((double)xu[k] * (double)(AA + xn[k]), fu + F);
+            pp = lam * pp + xn[k] * sc;
+            if (k < ne) wpart += ldexp((double)xu[k] * (double)(AA + sm_v[k * kThreads + tid]), fu + F);
           }
         wpart *= P.h_fast;
         float wh = 0.f, wl = 0.f;
@@ -713,11 +724,13 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
       }
       // optional potentials out
       if (P.f_out != nullptr)
+#pragma unroll
         for (int k = 0; k < E; ++k)
           if (k < ne) P.f_out[g0 + k] = log((double)xu[k]) + (double)fu * 0.6931471805599453;
       if (P.g_out != nullptr)
+#pragma unroll
         for (int k = 0; k < E; ++k)
-          if (k < ne) P.g_out[g0 + k] = log((double)xv[k]) + (double)fv * 0.6931471805599453;
+          if (k < ne) P.g_out[g0 + k] = log((double)xn[k]) + (double)fv * 0.6931471805599453;
       if (rank == 0 && tid == 0) {
         const double err_last = (double)eh_last + (double)el_last;
         PairResult R;
@@ -746,11 +759,11 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
 // ---------------------------------------------------------------------------
 int team_threads() { return kThreads; }
 
-int team_elems_max(int kind) { return kind == KK_PLAIN_F64 ? 4 : 16; }
+int team_elems_max(int kind) { return kind == KK_PLAIN_F64 ? 8 : 32; }
 
 size_t team_smem_bytes(int kind) {
   const size_t vs = kind == KK_PLAIN_F64 ? sizeof(double) : sizeof(float);
-  return 2 * vs * (size_t)team_elems_max(kind) * kThreads;
+  return 3 * vs * (size_t)team_elems_max(kind) * kThreads;
 }
 
 int elems_cap_for(int kind, double c) {
@@ -765,7 +778,7 @@ int elems_cap_for(int kind, double c) {
 template <class V, class C, int E>
 static cudaError_t launch_kind(const TeamLaunch& L, int mode, cudaStream_t st) {
   auto kfn = fs1_team_kernel<V, C, E>;
-  const size_t smem = 2 * sizeof(V) * (size_t)E * kThreads;
+  const size_t smem = 3 * sizeof(V) * (size_t)E * kThreads;
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = L.num_teams * L.team_size;
@@ -785,9 +798,9 @@ int launch_team_1d(int kind, const TeamLaunch& L, void* stream) {
   if (L.team_size > kMaxTeamCtas) return FS1_EINVAL;
   cudaError_t e;
   switch (kind) {
-    case KK_PLAIN_F64: e = launch_kind<double, double, 4>(L, mode, st); break;
-    case KK_PLAIN_F32: e = launch_kind<float, float, 16>(L, mode, st); break;
-    case KK_LOG_F32: e = launch_kind<float, XF, 16>(L, mode, st); break;
+    case KK_PLAIN_F64: e = launch_kind<double, double, 8>(L, mode, st); break;
+    case KK_PLAIN_F32: e = launch_kind<float, float, 32>(L, mode, st); break;
+    case KK_LOG_F32: e = launch_kind<float, XF, 32>(L, mode, st); break;
     default: return FS1_EINVAL;
   }
   if (e != cudaSuccess) {
@@ -800,7 +813,7 @@ int launch_team_1d(int kind, const TeamLaunch& L, void* stream) {
 template <class V, class C, int E>
 static int coresident() {
   auto kfn = fs1_team_kernel<V, C, E>;
-  const size_t smem = 2 * sizeof(V) * (size_t)E * kThreads;
+  const size_t smem = 3 * sizeof(V) * (size_t)E * kThreads;
   cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0, dev = 0, sms = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, kThreads, smem) != cudaSuccess) return 0;
@@ -811,9 +824,9 @@ static int coresident() {
 
 int max_coresident_ctas(int kind) {
   switch (kind & 0xff) {
-    case KK_PLAIN_F64: return coresident<double, double, 4>();
-    case KK_PLAIN_F32: return coresident<float, float, 16>();
-    case KK_LOG_F32: return coresident<float, XF, 16>();
+    case KK_PLAIN_F64: return coresident<double, double, 8>();
+    case KK_PLAIN_F32: return coresident<float, float, 32>();
+    case KK_LOG_F32: return coresident<float, XF, 32>();
   }
   return 0;
 }
