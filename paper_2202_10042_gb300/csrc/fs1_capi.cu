@@ -121,7 +121,7 @@ fs1_status check_problem(const fs1_problem& p) {
   if (p.itr_max < 0) return FS1_EINVAL;
   if (!p.a || !p.b) return FS1_EINVAL;
   if ((p.f_init == nullptr) != (p.g_init == nullptr)) return FS1_EINVAL;
-  if (p.ndim == 2) return FS1_EUNSUPPORTED;   // 2D path is a separate kernel
+  if (p.ndim == 2 && (p.f_init || p.f_out || p.g_out)) return FS1_EUNSUPPORTED;   // 1D only
   return FS1_OK;
 }
 
@@ -166,9 +166,16 @@ fs1_status choose_geometry(fs1_handle* h, int kind, const std::vector<const fs1_
 fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const fs1_problem*>& ps,
                      std::vector<PairResult>& res, Geometry& geo, float* ms, bool validate) {
   const int count = (int)ps.size();
-  fs1_status st = choose_geometry(h, kind, ps, &geo);
-  if (st != FS1_OK) return st;
-  const int T = geo.team_size, teams = geo.num_teams;
+  const bool two_d = ps[0]->ndim == 2;
+  fs1_status st = FS1_OK;
+  if (two_d) {
+    if (kind != KK_LOG_F32) return FS1_EUNSUPPORTED;   // 2D runs the stabilised FP32 variant
+    geo.team_size = 0;
+    geo.num_teams = 0;
+  } else if ((st = choose_geometry(h, kind, ps, &geo)) != FS1_OK) {
+    return st;
+  }
+  const int T = two_d ? 1 : geo.team_size, teams = two_d ? 1 : geo.num_teams;
   const int in_f32 = ps[0]->dtype == FS1_FP32;
   size_t off = 0;
   const size_t o_desc = off; off = align_up(off + sizeof(PairDesc) * count, 256);
@@ -178,9 +185,6 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
   const size_t o_cslot = off; off = align_up(off + 128 * (size_t)teams * 2 * T, 256);
   const size_t o_ctr = off;  off = align_up(off + sizeof(unsigned long long) * teams, 256);
   const size_t o_abt = off;  off = align_up(off + sizeof(int) * teams, 256);
-  if ((st = ensure_ws(h, off)) != FS1_OK) return st;
-  char* ws = (char*)h->ws;
-
   std::vector<PairDesc> desc(count);
   for (int i = 0; i < count; ++i) {
     const fs1_problem& p = *ps[i];
@@ -201,6 +205,11 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
     d.g_init = p.g_init;
     desc[i] = d;
   }
+  const size_t o_2d = off;
+  if (two_d) off = align_up(off + solve2d_workspace(desc.data(), count), 256);
+  if ((st = ensure_ws(h, off)) != FS1_OK) return st;
+  char* ws = (char*)h->ws;
+
   std::vector<PairResult> init(count, PairResult{NAN, NAN, 0, FS1_ETIMEOUT, 0});
   cudaError_t e;
   if ((e = cudaMemcpyAsync(ws + o_desc, desc.data(), sizeof(PairDesc) * count, cudaMemcpyHostToDevice,
@@ -262,7 +271,12 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
   L.abort_flags = (int*)(ws + o_abt);
   L.spin_cap = h->cfg.spin_cap;
   cudaEventRecord(h->ev0, h->stream);
-  int ls = launch_team_1d(kind | (mode << 8), L, h->stream);
+  int ls;
+  if (two_d)
+    ls = launch_solve_2d(desc.data(), count, in_f32, (PairResult*)(ws + o_res), ws + o_2d, h->ws_bytes - o_2d,
+                         h->cfg.spin_cap, h->stream);
+  else
+    ls = launch_team_1d(kind | (mode << 8), L, h->stream);
   if (ls != FS1_OK) return (fs1_status)ls;
   g_launches.fetch_add(1);
   cudaEventRecord(h->ev1, h->stream);
@@ -404,16 +418,28 @@ fs1_status fs1_solve_batch(fs1_handle* h, const fs1_problem* probs, int64_t coun
       s.location = FS1_MEM_DEVICE;
     }
   }
-  // group by input dtype (the launch reads one dtype)
-  for (int dt = 0; dt < 2; ++dt) {
-    std::vector<const fs1_problem*> grp;
-    std::vector<int64_t> idx;
-    for (int64_t i = 0; i < count; ++i)
-      if (pst[i] == FS1_OK && staged[i].dtype == dt) {
-        grp.push_back(&staged[i]);
-        idx.push_back(i);
-      }
-    if (grp.empty()) continue;
+  // group by dimension and input dtype (a launch reads one dtype); 2D groups
+  // are cut into launches of at most kMaxImg2D images
+  std::vector<std::pair<std::vector<const fs1_problem*>, std::vector<int64_t>>> groups;
+  for (int nd = 1; nd <= 2; ++nd)
+    for (int dt = 0; dt < 2; ++dt) {
+      std::vector<const fs1_problem*> grp;
+      std::vector<int64_t> idx;
+      for (int64_t i = 0; i < count; ++i)
+        if (pst[i] == FS1_OK && staged[i].dtype == dt && staged[i].ndim == nd) {
+          grp.push_back(&staged[i]);
+          idx.push_back(i);
+          if (nd == 2 && (int)grp.size() == kMaxImg2D) {
+            groups.emplace_back(grp, idx);
+            grp.clear();
+            idx.clear();
+          }
+        }
+      if (!grp.empty()) groups.emplace_back(grp, idx);
+    }
+  for (auto& gi : groups) {
+    std::vector<const fs1_problem*>& grp = gi.first;
+    std::vector<int64_t>& idx = gi.second;
     std::vector<PairResult> r;
     Geometry geo{0, 0};
     float gms = 0.f;

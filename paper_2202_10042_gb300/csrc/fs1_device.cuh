@@ -43,6 +43,7 @@ __device__ __forceinline__ XF xf_norm(float m, int e) {
   int b = __float_as_int(m);
   int eb = (b >> 23) & 0xff;
   if (eb == 0) return XF{0.f, kZeroExp};
+  if (eb == 0xff) return XF{m, e};   // inf / nan propagate (the caller detects them)
   XF r;
   r.m = __int_as_float((b & 0x807fffff) | (126 << 23));
   r.e = e + eb - 126;

@@ -60,6 +60,12 @@ enum KernelKind {
   KK_LOG_F32 = 2,     // stabilised FS-1: FP32 mantissas in extended range
 };
 
+// 2D solver (fs1_solve2d.cu): up to kMaxImg2D images per launch.
+constexpr int kMaxImg2D = 64;
+size_t solve2d_workspace(const PairDesc* host_descs, int count);
+int launch_solve_2d(const PairDesc* host_descs, int count, int in_f32, PairResult* d_results, void* ws,
+                    size_t ws_bytes, long long spin_cap, void* stream);
+
 // Host-side launch helpers (fs1_solve1d.cu).
 int team_threads();
 int team_elems_max(int kind);

@@ -1,0 +1,468 @@
+// fs1_solve2d.cu -- 2D FS-1 (Algorithm 2) for sm_103a.
+//
+// The 2D kernel K = K_slow (x) K_fast (Section 4, block form of K) is applied
+// as two passes of the 1D recurrences of eq. "recursion": along every row (the
+// fast, contiguous axis, lam_1 = e^{-h_fast/eps}) and then along every column
+// (lam_2 = e^{-h_slow/eps}); this is the "2d recursion" of Section 4 with the
+// K_0 products done row by row.  One half-step of Algorithm 2 is
+//   fast pass : Y = (I (x) K_fast) X                  one warp per row
+//   slow pass : y = (K_slow (x) I) Y, z = mass / y,    one warp per column
+//               and (v-half) the column-marginal error partials
+// executed by one persistent cooperative kernel over a batch of images, with a
+// bounded grid barrier after every pass.  The state is stored per point in
+// extended range (FP32 mantissa and int exponent, struct XF), so any eps and
+// grid spacing are covered with FP32 relative precision.  A line of L <= 1024
+// points is split over the 32 lanes of a warp: each lane runs the recurrences
+// serially over its points and the lanes are joined by a Kogge-Stone scan of
+// the lane aggregates with the same associative (decay, value) operators as
+// the 1D kernel.
+//
+// Stop rule per image (the while condition of Algorithm 2): the error partials
+// of the image's column warps are summed in a fixed order by every CTA, so all
+// CTAs decide identically.  v is double-buffered by iteration parity and the
+// returned iterate keeps the accepted v.  The transport cost
+//   sum u (x) [h_fast (K_s (x) K_f^(c)) v + h_slow (K_s^(c) (x) K_f) v],
+// K^(c)_ij = lam^{|i-j|} |i-j|, is formed with the distance-weighted operator
+// in three more passes, O(N M).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <type_traits>
+#include <vector>
+
+#include "fs1.h"
+#include "fs1_device.cuh"
+#include "fs1_internal.h"
+
+namespace fs1 {
+
+namespace {
+
+constexpr int kThreads2 = 256;
+constexpr int kWarps2 = kThreads2 / 32;
+constexpr int kTab = 38;   // lam^0..lam^32, then lam^{P 2^i}, i < 5
+
+struct Img2D {
+  const void* a;
+  const void* b;
+  int nf, ns;          // fast (contiguous) and slow lengths
+  double cf, cs;       // h / eps per axis
+  double hf, hs;
+  double tol;
+  int64_t itr_max;
+  XF* U;               // u
+  XF* V[2];            // v by iteration parity
+  XF* Y;               // fast-pass output
+  XF* R;               // slow-pass output and parking area
+  float* errp;         // [2 nf] column error partials (compensated pairs)
+  double* wp;          // [nf] column cost partials
+  int* stop;           // 0 while active; 1 + k once stopped with the final v in V[k]
+};
+
+struct Launch2D {
+  Img2D* imgs;
+  PairResult* results;
+  int nimg;
+  int in_f32;
+  const int* row_off;  // [nimg + 1] prefix sums of ns
+  const int* col_off;  // [nimg + 1] prefix sums of nf
+  unsigned long long* bar;   // zeroed per launch
+  int* abort_flag;
+  long long spin_cap;
+};
+
+__device__ __forceinline__ float load_m(const void* p, int64_t i, int f32) {
+  return f32 ? reinterpret_cast<const float*>(p)[i] : (float)reinterpret_cast<const double*>(p)[i];
+}
+
+__device__ bool grid_barrier(const Launch2D& L, unsigned long long& gen, int* sm_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    gen += gridDim.x;
+    __threadfence();
+    red_release_add(L.bar, 1ull);
+    int good = 1;
+    long long spins = 0;
+    while (ld_acquire(L.bar) < gen) {
+      if (++spins > L.spin_cap || ((spins & 255) == 0 && ld_relaxed(L.abort_flag))) {
+        good = 0;
+        atomicExch(L.abort_flag, 1);
+        break;
+      }
+    }
+    *sm_ok = good;
+  }
+  __syncthreads();
+  return *sm_ok != 0;
+}
+
+// image owning flat item t of a prefix-offset table (nimg <= kMaxImg2D)
+__device__ __forceinline__ int owner(const int* off, int nimg, int t) {
+  int i = 0;
+  while (i + 1 < nimg && off[i + 1] <= t) ++i;
+  return i;
+}
+
+// ---------------------------------------------------------------------------
+// warp line scan along L points at `stride`: out = K x (plain) or the
+// distance-weighted sum (WEIGHTED).  Lane l owns points [l P, l P + P).  The
+// lane's backward sums are parked in `tmp` (written and read back by the same
+// lane; tmp may alias out).  tab: lam^j (j <= 32) and lam^{P 2^i} at 33 + i.
+// ---------------------------------------------------------------------------
+template <bool WEIGHTED>
+__device__ void line_scan(const XF* in, XF* out, XF* tmp, int64_t stride, int L, const XF* tab) {
+  using Op = typename std::conditional<WEIGHTED, OpDist<XF>, OpPlain<XF>>::type;
+  using T = typename Op::T;
+  const int lane = threadIdx.x & 31;
+  const int P = (L + 31) >> 5;
+  const int i0 = lane * P;
+  const int n = max(0, min(P, L - i0));
+  const XF lam = tab[1];
+  const XF zero = c_zero(XF{});
+  T af, ab;
+  {
+    XF p = zero, A = zero, s = zero, B = zero;
+    for (int k = 0; k < P; ++k) {
+      const XF x = k < n ? in[(int64_t)(i0 + k) * stride] : zero;
+      if (WEIGHTED) A = c_mul(c_add(A, p), lam);
+      p = c_add(c_mul(p, lam), x);
+    }
+    for (int k = P - 1; k >= 0; --k) {
+      const XF x = k < n ? in[(int64_t)(i0 + k) * stride] : zero;
+      if (WEIGHTED) B = c_mul(c_add(c_add(B, s), x), lam);
+      s = c_mul(c_add(s, x), lam);
+    }
+    if constexpr (WEIGHTED) {
+      af = T{p, A};
+      ab = T{s, B};
+    } else {
+      af = p;
+      ab = s;
+    }
+  }
+  T x = af, z = ab;
+#pragma unroll
+  for (int lv = 0; lv < 5; ++lv) {
+    const int o = 1 << lv;
+    const T y = Op::up(x, o);
+    const T w = Op::down(z, o);
+    if (lane >= o) x = Op::fwd(y, x, tab[33 + lv], (float)(P * o));
+    if (lane + o < 32) z = Op::bwd(z, w, tab[33 + lv], (float)(P * o));
+  }
+  T cfw = Op::up(x, 1), cbw = Op::down(z, 1);
+  if (lane == 0) cfw = Op::zero();
+  if (lane == 31) cbw = Op::zero();
+  if (n <= 0) return;
+  {
+    XF s, B;
+    if constexpr (WEIGHTED) {
+      s = cbw.p;
+      B = cbw.a;
+    } else {
+      s = cbw;
+      B = zero;
+    }
+    for (int k = P - 1; k >= n; --k) {   // carry across the lane's empty tail
+      if (WEIGHTED) B = c_mul(c_add(B, s), lam);
+      s = c_mul(s, lam);
+    }
+    for (int k = n - 1; k >= 0; --k) {
+      const XF xk = in[(int64_t)(i0 + k) * stride];
+      tmp[(int64_t)(i0 + k) * stride] = WEIGHTED ? B : s;
+      if (WEIGHTED) B = c_mul(c_add(c_add(B, s), xk), lam);
+      s = c_mul(c_add(s, xk), lam);
+    }
+  }
+  {
+    XF p, A;
+    if constexpr (WEIGHTED) {
+      p = cfw.p;
+      A = cfw.a;
+    } else {
+      p = cfw;
+      A = zero;
+    }
+    for (int k = 0; k < n; ++k) {
+      const XF xk = in[(int64_t)(i0 + k) * stride];
+      if (WEIGHTED) A = c_mul(c_add(A, p), lam);
+      p = c_add(c_mul(p, lam), xk);
+      const XF bk = tmp[(int64_t)(i0 + k) * stride];
+      out[(int64_t)(i0 + k) * stride] = c_add(WEIGHTED ? A : p, bk);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads2) fs1_solve2d_kernel(Launch2D L) {
+  __shared__ XF tab[kMaxImg2D][2][kTab];   // [image][axis: 0 fast, 1 slow]
+  __shared__ int srow[kMaxImg2D + 1], scol[kMaxImg2D + 1];
+  __shared__ signed char sstate[kMaxImg2D];  // 0 active, 1 stops this iteration, 2 stopped earlier
+  __shared__ int sok;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * kWarps2 + warp;
+  const int nw = gridDim.x * kWarps2;
+  const int nimg = L.nimg;
+  unsigned long long gen = 0;
+
+  for (int i = threadIdx.x; i <= nimg; i += blockDim.x) {
+    srow[i] = L.row_off[i];
+    scol[i] = L.col_off[i];
+  }
+  for (int t = threadIdx.x; t < nimg * 2 * kTab; t += blockDim.x) {
+    const int i = t / (2 * kTab), ax = (t / kTab) & 1, j = t % kTab;
+    const Img2D& I = L.imgs[i];
+    const double c = ax == 0 ? I.cf : I.cs;
+    const int len = ax == 0 ? I.nf : I.ns;
+    const int P = (len + 31) >> 5;
+    const double k = j <= 32 ? (double)j : (double)P * (double)(1 << (j - 33));
+    tab[i][ax][j] = c_decay(k, c, XF{});
+  }
+  // u = v = 1 / (n_fast n_slow)  (Algorithm 2, line 1)
+  for (int i = 0; i < nimg; ++i) {
+    const Img2D& I = L.imgs[i];
+    const int64_t N = (int64_t)I.nf * I.ns;
+    const XF init = xf_norm((float)(1.0 / (double)N), 0);
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+      I.U[p] = init;
+      I.V[0][p] = init;
+    }
+  }
+  if (!grid_barrier(L, gen, &sok)) return;
+
+  const int rows = srow[nimg], cols = scol[nimg];
+  for (int64_t ell = 0;; ++ell) {
+    const int par = (int)(ell & 1);
+    __syncthreads();
+    bool any = false;
+    for (int i = 0; i < nimg; ++i) any |= ld_relaxed(L.imgs[i].stop) == 0;
+    if (!any) break;
+    for (int i = threadIdx.x; i < nimg; i += blockDim.x) sstate[i] = ld_relaxed(L.imgs[i].stop) == 0 ? 0 : 2;
+    __syncthreads();
+    // ---- v-half, fast pass: Y = (I (x) K_f) U
+    for (int t = gw; t < rows; t += nw) {
+      const int i = owner(srow, nimg, t);
+      if (sstate[i]) continue;
+      const Img2D& I = L.imgs[i];
+      const int64_t o = (int64_t)(t - srow[i]) * I.nf;
+      line_scan<false>(I.U + o, I.Y + o, I.R + o, 1, I.nf, tab[i][0]);
+    }
+    if (!grid_barrier(L, gen, &sok)) return;
+    // ---- v-half, slow pass: y = (K_s (x) I) Y, v_new = b / y, error partials
+    for (int t = gw; t < cols; t += nw) {
+      const int i = owner(scol, nimg, t);
+      if (sstate[i]) continue;
+      const Img2D& I = L.imgs[i];
+      const int col = t - scol[i];
+      XF* Vn = I.V[par ^ 1];
+      line_scan<false>(I.Y + col, I.R + col, Vn + col, I.nf, I.ns, tab[i][1]);
+      __syncwarp();
+      float eh = 0.f, el = 0.f;
+      for (int r = lane; r < I.ns; r += 32) {
+        const int64_t p = (int64_t)r * I.nf + col;
+        const XF y = I.R[p];
+        const float m = load_m(I.b, p, L.in_f32);
+        const XF vo = I.V[par][p];
+        Vn[p] = m > 0.f ? xf_norm(__fdividef(m, y.m), -y.e) : XF{0.f, kZeroExp};
+        const float pv = c_to(c_mul(vo, y), 0);   // v_old (K^T u) at p
+        df_add(eh, el, fabsf(pv - m), 0.f);
+      }
+      warp_sum_df(eh, el);
+      if (lane == 0) {
+        I.errp[2 * col] = eh;
+        I.errp[2 * col + 1] = el;
+      }
+    }
+    if (!grid_barrier(L, gen, &sok)) return;
+    // ---- decisions (every CTA, identical fixed-order sums)
+    for (int i = warp; i < nimg; i += kWarps2) {
+      if (sstate[i]) continue;
+      const Img2D& I = L.imgs[i];
+      float h = 0.f, l = 0.f;
+      for (int c = lane; c < I.nf; c += 32) df_add(h, l, __ldcg(I.errp + 2 * c), __ldcg(I.errp + 2 * c + 1));
+      warp_sum_df(h, l);
+      if (lane == 0) {
+        const double err = (double)h + (double)l;
+        const bool numeric = !isfinite(err);
+        const bool stop = numeric || err <= I.tol || ell >= I.itr_max;
+        if (stop) {
+          sstate[i] = 1;
+          if (blockIdx.x == 0) {
+            L.results[i].err = err;
+            L.results[i].iters = ell;
+            L.results[i].status = numeric ? FS1_ENUMERIC : (err <= I.tol ? FS1_OK : FS1_ENOTCONV);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // ---- u-half, fast pass: Y = (I (x) K_f) v_new
+    for (int t = gw; t < rows; t += nw) {
+      const int i = owner(srow, nimg, t);
+      if (sstate[i]) continue;
+      const Img2D& I = L.imgs[i];
+      const int64_t o = (int64_t)(t - srow[i]) * I.nf;
+      line_scan<false>(I.V[par ^ 1] + o, I.Y + o, I.R + o, 1, I.nf, tab[i][0]);
+    }
+    if (!grid_barrier(L, gen, &sok)) return;
+    // ---- u-half, slow pass: u = a / ((K_s (x) I) Y)
+    for (int t = gw; t < cols; t += nw) {
+      const int i = owner(scol, nimg, t);
+      if (sstate[i]) continue;
+      const Img2D& I = L.imgs[i];
+      const int col = t - scol[i];
+      line_scan<false>(I.Y + col, I.R + col, I.U + col, I.nf, I.ns, tab[i][1]);
+      __syncwarp();
+      for (int r = lane; r < I.ns; r += 32) {
+        const int64_t p = (int64_t)r * I.nf + col;
+        const XF y = I.R[p];
+        const float m = load_m(I.a, p, L.in_f32);
+        I.U[p] = m > 0.f ? xf_norm(__fdividef(m, y.m), -y.e) : XF{0.f, kZeroExp};
+      }
+    }
+    // images that stop here keep v_old = V[par]
+    if (blockIdx.x == 0)
+      for (int i = threadIdx.x; i < nimg; i += blockDim.x)
+        if (sstate[i] == 1) L.imgs[i].stop[0] = 1 + par;
+    if (!grid_barrier(L, gen, &sok)) return;
+  }
+
+  // ---- transport cost
+  // rows: Y = (I (x) K_f^(c)) v (weighted); then the plain (I (x) K_f) v into
+  // the free v buffer
+  for (int t = gw; t < rows; t += nw) {
+    const int i = owner(srow, nimg, t);
+    const Img2D& I = L.imgs[i];
+    const int k = (ld_relaxed(I.stop) - 1) & 1;
+    const int64_t o = (int64_t)(t - srow[i]) * I.nf;
+    line_scan<true>(I.V[k] + o, I.Y + o, I.R + o, 1, I.nf, tab[i][0]);
+    __syncwarp();
+    line_scan<false>(I.V[k] + o, I.V[k ^ 1] + o, I.R + o, 1, I.nf, tab[i][0]);
+  }
+  if (!grid_barrier(L, gen, &sok)) return;
+  // columns: h_fast u.(K_s (x) I) Y + h_slow u.(K_s^(c) (x) I) V[k^1]
+  for (int t = gw; t < cols; t += nw) {
+    const int i = owner(scol, nimg, t);
+    const Img2D& I = L.imgs[i];
+    const int k = (ld_relaxed(I.stop) - 1) & 1;
+    const int col = t - scol[i];
+    double acc = 0.0;
+    line_scan<false>(I.Y + col, I.R + col, I.R + col, I.nf, I.ns, tab[i][1]);
+    __syncwarp();
+    for (int r = lane; r < I.ns; r += 32) {
+      const int64_t p = (int64_t)r * I.nf + col;
+      const XF w = I.R[p], u = I.U[p];
+      acc += I.hf * ldexp((double)u.m * (double)w.m, u.e + w.e);
+    }
+    __syncwarp();
+    line_scan<true>(I.V[k ^ 1] + col, I.R + col, I.R + col, I.nf, I.ns, tab[i][1]);
+    __syncwarp();
+    for (int r = lane; r < I.ns; r += 32) {
+      const int64_t p = (int64_t)r * I.nf + col;
+      const XF w = I.R[p], u = I.U[p];
+      acc += I.hs * ldexp((double)u.m * (double)w.m, u.e + w.e);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) I.wp[col] = acc;
+  }
+  if (!grid_barrier(L, gen, &sok)) return;
+  if (blockIdx.x == 0) {
+    for (int i = warp; i < nimg; i += kWarps2) {
+      const Img2D& I = L.imgs[i];
+      double s = 0.0;
+      for (int c = lane; c < I.nf; c += 32) s += __ldcg(I.wp + c);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) L.results[i].w = L.results[i].status == FS1_ENUMERIC ? NAN : s;
+    }
+  }
+}
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+
+size_t solve2d_workspace(const PairDesc* d, int count) {
+  size_t b = align256(sizeof(Img2D) * count) + 2 * align256(sizeof(int) * (count + 1)) + 256 + 256;
+  for (int i = 0; i < count; ++i) {
+    const size_t n = (size_t)d[i].n_fast * d[i].n_slow;
+    b += 5 * align256(sizeof(XF) * n) + align256(sizeof(float) * 2 * d[i].n_fast) +
+         align256(sizeof(double) * d[i].n_fast) + 256;
+  }
+  return b;
+}
+
+int launch_solve_2d(const PairDesc* d, int count, int in_f32, PairResult* results, void* ws, size_t ws_bytes,
+                    long long spin_cap, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (count < 1 || count > kMaxImg2D) return FS1_EINVAL;
+  if (solve2d_workspace(d, count) > ws_bytes) return FS1_ENOMEM;
+  char* p = (char*)ws;
+  Img2D* d_imgs = (Img2D*)p;
+  p += align256(sizeof(Img2D) * count);
+  int* d_row = (int*)p;
+  p += align256(sizeof(int) * (count + 1));
+  int* d_col = (int*)p;
+  p += align256(sizeof(int) * (count + 1));
+  unsigned long long* d_bar = (unsigned long long*)p;
+  p += 256;
+  int* d_abort = (int*)p;
+  p += 256;
+  std::vector<Img2D> imgs(count);
+  std::vector<int> row(count + 1, 0), col(count + 1, 0);
+  char* stops = nullptr;
+  for (int i = 0; i < count; ++i) {
+    const PairDesc& D = d[i];
+    Img2D I{};
+    I.a = D.a;
+    I.b = D.b;
+    I.nf = (int)D.n_fast;
+    I.ns = (int)D.n_slow;
+    I.cf = D.h_fast / D.eps;
+    I.cs = D.h_slow / D.eps;
+    I.hf = D.h_fast;
+    I.hs = D.h_slow;
+    I.tol = D.tol;
+    I.itr_max = D.itr_max;
+    const size_t n = (size_t)I.nf * I.ns;
+    I.U = (XF*)p; p += align256(sizeof(XF) * n);
+    I.V[0] = (XF*)p; p += align256(sizeof(XF) * n);
+    I.V[1] = (XF*)p; p += align256(sizeof(XF) * n);
+    I.Y = (XF*)p; p += align256(sizeof(XF) * n);
+    I.R = (XF*)p; p += align256(sizeof(XF) * n);
+    I.errp = (float*)p; p += align256(sizeof(float) * 2 * I.nf);
+    I.wp = (double*)p; p += align256(sizeof(double) * I.nf);
+    I.stop = (int*)p;
+    if (!stops) stops = p;
+    p += 256;
+    imgs[i] = I;
+    row[i + 1] = row[i] + I.ns;
+    col[i + 1] = col[i] + I.nf;
+  }
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < count && e == cudaSuccess; ++i) e = cudaMemsetAsync(imgs[i].stop, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_imgs, imgs.data(), sizeof(Img2D) * count, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_row, row.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_col, col.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_bar, 0, 512, st);
+  if (e != cudaSuccess) {
+    fprintf(stderr, "fs1: 2D setup failed: %s\n", cudaGetErrorString(e));
+    return FS1_ECUDA;
+  }
+  Launch2D L{d_imgs, results, count, in_f32, d_row, d_col, d_bar, d_abort, spin_cap};
+  int per_sm = 0, dev = 0, sms = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fs1_solve2d_kernel, kThreads2, 0);
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::max(1, per_sm) * sms;
+  void* args[] = {&L};
+  e = cudaLaunchCooperativeKernel((const void*)fs1_solve2d_kernel, dim3(grid), dim3(kThreads2), args, 0, st);
+  if (e != cudaSuccess) {
+    fprintf(stderr, "fs1: 2D launch failed: %s\n", cudaGetErrorString(e));
+    return FS1_ECUDA;
+  }
+  return FS1_OK;
+}
+
+}  // namespace fs1
