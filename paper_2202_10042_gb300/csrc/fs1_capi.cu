@@ -162,6 +162,135 @@ fs1_status choose_geometry(fs1_handle* h, int kind, const std::vector<const fs1_
   return FS1_OK;
 }
 
+// Heterogeneous team plan for a batch of 1D problems: problems are put in
+// classes by the fewest CTAs that hold them on chip (rounded up to a power of
+// two); CTAs are split over the classes in proportion to their estimated work
+// (N * itr_max); every class is a queue of its problems in decreasing cost
+// (longest-processing-time first) served by its teams.
+struct Plan {
+  std::vector<int> cta_team, cta_rank, team_T, team_slot, team_class, class_off, order, class_T;
+  std::vector<int> prob_T;   // team size of each problem
+  int num_teams = 0, grid = 0, max_T = 1, slots = 0;
+};
+
+fs1_status plan_teams(fs1_handle* h, int kind, const std::vector<const fs1_problem*>& ps, Plan* P) {
+  const int thr = team_threads();
+  const int maxc = max_coresident_ctas(kind);
+  if (maxc <= 0) return FS1_ECUDA;
+  const int n = (int)ps.size();
+  std::vector<int> tmin(n);
+  std::vector<double> cost(n);
+  for (int i = 0; i < n; ++i) {
+    const double c = ps[i]->h[0] / ps[i]->eps;
+    const int64_t cap = elems_cap_for(kind, c);
+    const int64_t np = npoints(*ps[i]);
+    const int64_t t = (np + thr * cap - 1) / (thr * cap);
+    if (t > maxc) return FS1_EUNSUPPORTED;
+    int p2 = 1;
+    while (p2 < t) p2 <<= 1;
+    tmin[i] = std::min<int>(p2, maxc);
+    if (h->cfg.team_size > 0) {
+      if (h->cfg.team_size > maxc) return FS1_EINVAL;
+      tmin[i] = std::max<int>((int)t, h->cfg.team_size);
+    }
+    cost[i] = (double)np * (double)std::max<int64_t>(1, ps[i]->itr_max);
+  }
+  // classes by team size
+  std::vector<int> keys(tmin);
+  std::sort(keys.begin(), keys.end());
+  keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+  const int nc = (int)keys.size();
+  std::vector<double> W(nc, 0.0);
+  std::vector<int> cnt(nc, 0), cls(n);
+  for (int i = 0; i < n; ++i) {
+    cls[i] = (int)(std::lower_bound(keys.begin(), keys.end(), tmin[i]) - keys.begin());
+    W[cls[i]] += cost[i];
+    cnt[cls[i]] += 1;
+  }
+  double Wt = 0.0;
+  for (double w : W) Wt += w;
+  std::vector<int> T(keys), teams(nc, 1);
+  int base = 0;
+  for (int k = 0; k < nc; ++k) base += T[k];
+  if (base > maxc) return FS1_EUNSUPPORTED;   // caller splits by class
+  if (nc == 1) {
+    teams[0] = std::max(1, std::min(cnt[0], maxc / T[0]));
+    if (h->cfg.team_size <= 0) {
+      int tuse = 1;
+      for (int i = 0; i < n; ++i)
+        tuse = std::max<int>(tuse, (int)std::min<int64_t>((npoints(*ps[i]) + thr - 1) / thr, maxc));
+      T[0] = std::max(T[0], std::min(tuse, maxc / teams[0]));
+    }
+  } else {
+    for (int k = 0; k < nc; ++k) {
+      const int want = (int)std::floor(maxc * W[k] / Wt);
+      teams[k] = std::max(1, std::min(cnt[k], want / T[k]));
+    }
+    auto used = [&]() {
+      int u = 0;
+      for (int k = 0; k < nc; ++k) u += teams[k] * T[k];
+      return u;
+    };
+    while (used() > maxc) {
+      int kk = -1;
+      for (int k = 0; k < nc; ++k)
+        if (teams[k] > 1 && (kk < 0 || teams[k] * T[k] > teams[kk] * T[kk])) kk = k;
+      if (kk < 0) break;
+      --teams[kk];
+    }
+    // leftover CTAs: more teams where the work per team is largest
+    for (;;) {
+      int kk = -1;
+      double best = 0.0;
+      for (int k = 0; k < nc; ++k)
+        if (teams[k] < cnt[k] && used() + T[k] <= maxc && W[k] / teams[k] > best) {
+          best = W[k] / teams[k];
+          kk = k;
+        }
+      if (kk < 0) break;
+      ++teams[kk];
+    }
+  }
+  // queues in decreasing cost
+  P->class_off.assign(nc + 1, 0);
+  for (int k = 0; k < nc; ++k) P->class_off[k + 1] = P->class_off[k] + cnt[k];
+  P->order.assign(n, 0);
+  std::vector<int> idx(n);
+  for (int i = 0; i < n; ++i) idx[i] = i;
+  std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+    if (cls[x] != cls[y]) return cls[x] < cls[y];
+    return cost[x] > cost[y];
+  });
+  for (int i = 0; i < n; ++i) P->order[i] = idx[i];
+  // teams and CTAs
+  P->cta_team.clear();
+  P->cta_rank.clear();
+  P->team_T.clear();
+  P->team_slot.clear();
+  P->team_class.clear();
+  P->class_T = T;
+  int slot = 0;
+  for (int k = 0; k < nc; ++k)
+    for (int t = 0; t < teams[k]; ++t) {
+      const int team = (int)P->team_T.size();
+      P->team_T.push_back(T[k]);
+      P->team_slot.push_back(slot);
+      P->team_class.push_back(k);
+      slot += 2 * T[k];
+      for (int r = 0; r < T[k]; ++r) {
+        P->cta_team.push_back(team);
+        P->cta_rank.push_back(r);
+      }
+      P->max_T = std::max(P->max_T, T[k]);
+    }
+  P->num_teams = (int)P->team_T.size();
+  P->grid = (int)P->cta_team.size();
+  P->slots = slot;
+  P->prob_T.assign(n, 0);
+  for (int i = 0; i < n; ++i) P->prob_T[i] = T[cls[i]];
+  return FS1_OK;
+}
+
 // run one group (same kind, all 1D, device-located) in one launch
 fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const fs1_problem*>& ps,
                      std::vector<PairResult>& res, Geometry& geo, float* ms, bool validate) {
@@ -175,16 +304,28 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
   } else if ((st = choose_geometry(h, kind, ps, &geo)) != FS1_OK) {
     return st;
   }
-  const int T = two_d ? 1 : geo.team_size, teams = two_d ? 1 : geo.num_teams;
+  Plan plan;
+  const bool planned = !two_d && mode == 0;
+  if (planned && (st = plan_teams(h, kind, ps, &plan)) != FS1_OK) return st;
+  const int T = two_d ? 1 : (planned ? plan.max_T : geo.team_size);
+  const int teams = two_d ? 1 : (planned ? plan.num_teams : geo.num_teams);
+  const size_t nslots = planned ? (size_t)plan.slots : (size_t)teams * 2 * T;
   const int in_f32 = ps[0]->dtype == FS1_FP32;
   size_t off = 0;
   const size_t o_desc = off; off = align_up(off + sizeof(PairDesc) * count, 256);
   const size_t o_res = off;  off = align_up(off + sizeof(PairResult) * count, 256);
   const size_t o_val = off;  off = align_up(off + sizeof(ValOut) * count, 256);
-  const size_t o_slot = off; off = align_up(off + sizeof(Slot) * (size_t)teams * 2 * T, 256);
-  const size_t o_cslot = off; off = align_up(off + 128 * (size_t)teams * 2 * T, 256);
+  const size_t o_slot = off; off = align_up(off + sizeof(Slot) * nslots, 256);
+  const size_t o_cslot = off; off = align_up(off + 128 * nslots, 256);
   const size_t o_ctr = off;  off = align_up(off + sizeof(unsigned long long) * teams, 256);
   const size_t o_abt = off;  off = align_up(off + sizeof(int) * teams, 256);
+  // plan arrays: cta_team, cta_rank [grid]; team_T, team_slot, team_class
+  // [teams]; class_off [nc + 1]; order [count]; class_next [nc]
+  const int nclass = planned ? (int)plan.class_T.size() : 0;
+  const int pgrid = planned ? plan.grid : 0;
+  const size_t plan_ints = planned ? (size_t)2 * pgrid + 3 * teams + (nclass + 1) + count + nclass : 0;
+  const size_t o_plan = off; off = align_up(off + sizeof(int) * plan_ints, 256);
+  const size_t o_tick = off; off = align_up(off + sizeof(unsigned long long) * (planned ? teams : 0), 256);
   std::vector<PairDesc> desc(count);
   for (int i = 0; i < count; ++i) {
     const fs1_problem& p = *ps[i];
@@ -218,8 +359,24 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
   if ((e = cudaMemcpyAsync(ws + o_res, init.data(), sizeof(PairResult) * count, cudaMemcpyHostToDevice,
                            h->stream)) != cudaSuccess)
     return cuda_fail(e, "result init");
-  cudaMemsetAsync(ws + o_slot, 0, sizeof(Slot) * (size_t)teams * 2 * T, h->stream);
-  cudaMemsetAsync(ws + o_cslot, 0, 128 * (size_t)teams * 2 * T, h->stream);
+  cudaMemsetAsync(ws + o_slot, 0, sizeof(Slot) * nslots, h->stream);
+  cudaMemsetAsync(ws + o_cslot, 0, 128 * nslots, h->stream);
+  std::vector<int> pints;
+  if (planned) {
+    pints.reserve(plan_ints);
+    pints.insert(pints.end(), plan.cta_team.begin(), plan.cta_team.end());
+    pints.insert(pints.end(), plan.cta_rank.begin(), plan.cta_rank.end());
+    pints.insert(pints.end(), plan.team_T.begin(), plan.team_T.end());
+    pints.insert(pints.end(), plan.team_slot.begin(), plan.team_slot.end());
+    pints.insert(pints.end(), plan.team_class.begin(), plan.team_class.end());
+    pints.insert(pints.end(), plan.class_off.begin(), plan.class_off.end());
+    pints.insert(pints.end(), plan.order.begin(), plan.order.end());
+    pints.insert(pints.end(), (size_t)nclass, 0);   // class_next
+    if ((e = cudaMemcpyAsync(ws + o_plan, pints.data(), sizeof(int) * pints.size(), cudaMemcpyHostToDevice,
+                             h->stream)) != cudaSuccess)
+      return cuda_fail(e, "plan copy");
+    cudaMemsetAsync(ws + o_tick, 0, sizeof(unsigned long long) * teams, h->stream);
+  }
   cudaMemsetAsync(ws + o_ctr, 0, sizeof(unsigned long long) * teams, h->stream);
   cudaMemsetAsync(ws + o_abt, 0, sizeof(int) * teams, h->stream);
 
@@ -269,6 +426,19 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
   L.cslots = (unsigned long long*)(ws + o_cslot);
   L.counters = (unsigned long long*)(ws + o_ctr);
   L.abort_flags = (int*)(ws + o_abt);
+  if (planned) {
+    int* pi = (int*)(ws + o_plan);
+    L.grid = pgrid;
+    L.cta_team = pi;
+    L.cta_rank = pi + pgrid;
+    L.team_T = pi + 2 * pgrid;
+    L.team_slot = pi + 2 * pgrid + teams;
+    L.team_class = pi + 2 * pgrid + 2 * teams;
+    L.class_off = pi + 2 * pgrid + 3 * teams;
+    L.order = pi + 2 * pgrid + 3 * teams + nclass + 1;
+    L.class_next = pi + 2 * pgrid + 3 * teams + nclass + 1 + count;
+    L.tickets = (unsigned long long*)(ws + o_tick);
+  }
   L.spin_cap = h->cfg.spin_cap;
   cudaEventRecord(h->ev0, h->stream);
   int ls;
@@ -286,6 +456,7 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
     return cuda_fail(e, "result copy");
   if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(e, "solve");
   cudaEventElapsedTime(ms, h->ev0, h->ev1);
+  if (planned) geo.team_size = plan.max_T;
   return FS1_OK;
 }
 

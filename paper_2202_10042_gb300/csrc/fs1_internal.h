@@ -52,6 +52,17 @@ struct TeamLaunch {
   unsigned long long* counters;    // [num_teams] reserved (zeroed per launch)
   int* abort_flags;                // [num_teams] (zeroed per launch)
   long long spin_cap;              // bounded-wait polls before giving up
+  // Heterogeneous teams with dynamic work queues (all null / 0: uniform teams
+  // of team_size CTAs taking pairs team, team + num_teams, ...).
+  int grid;                        // CTAs of the launch (0: num_teams * team_size)
+  const int* cta_team;             // [grid] team of each CTA
+  const int* cta_rank;             // [grid] rank of each CTA in its team
+  const int* team_T;               // [num_teams] CTAs of each team
+  const int* team_slot;            // [num_teams] first slot of the team's [2][T] slots
+  const int* team_class;           // [num_teams] work class served by the team
+  const int* class_off;            // [nclass + 1] offsets of each class's pairs in `order`
+  int* class_next;                 // [nclass] queue heads (zeroed per launch)
+  unsigned long long* tickets;     // [num_teams] pair broadcast words (zeroed per launch)
 };
 
 enum KernelKind {

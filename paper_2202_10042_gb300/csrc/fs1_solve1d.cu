@@ -62,6 +62,13 @@ struct DecayTables {
 
 constexpr int kMaxTeamCtas = 256;   // the team reduction serves up to 256 CTAs
 
+// where a CTA sits: its team, rank, team size and the team's slots
+struct TeamCtx {
+  int team, rank, T;
+  size_t slot_base;   // first slot of the team's [2][T] slot block
+  int* abort;
+};
+
 template <class T>
 struct SlotPayload {
   T f, b;
@@ -210,12 +217,12 @@ __device__ __forceinline__ XF xf_unbits(unsigned frac, unsigned e16) {
 // publish / poll a CTA's slot: compact words for XF carries when `compact`,
 // tagged 32-bit chunks (generic slots) otherwise
 template <class T>
-__device__ __forceinline__ void publish(const TeamLaunch& L, int team, int rank, unsigned epoch, bool compact,
+__device__ __forceinline__ void publish(const TeamLaunch& L, const TeamCtx& tc, unsigned epoch, bool compact,
                                         const T& f, const T& b, float eh, float el) {
-  const int T_ = L.team_size;
+  const size_t slot = tc.slot_base + (size_t)(epoch & 1) * tc.T + tc.rank;
   if constexpr (std::is_same<T, XF>::value) {
     if (compact) {
-      unsigned long long* w = L.cslots + (((size_t)team * 2 + (epoch & 1)) * T_ + rank) * kCompactWords;
+      unsigned long long* w = L.cslots + slot * kCompactWords;
       unsigned ff, fe, bf, be;
       xf_bits(f, ff, fe);
       xf_bits(b, bf, be);
@@ -228,16 +235,15 @@ __device__ __forceinline__ void publish(const TeamLaunch& L, int team, int rank,
       return;
     }
   }
-  Slot* s = L.slots + ((size_t)team * 2 + (epoch & 1)) * T_ + rank;
-  slot_publish<T>(s, f, b, eh, el, epoch);
+  slot_publish<T>(L.slots + slot, f, b, eh, el, epoch);
 }
 template <class T>
-__device__ __forceinline__ bool try_read(const TeamLaunch& L, int team, int j, unsigned epoch, bool compact,
+__device__ __forceinline__ bool try_read(const TeamLaunch& L, const TeamCtx& tc, int j, unsigned epoch, bool compact,
                                          SlotPayload<T>& out) {
-  const int T_ = L.team_size;
+  const size_t slot = tc.slot_base + (size_t)(epoch & 1) * tc.T + j;
   if constexpr (std::is_same<T, XF>::value) {
     if (compact) {
-      const unsigned long long* w = L.cslots + (((size_t)team * 2 + (epoch & 1)) * T_ + j) * kCompactWords;
+      const unsigned long long* w = L.cslots + slot * kCompactWords;
       unsigned long long w0, w1;
       ld_relaxed_v2(w, w0, w1);
       const unsigned tg = epoch & 0xFFu;
@@ -249,8 +255,7 @@ __device__ __forceinline__ bool try_read(const TeamLaunch& L, int team, int j, u
       return true;
     }
   }
-  const Slot* s = L.slots + ((size_t)team * 2 + (epoch & 1)) * T_ + j;
-  return slot_try_read<T>(s, epoch, out);
+  return slot_try_read<T>(L.slots + slot, epoch, out);
 }
 
 // sums over the 16 lanes of each half-warp
@@ -303,14 +308,14 @@ __device__ __forceinline__ void hw_sum_df(float& hi, float& lo) {
 // up.  decision: 0 continue, 1 error <= tol, 2 error not finite.
 // ---------------------------------------------------------------------------
 template <class Op, class C, class EV>
-__device__ __forceinline__ bool exchange(const TeamLaunch& L, int team, int rank, unsigned& epoch,
+__device__ __forceinline__ bool exchange(const TeamLaunch& L, const TeamCtx& tc, unsigned& epoch,
                                          unsigned& xc, typename Op::T af, typename Op::T ab, EV err_part,
                                          int Eeff, const DecayTables<C>& tb, XchgSmem<typename Op::T>& X,
                                          typename Op::T& cf, typename Op::T& cb, float tol_h, float tol_l,
                                          int& decision, float* err_h, float* err_l, bool compact = false) {
   using T = typename Op::T;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int T_ = L.team_size;
+  const int T_ = tc.T, rank = tc.rank;
   const int par = (int)(xc++ & 1u);
   // ---- A
   float eh, el;
@@ -350,15 +355,15 @@ __device__ __forceinline__ bool exchange(const TeamLaunch& L, int team, int rank
       }
       const T ctf = warp_sum_c(xf);
       const T ctb = warp_sum_c(xb);
-      if (lane == 0) publish<T>(L, team, rank, epoch, compact, ctf, ctb, th, tl);
+      if (lane == 0) publish<T>(L, tc, epoch, compact, ctf, ctb, th, tl);
     }
     // ---- C: every thread with tid < T polls slot tid (independent loads)
     if ((int)threadIdx.x < T_) {
       SlotPayload<T> p;
       long long spins = 0;
       bool good = true;
-      while (!try_read<T>(L, team, threadIdx.x, epoch, compact, p)) {
-        if (++spins > L.spin_cap || ((spins & 63) == 0 && ld_relaxed(L.abort_flags + team))) {
+      while (!try_read<T>(L, tc, threadIdx.x, epoch, compact, p)) {
+        if (++spins > L.spin_cap || ((spins & 63) == 0 && ld_relaxed(tc.abort))) {
           good = false;
           break;
         }
@@ -369,7 +374,7 @@ __device__ __forceinline__ bool exchange(const TeamLaunch& L, int team, int rank
       if (good) {
         X.stage[threadIdx.x] = p;
       } else {
-        atomicExch(L.abort_flags + team, 1);
+        atomicExch(tc.abort, 1);
         atomicExch(&X.ok, 0);
       }
     }
@@ -449,20 +454,71 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
   __shared__ XchgSmem<DT> XD;
   __shared__ XchgSmem<PT> XP;
 
-  const int T = L.team_size;
-  const int team = blockIdx.x / T;
-  const int rank = blockIdx.x % T;
+  __shared__ int sm_item;
   const int tid = threadIdx.x;
+  TeamCtx tc;
+  int cls = -1;
+  if (L.cta_team) {
+    tc.team = L.cta_team[blockIdx.x];
+    tc.rank = L.cta_rank[blockIdx.x];
+    tc.T = L.team_T[tc.team];
+    tc.slot_base = (size_t)L.team_slot[tc.team];
+    cls = L.team_class[tc.team];
+  } else {
+    tc.T = L.team_size;
+    tc.team = blockIdx.x / tc.T;
+    tc.rank = blockIdx.x % tc.T;
+    tc.slot_base = (size_t)tc.team * 2 * tc.T;
+  }
+  tc.abort = L.abort_flags + tc.team;
+  const int T = tc.T, team = tc.team, rank = tc.rank;
   if (team >= L.num_teams) return;
-  unsigned epoch = 0, xc = 0;
+  unsigned epoch = 0, xc = 0, seq = 0;
   if (tid == 0) {
     XD.ok = 1;
     XP.ok = 1;
   }
   __syncthreads();
 
-  for (int pi = team; pi < L.num_pairs; pi += L.num_teams) {
-    const int pid = L.order ? L.order[pi] : pi;
+  for (int pi = team;; pi += L.num_teams) {
+    int pid;
+    if (cls < 0) {
+      if (pi >= L.num_pairs) break;
+      pid = L.order ? L.order[pi] : pi;
+    } else {
+      // next pair of the class queue; the team's rank 0 takes the ticket and
+      // broadcasts it to the other CTAs of the team through a tagged word
+      ++seq;
+      if (tid == 0) {
+        int item;
+        if (rank == 0) {
+          item = atomicAdd(L.class_next + cls, 1);
+          if (T > 1) {
+            const unsigned long long w = ((unsigned long long)seq << 32) | (unsigned)item;
+            asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(L.tickets + team), "l"(w) : "memory");
+          }
+        } else {
+          long long spins = 0;
+          unsigned long long w = 0;
+          for (;;) {
+            asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(L.tickets + team) : "memory");
+            if ((unsigned)(w >> 32) == seq) break;
+            if (++spins > L.spin_cap || ((spins & 63) == 0 && ld_relaxed(tc.abort))) {
+              atomicExch(tc.abort, 1);
+              w = 0xFFFFFFFFull;   // -1: give up
+              break;
+            }
+          }
+          item = (int)(unsigned)w;
+        }
+        sm_item = item;
+      }
+      __syncthreads();
+      const int item = sm_item;
+      if (item < 0) return;   // the ticket wait gave up (the other CTAs time out too)
+      if (item >= L.class_off[cls + 1] - L.class_off[cls]) break;
+      pid = L.order[L.class_off[cls] + item];
+    }
     const PairDesc P = L.pairs[pid];
     const int64_t N = P.n;
     const double c = P.h_fast / P.eps;
@@ -560,7 +616,7 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
       for (int k = E - 1; k >= 0; --k)
         if (k < Eeff) s = lam * (s + xu[k]);
       int dec;
-      if (!exchange<OpP, C>(L, team, rank, epoch, xc, c_from(r, fu, C{}), c_from(s, fu, C{}), (V)0, Eeff, tb, XP,
+      if (!exchange<OpP, C>(L, tc, epoch, xc, c_from(r, fu, C{}), c_from(s, fu, C{}), (V)0, Eeff, tb, XP,
                             cf, cb, 0.f, 0.f, dec, nullptr, nullptr, compact))
         goto timed_out;
     }
@@ -611,7 +667,7 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
             break;
           }
           int dec;
-          if (!exchange<OpP, C>(L, team, rank, epoch, xc, c_from(af, fz, C{}), c_from(ab, fz, C{}), ep, Eeff, tb, XP,
+          if (!exchange<OpP, C>(L, tc, epoch, xc, c_from(af, fz, C{}), c_from(ab, fz, C{}), ep, Eeff, tb, XP,
                                 cf, cb, tol_h, tol_l, dec, &eh_last, &el_last, compact))
             goto timed_out;
           if (dec != 0 || ell >= P.itr_max) {
@@ -656,7 +712,7 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
           fu = fz;
           hu = (EXT && zmax > 0) ? fz + fexp((float)zmax) : kZeroExp;
           int dec;
-          if (!exchange<OpP, C>(L, team, rank, epoch, xc, c_from(af, fz, C{}), c_from(ab, fz, C{}), (V)0, Eeff, tb,
+          if (!exchange<OpP, C>(L, tc, epoch, xc, c_from(af, fz, C{}), c_from(ab, fz, C{}), (V)0, Eeff, tb,
                                 XP, cf, cb, 0.f, 0.f, dec, nullptr, nullptr, compact))
             goto timed_out;
         }
@@ -689,7 +745,7 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
         DT ab{c_from(s, fv, C{}), c_from(B, fv, C{})};
         DT dcf, dcb;
         int dec;
-        if (!exchange<OpD, C>(L, team, rank, epoch, xc, af, ab, (V)0, Eeff, tb, XD, dcf, dcb, 0.f, 0.f, dec, nullptr,
+        if (!exchange<OpD, C>(L, tc, epoch, xc, af, ab, (V)0, Eeff, tb, XD, dcf, dcb, 0.f, 0.f, dec, nullptr,
                               nullptr))
           goto timed_out;
         int F = 0;
@@ -717,7 +773,7 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
         wpart *= P.h_fast;
         float wh = 0.f, wl = 0.f;
         PT z0 = OpP::zero(), c0, c1;
-        if (!exchange<OpP, C>(L, team, rank, epoch, xc, z0, z0, wpart, Eeff, tb, XP, c0, c1, 0.f, 0.f, dec, &wh,
+        if (!exchange<OpP, C>(L, tc, epoch, xc, z0, z0, wpart, Eeff, tb, XP, c0, c1, 0.f, 0.f, dec, &wh,
                               &wl))
           goto timed_out;
         wpart = (double)wh + (double)wl;
@@ -781,7 +837,8 @@ static cudaError_t launch_kind(const TeamLaunch& L, int mode, cudaStream_t st) {
   const size_t smem = 3 * sizeof(V) * (size_t)E * kThreads;
   cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int grid = L.num_teams * L.team_size;
+  // heterogeneous launches carry their grid; team_size is then the largest team
+  const int grid = L.grid > 0 ? L.grid : L.num_teams * L.team_size;
   if (L.team_size > 1) {
     TeamLaunch Lc = L;
     void* args[] = {&Lc, &mode};

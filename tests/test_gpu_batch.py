@@ -1,0 +1,71 @@
+"""Uneven batches in one persistent launch (workload 3 shape): parity against
+the CPU FP64 oracle per pair, and the same result alone and in the mix."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import cref
+from paper_2202_10042_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-4
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2202_10042_gb300 import fs1
+    fs1.load()
+    return torch, fs1
+
+
+def _solve(env, ps, **kw):
+    torch, fs1 = env
+    s = fs1.Solver("log", "fp32", **kw)
+    keep, probs = [], []
+    for p in ps:
+        a = torch.tensor(p.a, dtype=torch.float64, device="cuda")
+        b = torch.tensor(p.b, dtype=torch.float64, device="cuda")
+        keep += [a, b]
+        probs.append(fs1.Solver.problem(a, b, p.h[0], p.eps, p.tol, p.itr_max))
+    st, w, infos = s.solve(probs)
+    s.close()
+    return w, infos
+
+
+def test_workload3_sample_against_oracle(env):
+    _, fs1 = env
+    ps = [inputs.workload3(i, itr_max=150) for i in range(40)]
+    w, infos = _solve(env, ps)
+    refs = cref.solve_many([(p.a, p.b, p.h[0], p.eps, 0.0, infos[k].iters) for k, p in enumerate(ps)],
+                           tau=1e10)
+    ns = sorted(p.a.size for p in ps)
+    assert ns[0] < 2000 and ns[-1] > 20000   # the sample spans several team classes
+    for k, (p, r) in enumerate(zip(ps, refs)):
+        assert infos[k].status in (fs1.FS1_OK, fs1.FS1_ENOTCONV)
+        assert abs(w[k] - r.w) <= TOL32 * abs(r.w), (k, p.a.size, p.eps, w[k], r.w)
+        if infos[k].status == fs1.FS1_OK:
+            assert infos[k].marginal_err <= p.tol
+
+
+def test_same_alone_and_in_mix(env):
+    ps = [inputs.workload3(i, itr_max=400) for i in range(24)]
+    w_mix, i_mix = _solve(env, ps)
+    for k in (0, 7, 13, 23):
+        w1, i1 = _solve(env, [ps[k]])
+        assert i1[0].iters == i_mix[k].iters or abs(i1[0].iters - i_mix[k].iters) <= 1
+        assert abs(w1[0] - w_mix[k]) <= TOL32 * abs(w_mix[k])
+
+
+def test_forced_team_size_and_order_independence(env):
+    ps = [inputs.workload3(i, itr_max=100, n_range=(3000, 30000)) for i in range(12)]
+    w_a, _ = _solve(env, ps)
+    w_b, _ = _solve(env, ps[::-1])
+    w_c, _ = _solve(env, ps, team_size=8)
+    for k in range(12):
+        assert abs(w_a[k] - w_b[11 - k]) <= TOL32 * abs(w_a[k])
+        assert abs(w_a[k] - w_c[k]) <= TOL32 * abs(w_a[k])
