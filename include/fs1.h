@@ -88,7 +88,8 @@ typedef struct fs1_problem {
   int64_t itr_max;      /* iteration cap (>= 0) */
   const void* a;        /* histogram a (the paper's u): n[0]*n[1] values >= 0, sum > 0 */
   const void* b;        /* histogram b (the paper's v); same total mass as a */
-  double* f_out;        /* optional: log u of the final iterate (FP64, n values) */
+  double* f_out;        /* optional: log u of the final iterate (FP64, n[0]*n[1] values,
+                           same layout as a) */
   double* g_out;        /* optional: log v of the final iterate */
   const double* f_init; /* optional warm start: log u, log v of an earlier run's final */
   const double* g_init; /*   iterate (both or neither); resumes bit-identically */

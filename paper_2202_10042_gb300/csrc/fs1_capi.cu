@@ -121,7 +121,6 @@ fs1_status check_problem(const fs1_problem& p) {
   if (p.itr_max < 0) return FS1_EINVAL;
   if (!p.a || !p.b) return FS1_EINVAL;
   if ((p.f_init == nullptr) != (p.g_init == nullptr)) return FS1_EINVAL;
-  if (p.ndim == 2 && (p.f_init || p.f_out || p.g_out)) return FS1_EUNSUPPORTED;   // 1D only
   return FS1_OK;
 }
 

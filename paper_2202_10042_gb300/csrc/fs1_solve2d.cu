@@ -56,6 +56,10 @@ struct Img2D {
   XF* V[2];            // v by iteration parity
   XF* Y;               // fast-pass output
   XF* R;               // slow-pass output and parking area
+  const double* f_init;   // optional warm start (log u, log v), row major
+  const double* g_init;
+  double* f_out;          // optional potentials out
+  double* g_out;
   float* errp;         // [2 nf] column error partials (compensated pairs)
   double* wp;          // [nf] column cost partials
   int* stop;           // 0 while active; 1 + k once stopped with the final v in V[k]
@@ -96,6 +100,17 @@ __device__ bool grid_barrier(const Launch2D& L, unsigned long long& gen, int* sm
   }
   __syncthreads();
   return *sm_ok != 0;
+}
+
+// extended-range value of e^x (x = -inf gives zero)
+__device__ __forceinline__ XF xf_from_log(double x) {
+  if (!(x > -INFINITY)) return XF{0.f, kZeroExp};
+  const double t = x * 1.4426950408889634;
+  const double e = floor(t);
+  return xf_norm((float)exp2(t - e), (int)e);
+}
+__device__ __forceinline__ double xf_log(XF v) {
+  return v.m > 0.f ? log((double)v.m) + (double)v.e * 0.6931471805599453 : -INFINITY;
 }
 
 // image owning flat item t of a prefix-offset table (nimg <= kMaxImg2D)
@@ -218,14 +233,14 @@ __global__ void __launch_bounds__(kThreads2) fs1_solve2d_kernel(Launch2D L) {
     const double k = j <= 32 ? (double)j : (double)P * (double)(1 << (j - 33));
     tab[i][ax][j] = c_decay(k, c, XF{});
   }
-  // u = v = 1 / (n_fast n_slow)  (Algorithm 2, line 1)
+  // u = v = 1 / (n_fast n_slow)  (Algorithm 2, line 1), or a warm start
   for (int i = 0; i < nimg; ++i) {
     const Img2D& I = L.imgs[i];
     const int64_t N = (int64_t)I.nf * I.ns;
     const XF init = xf_norm((float)(1.0 / (double)N), 0);
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
-      I.U[p] = init;
-      I.V[0][p] = init;
+      I.U[p] = I.f_init ? xf_from_log(I.f_init[p]) : init;
+      I.V[0][p] = I.g_init ? xf_from_log(I.g_init[p]) : init;
     }
   }
   if (!grid_barrier(L, gen, &sok)) return;
@@ -367,6 +382,17 @@ __global__ void __launch_bounds__(kThreads2) fs1_solve2d_kernel(Launch2D L) {
     if (lane == 0) I.wp[col] = acc;
   }
   if (!grid_barrier(L, gen, &sok)) return;
+  // optional potentials out: log u and log v of the returned iterate
+  for (int i = 0; i < nimg; ++i) {
+    const Img2D& I = L.imgs[i];
+    if (!I.f_out && !I.g_out) continue;
+    const int k = (ld_relaxed(I.stop) - 1) & 1;
+    const int64_t N = (int64_t)I.nf * I.ns;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+      if (I.f_out) I.f_out[p] = xf_log(I.U[p]);
+      if (I.g_out) I.g_out[p] = xf_log(I.V[k][p]);
+    }
+  }
   if (blockIdx.x == 0) {
     for (int i = warp; i < nimg; i += kWarps2) {
       const Img2D& I = L.imgs[i];
@@ -425,6 +451,10 @@ int launch_solve_2d(const PairDesc* d, int count, int in_f32, PairResult* result
     I.hs = D.h_slow;
     I.tol = D.tol;
     I.itr_max = D.itr_max;
+    I.f_init = D.f_init;
+    I.g_init = D.g_init;
+    I.f_out = D.f_out;
+    I.g_out = D.g_out;
     const size_t n = (size_t)I.nf * I.ns;
     I.U = (XF*)p; p += align256(sizeof(XF) * n);
     I.V[0] = (XF*)p; p += align256(sizeof(XF) * n);

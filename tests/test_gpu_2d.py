@@ -105,3 +105,21 @@ def test_workload4_full_size_sampled(env):
         assert infos[i].iters == r.iters == 40
         assert abs(w[i] - r.w) <= TOL32 * abs(r.w)
         assert abs(infos[i].marginal_err - r.err) <= 1e-3 * r.err
+
+
+def test_2d_warm_start_resume_bit_identical(env):
+    torch, fs1 = env
+    a2, b2 = _rand2d(77, 40, 56)
+    h, eps = (1 / 56, 1 / 40), 0.01
+    ta = torch.tensor(a2, device="cuda")
+    tb = torch.tensor(b2, device="cuda")
+    s = fs1.Solver("log", "fp32")
+    st, w_full, i_full = s.solve([fs1.Solver.problem(ta, tb, h, eps, 0.0, 50)])
+    f = torch.empty_like(ta)
+    g = torch.empty_like(ta)
+    s.solve([fs1.Solver.problem(ta, tb, h, eps, 0.0, 20, f_out=f, g_out=g)])
+    st, w_res, i_res = s.solve([fs1.Solver.problem(ta, tb, h, eps, 0.0, 30, f_init=f, g_init=g)])
+    s.close()
+    assert i_res[0].iters == 30
+    assert w_res[0] == w_full[0]
+    assert i_res[0].marginal_err == i_full[0].marginal_err
