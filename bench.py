@@ -241,7 +241,8 @@ def run_gpu(args):
     host = make_pairs(idx, W["n"], W["eps"], W["tol"], W["itr_max"])
     h = 1.0 / W["n"]
     stream = torch.cuda.current_stream(dev)
-    solver = fs1.Solver("log", "fp32", stream=stream.cuda_stream)
+    solver = fs1.Solver("log", "fp32", stream=stream.cuda_stream, team_size=args.team_size,
+                        autotune=not args.no_autotune, use_graph=not args.no_graph)
 
     # device-resident inputs
     dev_t = [(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)) for a, b in host]
@@ -338,6 +339,8 @@ def run_gpu(args):
                 "config": {"workload": W["name"], "n": W["n"], "pairs": len(idx), "eps": W["eps"],
                            "tol": W["tol"], "itr_max": W["itr_max"], "parallelism": f"dp{world} (pairs)",
                            "l2": "inputs larger than L2 (%.1f GB per step)" % (h2d / 1e9),
+                           "team_size": int(infos[0].team_size),
+                           "launch": "graph replay" if solver.stats()["graph_replays"] else "direct",
                            "iters_min": min(iters), "iters_max": max(iters),
                            "err_median": statistics.median(errs)},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -377,6 +380,9 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-iters", type=int, default=300)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--team-size", type=int, default=0, help="CTAs per pair (0: autotuned)")
+    ap.add_argument("--no-autotune", action="store_true", help="fixed team-size heuristic")
+    ap.add_argument("--no-graph", action="store_true", help="direct launches instead of graph replay")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

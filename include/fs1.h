@@ -15,8 +15,9 @@
  * Conventions
  *   - All functions return an fs1_status; none aborts or throws.
  *   - Pointers in fs1_problem are DEVICE pointers unless the problem's
- *     `location` is FS1_MEM_HOST, in which case the library stages them to
- *     the device itself (an allocation and two copies per call).
+ *     `location` is FS1_MEM_HOST, in which case the library copies them into
+ *     a grow-only device staging buffer of the handle (and the optional
+ *     outputs back) on the handle's stream.
  *   - Calls are ordered on the handle's CUDA stream (fs1_config.stream; NULL =
  *     the legacy default stream).  fs1_w1 and fs1_solve_batch synchronise that
  *     stream before returning, so their host outputs are valid on return.
@@ -71,6 +72,16 @@ typedef struct fs1_config {
   long long spin_cap;   /* polls of a team barrier before FS1_ETIMEOUT (default 1<<22) */
   size_t hbm_budget;    /* bytes of device workspace the handle may hold; 0 = no limit */
   void* stream;         /* cudaStream_t the handle works on (NULL = default stream) */
+  int autotune;         /* 1 (default): the first batch of each size class times short
+                           trial solves for the candidate team sizes and keeps the best
+                           (cached in the handle, and in the file named by the environment
+                           variable FS1_AUTOTUNE_CACHE when set); 0: fixed heuristic.
+                           Ignored when team_size > 0 */
+  int trial_iters;      /* iterations of an autotune trial (default 48) */
+  int use_graph;        /* 1 (default): from the second 1D call with the same launch
+                           signature on, the call's device work (header copy, slot reset,
+                           input check, team kernel, result copy) is one replayed CUDA
+                           graph; 0: direct launches */
 } fs1_config;
 
 typedef struct fs1_problem {
@@ -92,7 +103,9 @@ typedef struct fs1_problem {
                            same layout as a) */
   double* g_out;        /* optional: log v of the final iterate */
   const double* f_init; /* optional warm start: log u, log v of an earlier run's final */
-  const double* g_init; /*   iterate (both or neither); resumes bit-identically */
+  const double* g_init; /*   iterate (both or neither).  With the FP32 variants and the
+                           same team size, a run of l1 iterations resumed for l2 more
+                           ends bit-identical to one run of l1 + l2 iterations */
 } fs1_problem;
 
 typedef struct fs1_info {
@@ -114,7 +127,11 @@ fs1_status fs1_config_default(fs1_config* cfg);
 
 /* Create a handle on the current CUDA device.  cfg may be NULL (defaults).
  * The handle owns its device workspace (team exchange slots, barrier counters,
- * result and descriptor arrays); it grows on demand within hbm_budget. */
+ * result and descriptor arrays), which grows on demand within hbm_budget, a
+ * pinned host mirror of the launch header and results, a private stream on
+ * which graphs are captured (they are launched on cfg.stream), up to four
+ * captured graphs, and the autotuner's table (read from FS1_AUTOTUNE_CACHE
+ * when that environment variable names a readable file). */
 fs1_status fs1_create(const fs1_config* cfg, fs1_handle** out);
 
 /* Solve one problem (Algorithm 1 in 1D, Algorithm 2 in 2D).
@@ -122,10 +139,15 @@ fs1_status fs1_create(const fs1_config* cfg, fs1_handle** out);
  * Returns the problem's status (FS1_ENOTCONV is a warning; w1 is valid). */
 fs1_status fs1_w1(fs1_handle* h, const fs1_problem* prob, double* w1_out, fs1_info* info_out);
 
-/* Solve `count` independent problems in as few persistent launches as the mix
- * of sizes allows (one per group of problems that share a variant, dimension
- * and team size).  w1_out (count doubles) and infos (count entries) are host
- * arrays and may be NULL.  Returns the worst status over the batch. */
+/* Solve `count` independent problems.  1D problems of one input dtype run in
+ * ONE persistent launch whatever their sizes: they are put in classes by the
+ * fewest CTAs that hold a pair on chip, the GPU's CTAs are split over the
+ * classes in proportion to their work (N * itr_max), and each class's teams
+ * take its pairs from a queue in decreasing cost.  2D problems run in
+ * launches of up to 64 images.  Each problem's inputs are checked on the
+ * device first; a failing problem gets FS1_EINVAL and is not solved.
+ * w1_out (count doubles) and infos (count entries) are host arrays and may be
+ * NULL.  Returns the worst status over the batch. */
 fs1_status fs1_solve_batch(fs1_handle* h, const fs1_problem* probs, int64_t count,
                            double* w1_out, fs1_info* infos);
 
@@ -164,6 +186,10 @@ fs1_status fs1_w1_noalloc(const fs1_config* cfg, const fs1_problem* prob, double
 
 /* Human-readable name of a status code (static string). */
 const char* fs1_status_string(fs1_status s);
+
+/* Counters of a handle, written to out[0..3]: graph replays, graphs
+ * captured, size classes in the autotuner's table, autotune trial launches. */
+fs1_status fs1_handle_stats(const fs1_handle* h, int64_t* out);
 
 /* Library version string. */
 const char* fs1_version(void);

@@ -9,6 +9,10 @@
 
 #include <algorithm>
 #include <atomic>
+#include <fstream>
+#include <map>
+#include <sstream>
+#include <string>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -20,16 +24,38 @@
 
 using namespace fs1;
 
+struct GraphEntry {
+  std::string key;             // launch signature the graph was captured for
+  cudaGraphExec_t exec = nullptr;
+};
+
 struct fs1_handle {
   fs1_config cfg;
   void* stage = nullptr;       // device staging for host-located problems
   size_t stage_bytes = 0;
   int device = 0;
   int sms = 0;
+  int cc = 0;                  // compute capability, 10 * major + minor
   cudaStream_t stream = nullptr;
   void* ws = nullptr;          // device workspace
   size_t ws_bytes = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // pinned host mirrors: the launch header (descriptors, initial results,
+  // plan, zeroed counters) copied in one transfer, and the results
+  void* hdr = nullptr;
+  size_t hdr_bytes = 0;
+  void* hres = nullptr;
+  size_t hres_bytes = 0;
+  // team-size autotuner: single-class batch signature -> team size
+  std::map<std::string, int> tuned;
+  bool tuning = false;         // inside trial solves
+  int force_T = 0;             // team size a trial imposes
+  // graphs of the 1D batch call, most recent first
+  cudaStream_t cap = nullptr;  // private stream that captures
+  std::vector<GraphEntry> graphs;
+  std::string pending;         // last signature seen but not captured yet
+  bool graphs_off = false;     // capture failed once: stay eager
+  int64_t replays = 0, captures = 0, trial_launches = 0;
 };
 
 namespace {
@@ -44,6 +70,8 @@ fs1_status cuda_fail(cudaError_t e, const char* what) {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+void drop_graphs(fs1_handle* h);
+
 fs1_status ensure_ws(fs1_handle* h, size_t bytes) {
   if (bytes <= h->ws_bytes) return FS1_OK;
   if (h->cfg.hbm_budget && bytes > h->cfg.hbm_budget) return FS1_ENOMEM;
@@ -53,6 +81,7 @@ fs1_status ensure_ws(fs1_handle* h, size_t bytes) {
     h->ws = nullptr;
     h->ws_bytes = 0;
   }
+  drop_graphs(h);   // graphs hold addresses in the old workspace
   size_t want = std::max(bytes, (size_t)1 << 20);
   if (cudaMalloc(&h->ws, want) != cudaSuccess) {
     cudaGetLastError();
@@ -62,45 +91,89 @@ fs1_status ensure_ws(fs1_handle* h, size_t bytes) {
   return FS1_OK;
 }
 
-// ---- validation: per pair, sums of a and b, any negative / non-finite ----
-struct ValOut {
-  double sa, sb;
-  int bad;
-  int pad;
-};
+void drop_graphs(fs1_handle* h) {
+  for (auto& g : h->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
+  h->pending.clear();
+}
 
-__global__ void validate_kernel(const PairDesc* pairs, int in_f32, ValOut* out) {
+fs1_status ensure_pinned(fs1_handle* h, void** buf, size_t* have, size_t bytes) {
+  if (bytes <= *have) return FS1_OK;
+  if (*buf) {
+    cudaStreamSynchronize(h->stream);
+    cudaFreeHost(*buf);
+    *buf = nullptr;
+    *have = 0;
+  }
+  drop_graphs(h);   // graphs hold the old host addresses
+  const size_t want = std::max(bytes, (size_t)64 << 10);
+  if (cudaHostAlloc(buf, want, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    *buf = nullptr;
+    return FS1_ENOMEM;
+  }
+  *have = want;
+  return FS1_OK;
+}
+
+// ---- validation: per pair, sums of a and b, any negative / non-finite ----
+// One block per pair.  The sums are compensated FP32 pairs (Knuth's two-sum
+// per addition), so the relative accuracy is about 2^-44 whatever N is, which
+// is far inside the 1e-6 mass-balance tolerance; FP64 inputs enter as the
+// pair (float(v), float(v - float(v))).  The block writes valid[pair] = 1
+// when a, b are finite, non-negative, of positive mass and of equal mass to
+// 1e-6 relative.
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bb = s - hi;
+  lo += (hi - (s - bb)) + (x - bb);
+  hi = s;
+}
+
+__global__ void validate_kernel(const PairDesc* pairs, int in_f32, int* valid) {
   const PairDesc P = pairs[blockIdx.x];
-  double sa = 0.0, sb = 0.0;
+  float ah = 0.f, al = 0.f, bh = 0.f, bl = 0.f;
   int bad = 0;
   for (int64_t i = threadIdx.x; i < P.n; i += blockDim.x) {
-    double va = in_f32 ? (double)((const float*)P.a)[i] : ((const double*)P.a)[i];
-    double vb = in_f32 ? (double)((const float*)P.b)[i] : ((const double*)P.b)[i];
-    if (!(va >= 0.0) || !(vb >= 0.0) || !isfinite(va) || !isfinite(vb)) bad = 1;
-    sa += va;
-    sb += vb;
+    float a0, a1 = 0.f, b0, b1 = 0.f;
+    if (in_f32) {
+      a0 = ((const float*)P.a)[i];
+      b0 = ((const float*)P.b)[i];
+    } else {
+      const double va = ((const double*)P.a)[i], vb = ((const double*)P.b)[i];
+      if (!(va >= 0.0) || !(vb >= 0.0) || !isfinite(va) || !isfinite(vb)) bad = 1;
+      a0 = (float)va;
+      a1 = (float)(va - (double)a0);
+      b0 = (float)vb;
+      b1 = (float)(vb - (double)b0);
+    }
+    if (!(a0 >= 0.f) || !(b0 >= 0.f) || !isfinite(a0) || !isfinite(b0)) bad = 1;
+    two_sum_acc(ah, al, a0);
+    two_sum_acc(bh, bl, b0);
+    al += a1;
+    bl += b1;
   }
-  __shared__ double ssa[32], ssb[32];
-  __shared__ int sbad;
-  if (threadIdx.x == 0) sbad = 0;
+  bad = __syncthreads_or(bad);
+  __shared__ double ss[2][32];
+  double sa = (double)ah + (double)al, sb = (double)bh + (double)bl;
   for (int o = 16; o > 0; o >>= 1) {
     sa += __shfl_xor_sync(0xffffffffu, sa, o);
     sb += __shfl_xor_sync(0xffffffffu, sb, o);
   }
-  __syncthreads();
-  if (bad) atomicOr(&sbad, 1);
   if ((threadIdx.x & 31) == 0) {
-    ssa[threadIdx.x >> 5] = sa;
-    ssb[threadIdx.x >> 5] = sb;
+    ss[0][threadIdx.x >> 5] = sa;
+    ss[1][threadIdx.x >> 5] = sb;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     double ta = 0, tb = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      ta += ssa[w];
-      tb += ssb[w];
+      ta += ss[0][w];
+      tb += ss[1][w];
     }
-    out[blockIdx.x] = ValOut{ta, tb, sbad, 0};
+    const bool ok = !bad && ta > 0.0 && tb > 0.0 && fabs(ta - tb) <= 1e-6 * fmax(ta, tb);
+    valid[blockIdx.x] = ok ? 1 : 0;
   }
 }
 
@@ -136,6 +209,7 @@ fs1_status choose_geometry(fs1_handle* h, int kind, const std::vector<const fs1_
   const int thr = team_threads();
   const int maxc = max_coresident_ctas(kind);
   if (maxc <= 0) return FS1_ECUDA;
+  const int tcap = std::min(maxc, kMaxTeamCtas);
   int tmin = 1, tuse = 1;
   for (auto* p : ps) {
     const double c = p->h[0] / p->eps;
@@ -143,14 +217,14 @@ fs1_status choose_geometry(fs1_handle* h, int kind, const std::vector<const fs1_
     const int64_t n = npoints(*p);
     const int64_t t = (n + thr * cap - 1) / (thr * cap);
     const int64_t tu = (n + thr - 1) / thr;
-    if (t > maxc) return FS1_EUNSUPPORTED;   // does not fit on chip
+    if (t > tcap) return FS1_EUNSUPPORTED;   // does not fit on chip
     tmin = std::max<int>(tmin, (int)t);
-    tuse = std::max<int>(tuse, (int)std::min<int64_t>(tu, maxc));
+    tuse = std::max<int>(tuse, (int)std::min<int64_t>(tu, tcap));
   }
   int T;
   if (h->cfg.team_size > 0) {
     T = std::max(tmin, h->cfg.team_size);
-    if (T > maxc) return FS1_EINVAL;
+    if (T > tcap) return FS1_EINVAL;
   } else {
     int teams = std::max(1, std::min((int)ps.size(), maxc / tmin));
     T = std::max(tmin, std::min(tuse, maxc / teams));
@@ -172,24 +246,55 @@ struct Plan {
   int num_teams = 0, grid = 0, max_T = 1, slots = 0;
 };
 
+// fewest CTAs that hold problem p on chip (0: more than fit)
+int64_t min_ctas(int kind, const fs1_problem& p) {
+  const int thr = team_threads();
+  const int64_t cap = elems_cap_for(kind, p.h[0] / p.eps);
+  return (npoints(p) + thr * cap - 1) / (thr * cap);
+}
+
+int pow2_at_least(int64_t t) {
+  int p2 = 1;
+  while (p2 < t) p2 <<= 1;
+  return p2;
+}
+
+// Signature of a batch whose problems all fall in one size class, for the
+// team-size tuning cache: device, kernel kind, the class's minimum team, the
+// size octave of the largest problem and the octave of the batch size.  Empty
+// when the batch spans several classes (those keep the proportional split).
+std::string tune_key(fs1_handle* h, int kind, const std::vector<const fs1_problem*>& ps, int maxc) {
+  int t0 = -1;
+  int64_t nmax = 1;
+  for (auto* p : ps) {
+    const int t = std::min(pow2_at_least(min_ctas(kind, *p)), std::min(maxc, kMaxTeamCtas));
+    if (t0 >= 0 && t != t0) return std::string();
+    t0 = t;
+    nmax = std::max<int64_t>(nmax, npoints(*p));
+  }
+  int nlog = 0, blog = 0;
+  while (((int64_t)1 << nlog) < nmax) ++nlog;
+  while (((size_t)2 << blog) <= ps.size()) ++blog;
+  char buf[96];
+  snprintf(buf, sizeof buf, "cc%d.sm%d.k%d.t%d.n%d.b%d", h->cc, h->sms, kind, t0, nlog, blog);
+  return buf;
+}
+
 fs1_status plan_teams(fs1_handle* h, int kind, const std::vector<const fs1_problem*>& ps, Plan* P) {
   const int thr = team_threads();
   const int maxc = max_coresident_ctas(kind);
   if (maxc <= 0) return FS1_ECUDA;
+  const int tcap = std::min(maxc, kMaxTeamCtas);
   const int n = (int)ps.size();
   std::vector<int> tmin(n);
   std::vector<double> cost(n);
   for (int i = 0; i < n; ++i) {
-    const double c = ps[i]->h[0] / ps[i]->eps;
-    const int64_t cap = elems_cap_for(kind, c);
     const int64_t np = npoints(*ps[i]);
-    const int64_t t = (np + thr * cap - 1) / (thr * cap);
-    if (t > maxc) return FS1_EUNSUPPORTED;
-    int p2 = 1;
-    while (p2 < t) p2 <<= 1;
-    tmin[i] = std::min<int>(p2, maxc);
+    const int64_t t = min_ctas(kind, *ps[i]);
+    if (t > tcap) return FS1_EUNSUPPORTED;
+    tmin[i] = std::min<int>(pow2_at_least(t), tcap);
     if (h->cfg.team_size > 0) {
-      if (h->cfg.team_size > maxc) return FS1_EINVAL;
+      if (h->cfg.team_size > tcap) return FS1_EINVAL;
       tmin[i] = std::max<int>((int)t, h->cfg.team_size);
     }
     cost[i] = (double)np * (double)std::max<int64_t>(1, ps[i]->itr_max);
@@ -212,12 +317,20 @@ fs1_status plan_teams(fs1_handle* h, int kind, const std::vector<const fs1_probl
   int base = 0;
   for (int k = 0; k < nc; ++k) base += T[k];
   if (base > maxc) return FS1_EUNSUPPORTED;   // caller splits by class
-  if (nc == 1) {
+  int force = h->force_T;
+  if (nc == 1 && force <= 0 && h->cfg.autotune && h->cfg.team_size <= 0 && !h->tuning) {
+    auto it = h->tuned.find(tune_key(h, kind, ps, maxc));
+    if (it != h->tuned.end()) force = it->second;
+  }
+  if (nc == 1 && force > 0) {
+    T[0] = std::min(tcap, std::max(T[0], force));
+    teams[0] = std::max(1, std::min(cnt[0], maxc / T[0]));
+  } else if (nc == 1) {
     teams[0] = std::max(1, std::min(cnt[0], maxc / T[0]));
     if (h->cfg.team_size <= 0) {
       int tuse = 1;
       for (int i = 0; i < n; ++i)
-        tuse = std::max<int>(tuse, (int)std::min<int64_t>((npoints(*ps[i]) + thr - 1) / thr, maxc));
+        tuse = std::max<int>(tuse, (int)std::min<int64_t>((npoints(*ps[i]) + thr - 1) / thr, tcap));
       T[0] = std::max(T[0], std::min(tuse, maxc / teams[0]));
     }
   } else {
@@ -290,7 +403,108 @@ fs1_status plan_teams(fs1_handle* h, int kind, const std::vector<const fs1_probl
   return FS1_OK;
 }
 
-// run one group (same kind, all 1D, device-located) in one launch
+fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const fs1_problem*>& ps,
+                     std::vector<PairResult>& res, Geometry& geo, float* ms, bool validate);
+
+// Team-size autotuner for a batch whose problems share one size class.  Trial
+// solves of the class's costliest problems (as many as the smallest team runs
+// at once), `trial_iters` iterations each with tol = 0 and no outputs, are
+// timed for each candidate team size; the size with the most N * iterations
+// per second is kept under the batch signature (and appended to the cache
+// file named by FS1_AUTOTUNE_CACHE).
+fs1_status autotune(fs1_handle* h, int kind, const std::vector<const fs1_problem*>& ps, const std::string& key,
+                    int maxc) {
+  const int thr = team_threads();
+  const int tcap = std::min(maxc, kMaxTeamCtas);
+  int tmin = 1;
+  int64_t tuse = 1;
+  for (auto* p : ps) {
+    tmin = std::max(tmin, std::min(pow2_at_least(min_ctas(kind, *p)), tcap));
+    tuse = std::max<int64_t>(tuse, std::min<int64_t>((npoints(*p) + thr - 1) / thr, tcap));
+  }
+  // candidates: powers of two from tmin, and for 1, 2, 3, 4, 6, 8, 12, ...
+  // concurrent teams the team size that fills the GPU; none beyond the
+  // CTAs that still give every thread a grid point
+  std::vector<int> cand;
+  auto add = [&](int64_t T) {
+    T = std::min<int64_t>(std::max<int64_t>(T, tmin), std::max<int64_t>(tmin, tuse));
+    if (T <= tcap && std::find(cand.begin(), cand.end(), (int)T) == cand.end()) cand.push_back((int)T);
+  };
+  for (int64_t T = tmin; T <= tcap; T *= 2) add(T);
+  for (int t = 1; t <= maxc / tmin; t = t < 4 ? t + 1 : t + t / 2) add(maxc / t);
+  std::sort(cand.begin(), cand.end());
+  std::vector<const fs1_problem*> srt(ps);
+  auto cost = [](const fs1_problem* p) { return (double)npoints(*p) * (double)std::max<int64_t>(1, p->itr_max); };
+  std::stable_sort(srt.begin(), srt.end(), [&](const fs1_problem* x, const fs1_problem* y) { return cost(x) > cost(y); });
+  const size_t m = std::min(srt.size(), (size_t)std::max(1, maxc / tmin));
+  std::vector<fs1_problem> trial(m);
+  std::vector<const fs1_problem*> tp(m);
+  for (size_t i = 0; i < m; ++i) {
+    trial[i] = *srt[i];
+    trial[i].itr_max = std::max<int64_t>(1, std::min<int64_t>(srt[i]->itr_max, h->cfg.trial_iters));
+    trial[i].tol = 0.0;
+    trial[i].f_out = nullptr;
+    trial[i].g_out = nullptr;
+    tp[i] = &trial[i];
+  }
+  int best_T = 0;
+  double best_rate = 0.0;
+  h->tuning = true;
+  fs1_status st = FS1_OK;
+  for (const int T : cand) {
+    h->force_T = T;
+    std::vector<PairResult> r;
+    Geometry g{0, 0};
+    float tms = 0.f, t2 = 0.f;
+    // two runs, the faster one counts (the first also warms caches and clocks)
+    if ((st = run_group(h, kind, 0, tp, r, g, &tms, true)) != FS1_OK) break;
+    if ((st = run_group(h, kind, 0, tp, r, g, &t2, true)) != FS1_OK) break;
+    tms = std::min(tms, t2);
+    double work = 0.0;
+    for (size_t i = 0; i < m; ++i)
+      if (r[i].status == FS1_OK || r[i].status == FS1_ENOTCONV) work += (double)npoints(*tp[i]) * (double)r[i].iters;
+    const double rate = tms > 0.f ? work / tms : 0.0;
+    if (rate > best_rate) {
+      best_rate = rate;
+      best_T = T;
+    }
+  }
+  h->tuning = false;
+  h->force_T = 0;
+  if (st != FS1_OK) return st;
+  h->tuned[key] = best_T;   // 0: no trial ran; the fixed heuristic stays
+  if (const char* path = getenv("FS1_AUTOTUNE_CACHE")) {
+    if (FILE* f = fopen(path, "a")) {
+      fprintf(f, "%s %d\n", key.c_str(), best_T);
+      fclose(f);
+    }
+  }
+  return FS1_OK;
+}
+
+// Launch signature of a 1D call: the sizes, workspace offsets and kernel
+// arguments a captured graph bakes in.  The header's contents (descriptors,
+// plan) are data copied from pinned memory on every replay.
+std::string graph_key(int kind, int mode, int in_f32, int count, int grid, int T, int teams, int nclass,
+                      size_t nslots, size_t hdr, bool validate, long long spin_cap) {
+  char buf[192];
+  snprintf(buf, sizeof buf, "%d.%d.%d.%d.%d.%d.%d.%d.%zu.%zu.%d.%lld", kind, mode, in_f32, count, grid, T, teams,
+           nclass, nslots, hdr, (int)validate, spin_cap);
+  return buf;
+}
+
+// Run one group (same kind and input dtype; all 1D or all 2D; device-located).
+//
+// Workspace layout:
+//   header   descriptors | initial results | plan | tickets | counters | aborts
+//            (one host-to-device copy from its pinned mirror)
+//   valid    per-pair input-check flags (written by the check kernel)
+//   slots    generic | compact exchange slots (one memset)
+//   2D       per-image state of the 2D solver
+// A 1D call is: header copy, slot memset, input check, team kernel, result
+// copy, and one stream synchronisation; the team kernel skips (and reports
+// FS1_EINVAL for) pairs whose check failed.  From the second call with the
+// same launch signature on, that sequence is a replayed CUDA graph.
 fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const fs1_problem*>& ps,
                      std::vector<PairResult>& res, Geometry& geo, float* ms, bool validate) {
   const int count = (int)ps.size();
@@ -303,28 +517,35 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
   } else if ((st = choose_geometry(h, kind, ps, &geo)) != FS1_OK) {
     return st;
   }
-  Plan plan;
   const bool planned = !two_d && mode == 0;
+  if (planned && h->cfg.autotune && h->cfg.team_size <= 0 && !h->tuning) {
+    const int maxc = max_coresident_ctas(kind);
+    const std::string key = tune_key(h, kind, ps, maxc);
+    if (!key.empty() && !h->tuned.count(key) && (st = autotune(h, kind, ps, key, maxc)) != FS1_OK) return st;
+  }
+  Plan plan;
   if (planned && (st = plan_teams(h, kind, ps, &plan)) != FS1_OK) return st;
   const int T = two_d ? 1 : (planned ? plan.max_T : geo.team_size);
   const int teams = two_d ? 1 : (planned ? plan.num_teams : geo.num_teams);
-  const size_t nslots = planned ? (size_t)plan.slots : (size_t)teams * 2 * T;
+  const size_t nslots = two_d ? 0 : (planned ? (size_t)plan.slots : (size_t)teams * 2 * T);
   const int in_f32 = ps[0]->dtype == FS1_FP32;
+  const int nclass = planned ? (int)plan.class_T.size() : 0;
+  const int pgrid = planned ? plan.grid : 0;
+  // plan arrays: cta_team, cta_rank [grid]; team_T, team_slot, team_class
+  // [teams]; class_off [nc + 1]; order [count]; class_next [nc]
+  const size_t plan_ints = planned ? (size_t)2 * pgrid + 3 * teams + (nclass + 1) + count + nclass : 0;
   size_t off = 0;
   const size_t o_desc = off; off = align_up(off + sizeof(PairDesc) * count, 256);
   const size_t o_res = off;  off = align_up(off + sizeof(PairResult) * count, 256);
-  const size_t o_val = off;  off = align_up(off + sizeof(ValOut) * count, 256);
-  const size_t o_slot = off; off = align_up(off + sizeof(Slot) * nslots, 256);
-  const size_t o_cslot = off; off = align_up(off + 128 * nslots, 256);
-  const size_t o_ctr = off;  off = align_up(off + sizeof(unsigned long long) * teams, 256);
-  const size_t o_abt = off;  off = align_up(off + sizeof(int) * teams, 256);
-  // plan arrays: cta_team, cta_rank [grid]; team_T, team_slot, team_class
-  // [teams]; class_off [nc + 1]; order [count]; class_next [nc]
-  const int nclass = planned ? (int)plan.class_T.size() : 0;
-  const int pgrid = planned ? plan.grid : 0;
-  const size_t plan_ints = planned ? (size_t)2 * pgrid + 3 * teams + (nclass + 1) + count + nclass : 0;
   const size_t o_plan = off; off = align_up(off + sizeof(int) * plan_ints, 256);
   const size_t o_tick = off; off = align_up(off + sizeof(unsigned long long) * (planned ? teams : 0), 256);
+  const size_t o_ctr = off;  off = align_up(off + sizeof(unsigned long long) * teams, 256);
+  const size_t o_abt = off;  off = align_up(off + sizeof(int) * teams, 256);
+  const size_t hdr = off;
+  const size_t o_val = off;  off = align_up(off + sizeof(int) * count, 256);
+  const size_t o_slot = off; off = align_up(off + sizeof(Slot) * nslots, 256);
+  off = align_up(off + 128 * nslots, 256);
+  const size_t slot_end = off;
   std::vector<PairDesc> desc(count);
   for (int i = 0; i < count; ++i) {
     const fs1_problem& p = *ps[i];
@@ -348,113 +569,173 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
   const size_t o_2d = off;
   if (two_d) off = align_up(off + solve2d_workspace(desc.data(), count), 256);
   if ((st = ensure_ws(h, off)) != FS1_OK) return st;
+  if ((st = ensure_pinned(h, &h->hdr, &h->hdr_bytes, hdr)) != FS1_OK) return st;
+  if ((st = ensure_pinned(h, &h->hres, &h->hres_bytes, sizeof(PairResult) * count + sizeof(int) * count)) !=
+      FS1_OK)
+    return st;
   char* ws = (char*)h->ws;
 
-  std::vector<PairResult> init(count, PairResult{NAN, NAN, 0, FS1_ETIMEOUT, 0});
-  cudaError_t e;
-  if ((e = cudaMemcpyAsync(ws + o_desc, desc.data(), sizeof(PairDesc) * count, cudaMemcpyHostToDevice,
-                           h->stream)) != cudaSuccess)
-    return cuda_fail(e, "descriptor copy");
-  if ((e = cudaMemcpyAsync(ws + o_res, init.data(), sizeof(PairResult) * count, cudaMemcpyHostToDevice,
-                           h->stream)) != cudaSuccess)
-    return cuda_fail(e, "result init");
-  cudaMemsetAsync(ws + o_slot, 0, sizeof(Slot) * nslots, h->stream);
-  cudaMemsetAsync(ws + o_cslot, 0, 128 * nslots, h->stream);
-  std::vector<int> pints;
+  // header image (nothing of ours is in flight: every call ends synchronised)
+  char* hb = (char*)h->hdr;
+  memset(hb, 0, hdr);
+  memcpy(hb + o_desc, desc.data(), sizeof(PairDesc) * count);
+  PairResult* r0 = (PairResult*)(hb + o_res);
+  for (int i = 0; i < count; ++i) r0[i] = PairResult{NAN, NAN, 0, FS1_ETIMEOUT, 0};
   if (planned) {
-    pints.reserve(plan_ints);
-    pints.insert(pints.end(), plan.cta_team.begin(), plan.cta_team.end());
-    pints.insert(pints.end(), plan.cta_rank.begin(), plan.cta_rank.end());
-    pints.insert(pints.end(), plan.team_T.begin(), plan.team_T.end());
-    pints.insert(pints.end(), plan.team_slot.begin(), plan.team_slot.end());
-    pints.insert(pints.end(), plan.team_class.begin(), plan.team_class.end());
-    pints.insert(pints.end(), plan.class_off.begin(), plan.class_off.end());
-    pints.insert(pints.end(), plan.order.begin(), plan.order.end());
-    pints.insert(pints.end(), (size_t)nclass, 0);   // class_next
-    if ((e = cudaMemcpyAsync(ws + o_plan, pints.data(), sizeof(int) * pints.size(), cudaMemcpyHostToDevice,
-                             h->stream)) != cudaSuccess)
-      return cuda_fail(e, "plan copy");
-    cudaMemsetAsync(ws + o_tick, 0, sizeof(unsigned long long) * teams, h->stream);
-  }
-  cudaMemsetAsync(ws + o_ctr, 0, sizeof(unsigned long long) * teams, h->stream);
-  cudaMemsetAsync(ws + o_abt, 0, sizeof(int) * teams, h->stream);
-
-  std::vector<int> bad(count, 0);
-  if (validate) {
-    validate_kernel<<<count, 256, 0, h->stream>>>((const PairDesc*)(ws + o_desc), in_f32,
-                                                  (ValOut*)(ws + o_val));
-    g_launches.fetch_add(1);
-    std::vector<ValOut> vo(count);
-    if ((e = cudaMemcpyAsync(vo.data(), ws + o_val, sizeof(ValOut) * count, cudaMemcpyDeviceToHost,
-                             h->stream)) != cudaSuccess)
-      return cuda_fail(e, "validation copy");
-    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(e, "validation");
-    bool anybad = false;
-    for (int i = 0; i < count; ++i) {
-      const double sa = vo[i].sa, sb = vo[i].sb;
-      if (vo[i].bad || !(sa > 0.0) || !(sb > 0.0) || std::fabs(sa - sb) > 1e-6 * std::max(sa, sb)) {
-        bad[i] = 1;
-        anybad = true;
-      }
+    int* pi = (int*)(hb + o_plan);
+    for (const std::vector<int>* v : {&plan.cta_team, &plan.cta_rank, &plan.team_T, &plan.team_slot,
+                                      &plan.team_class, &plan.class_off, &plan.order}) {
+      std::copy(v->begin(), v->end(), pi);
+      pi += v->size();
     }
-    if (anybad) {
-      // solve only the valid ones
+    // class_next stays zero
+  }
+  PairResult* hres = (PairResult*)h->hres;
+  cudaError_t e;
+
+  if (two_d) {
+    if ((e = cudaMemcpyAsync(ws, hb, hdr, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
+      return cuda_fail(e, "header copy");
+    if (validate) {
+      int* hval = (int*)(hres + count);
+      validate_kernel<<<count, 256, 0, h->stream>>>((const PairDesc*)(ws + o_desc), in_f32, (int*)(ws + o_val));
+      g_launches.fetch_add(1);
+      if ((e = cudaMemcpyAsync(hval, ws + o_val, sizeof(int) * count, cudaMemcpyDeviceToHost, h->stream)) !=
+              cudaSuccess ||
+          (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
+        return cuda_fail(e, "input check");
       std::vector<const fs1_problem*> good;
       std::vector<int> idx;
       for (int i = 0; i < count; ++i)
-        if (!bad[i]) { good.push_back(ps[i]); idx.push_back(i); }
-      res.assign(count, PairResult{NAN, NAN, 0, FS1_EINVAL, 0});
-      if (good.empty()) return FS1_OK;
-      std::vector<PairResult> sub;
-      fs1_status s2 = run_group(h, kind, mode, good, sub, geo, ms, false);
-      if (s2 != FS1_OK) return s2;
-      for (size_t j = 0; j < idx.size(); ++j) res[idx[j]] = sub[j];
-      return FS1_OK;
+        if (hval[i]) {
+          good.push_back(ps[i]);
+          idx.push_back(i);
+        }
+      if ((int)good.size() < count) {
+        res.assign(count, PairResult{NAN, NAN, 0, FS1_EINVAL, 0});
+        if (good.empty()) return FS1_OK;
+        std::vector<PairResult> sub;
+        if ((st = run_group(h, kind, mode, good, sub, geo, ms, false)) != FS1_OK) return st;
+        for (size_t j = 0; j < idx.size(); ++j) res[idx[j]] = sub[j];
+        return FS1_OK;
+      }
     }
+    cudaEventRecord(h->ev0, h->stream);
+    const int ls = launch_solve_2d(desc.data(), count, in_f32, (PairResult*)(ws + o_res), ws + o_2d,
+                                   h->ws_bytes - o_2d, h->cfg.spin_cap, h->stream);
+    if (ls != FS1_OK) return (fs1_status)ls;
+    g_launches.fetch_add(1);
+    cudaEventRecord(h->ev1, h->stream);
+    if ((e = cudaMemcpyAsync(hres, ws + o_res, sizeof(PairResult) * count, cudaMemcpyDeviceToHost, h->stream)) !=
+        cudaSuccess)
+      return cuda_fail(e, "result copy");
+  } else {
+    TeamLaunch L{};
+    L.pairs = (const PairDesc*)(ws + o_desc);
+    L.results = (PairResult*)(ws + o_res);
+    L.order = nullptr;
+    L.num_pairs = count;
+    L.team_size = T;
+    L.num_teams = teams;
+    L.in_f32 = in_f32;
+    L.slots = (Slot*)(ws + o_slot);
+    L.cslots = (unsigned long long*)(ws + o_slot + align_up(sizeof(Slot) * nslots, 256));
+    L.counters = (unsigned long long*)(ws + o_ctr);
+    L.abort_flags = (int*)(ws + o_abt);
+    L.valid = validate ? (const int*)(ws + o_val) : nullptr;
+    if (planned) {
+      int* pi = (int*)(ws + o_plan);
+      L.grid = pgrid;
+      L.cta_team = pi;
+      L.cta_rank = pi + pgrid;
+      L.team_T = pi + 2 * pgrid;
+      L.team_slot = pi + 2 * pgrid + teams;
+      L.team_class = pi + 2 * pgrid + 2 * teams;
+      L.class_off = pi + 2 * pgrid + 3 * teams;
+      L.order = pi + 2 * pgrid + 3 * teams + nclass + 1;
+      L.class_next = pi + 2 * pgrid + 3 * teams + nclass + 1 + count;
+      L.tickets = (unsigned long long*)(ws + o_tick);
+    }
+    L.spin_cap = h->cfg.spin_cap;
+    // the call's stream work, issued on s (captured when s is the capture stream)
+    auto issue = [&](cudaStream_t s, bool capturing) -> fs1_status {
+      cudaError_t ee;
+      if ((ee = cudaMemcpyAsync(ws, hb, hdr, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cuda_fail(ee, "header copy");
+      if (nslots && (ee = cudaMemsetAsync(ws + o_slot, 0, slot_end - o_slot, s)) != cudaSuccess)
+        return cuda_fail(ee, "slot reset");
+      if (validate)
+        validate_kernel<<<count, 256, 0, s>>>((const PairDesc*)(ws + o_desc), in_f32, (int*)(ws + o_val));
+      if (capturing)
+        cudaEventRecordWithFlags(h->ev0, s, cudaEventRecordExternal);
+      else
+        cudaEventRecord(h->ev0, s);
+      const int ls = launch_team_1d(kind | (mode << 8), L, s);
+      if (ls != FS1_OK) return (fs1_status)ls;
+      if (capturing)
+        cudaEventRecordWithFlags(h->ev1, s, cudaEventRecordExternal);
+      else
+        cudaEventRecord(h->ev1, s);
+      if ((ee = cudaMemcpyAsync(hres, ws + o_res, sizeof(PairResult) * count, cudaMemcpyDeviceToHost, s)) !=
+          cudaSuccess)
+        return cuda_fail(ee, "result copy");
+      return FS1_OK;
+    };
+    const bool graphs = h->cfg.use_graph && !h->graphs_off && !h->tuning;
+    const std::string gkey =
+        graphs ? graph_key(kind, mode, in_f32, count, planned ? pgrid : teams * T, T, teams, nclass, nslots, hdr,
+                           validate, h->cfg.spin_cap)
+               : std::string();
+    cudaGraphExec_t exec = nullptr;
+    for (size_t k = 0; graphs && k < h->graphs.size(); ++k)
+      if (h->graphs[k].key == gkey) {
+        exec = h->graphs[k].exec;
+        std::rotate(h->graphs.begin(), h->graphs.begin() + k, h->graphs.begin() + k + 1);   // to the front
+        break;
+      }
+    if (!exec && graphs && h->pending == gkey) {
+      // second call with this signature: capture it
+      cudaGraph_t g = nullptr;
+      fs1_status cs = FS1_OK;
+      if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        cs = issue(h->cap, true);
+        const cudaError_t ce = cudaStreamEndCapture(h->cap, &g);
+        if (cs == FS1_OK && ce == cudaSuccess && g &&
+            cudaGraphInstantiate(&exec, g, 0) == cudaSuccess) {
+          h->graphs.insert(h->graphs.begin(), GraphEntry{gkey, exec});
+          if (h->graphs.size() > 4) {
+            cudaGraphExecDestroy(h->graphs.back().exec);
+            h->graphs.pop_back();
+          }
+        } else {
+          exec = nullptr;
+        }
+        if (g) cudaGraphDestroy(g);
+      }
+      if (!exec) {
+        cudaGetLastError();
+        h->graphs_off = true;   // stay eager on this handle
+        fprintf(stderr, "fs1: graph capture unavailable, launching directly\n");
+      }
+      h->pending.clear();
+      if (exec) ++h->captures;
+    }
+    if (exec) {
+      if ((e = cudaGraphLaunch(exec, h->stream)) != cudaSuccess) return cuda_fail(e, "graph launch");
+      ++h->replays;
+    } else {
+      if ((st = issue(h->stream, false)) != FS1_OK) return st;
+      if (graphs) h->pending = gkey;
+    }
+    g_launches.fetch_add(validate ? 2 : 1);
+    if (h->tuning) h->trial_launches += 1;
   }
-
-  TeamLaunch L{};
-  L.pairs = (const PairDesc*)(ws + o_desc);
-  L.results = (PairResult*)(ws + o_res);
-  L.order = nullptr;
-  L.num_pairs = count;
-  L.team_size = T;
-  L.num_teams = teams;
-  L.in_f32 = in_f32;
-  L.slots = (Slot*)(ws + o_slot);
-  L.cslots = (unsigned long long*)(ws + o_cslot);
-  L.counters = (unsigned long long*)(ws + o_ctr);
-  L.abort_flags = (int*)(ws + o_abt);
-  if (planned) {
-    int* pi = (int*)(ws + o_plan);
-    L.grid = pgrid;
-    L.cta_team = pi;
-    L.cta_rank = pi + pgrid;
-    L.team_T = pi + 2 * pgrid;
-    L.team_slot = pi + 2 * pgrid + teams;
-    L.team_class = pi + 2 * pgrid + 2 * teams;
-    L.class_off = pi + 2 * pgrid + 3 * teams;
-    L.order = pi + 2 * pgrid + 3 * teams + nclass + 1;
-    L.class_next = pi + 2 * pgrid + 3 * teams + nclass + 1 + count;
-    L.tickets = (unsigned long long*)(ws + o_tick);
-  }
-  L.spin_cap = h->cfg.spin_cap;
-  cudaEventRecord(h->ev0, h->stream);
-  int ls;
-  if (two_d)
-    ls = launch_solve_2d(desc.data(), count, in_f32, (PairResult*)(ws + o_res), ws + o_2d, h->ws_bytes - o_2d,
-                         h->cfg.spin_cap, h->stream);
-  else
-    ls = launch_team_1d(kind | (mode << 8), L, h->stream);
-  if (ls != FS1_OK) return (fs1_status)ls;
-  g_launches.fetch_add(1);
-  cudaEventRecord(h->ev1, h->stream);
-  res.resize(count);
-  if ((e = cudaMemcpyAsync(res.data(), ws + o_res, sizeof(PairResult) * count, cudaMemcpyDeviceToHost,
-                           h->stream)) != cudaSuccess)
-    return cuda_fail(e, "result copy");
   if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(e, "solve");
-  cudaEventElapsedTime(ms, h->ev0, h->ev1);
+  if (cudaEventElapsedTime(ms, h->ev0, h->ev1) != cudaSuccess) {
+    cudaGetLastError();
+    *ms = NAN;
+  }
+  res.assign(hres, hres + count);
   if (planned) geo.team_size = plan.max_T;
   return FS1_OK;
 }
@@ -484,6 +765,9 @@ fs1_status fs1_config_default(fs1_config* cfg) {
   cfg->spin_cap = 1ll << 22;
   cfg->hbm_budget = 0;
   cfg->stream = nullptr;
+  cfg->autotune = 1;
+  cfg->trial_iters = 48;
+  cfg->use_graph = 1;
   return FS1_OK;
 }
 
@@ -497,16 +781,32 @@ fs1_status fs1_create(const fs1_config* cfg, fs1_handle** out) {
   if (c.variant == FS1_VARIANT_LOG && c.precision != FS1_FP32) return FS1_EUNSUPPORTED;
   if (c.check_every != 1) return FS1_EUNSUPPORTED;
   if (c.spin_cap <= 0) c.spin_cap = 1ll << 22;
+  if (c.trial_iters <= 0) c.trial_iters = 48;
   fs1_handle* h = new (std::nothrow) fs1_handle;
   if (!h) return FS1_ENOMEM;
   h->cfg = c;
   cudaError_t e = cudaGetDevice(&h->device);
   if (e != cudaSuccess) { delete h; return cuda_fail(e, "cudaGetDevice"); }
   cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+  int ccmaj = 0, ccmin = 0;
+  cudaDeviceGetAttribute(&ccmaj, cudaDevAttrComputeCapabilityMajor, h->device);
+  cudaDeviceGetAttribute(&ccmin, cudaDevAttrComputeCapabilityMinor, h->device);
+  h->cc = 10 * ccmaj + ccmin;
   h->stream = (cudaStream_t)c.stream;
-  if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
-    delete h;
+  if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    fs1_destroy(h);
     return FS1_ECUDA;
+  }
+  if (c.autotune) {
+    if (const char* path = getenv("FS1_AUTOTUNE_CACHE")) {
+      if (FILE* f = fopen(path, "r")) {
+        char key[128];
+        int t = 0;
+        while (fscanf(f, "%127s %d", key, &t) == 2) h->tuned[key] = t;
+        fclose(f);
+      }
+    }
   }
   *out = h;
   return FS1_OK;
@@ -514,14 +814,27 @@ fs1_status fs1_create(const fs1_config* cfg, fs1_handle** out) {
 
 void fs1_destroy(fs1_handle* h) {
   if (!h) return;
-  if (h->ws || h->stage) {
+  if (h->ws || h->stage || h->hdr || h->hres) {
     cudaStreamSynchronize(h->stream);
     if (h->ws) cudaFree(h->ws);
     if (h->stage) cudaFree(h->stage);
+    if (h->hdr) cudaFreeHost(h->hdr);
+    if (h->hres) cudaFreeHost(h->hres);
   }
+  drop_graphs(h);
+  if (h->cap) cudaStreamDestroy(h->cap);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   delete h;
+}
+
+fs1_status fs1_handle_stats(const fs1_handle* h, int64_t* out) {
+  if (!h || !out) return FS1_EINVAL;
+  out[0] = h->replays;
+  out[1] = h->captures;
+  out[2] = (int64_t)h->tuned.size();
+  out[3] = h->trial_launches;
+  return FS1_OK;
 }
 
 fs1_status fs1_solve_batch(fs1_handle* h, const fs1_problem* probs, int64_t count, double* w1_out,

@@ -63,7 +63,12 @@ struct TeamLaunch {
   const int* class_off;            // [nclass + 1] offsets of each class's pairs in `order`
   int* class_next;                 // [nclass] queue heads (zeroed per launch)
   unsigned long long* tickets;     // [num_teams] pair broadcast words (zeroed per launch)
+  const int* valid;                // [num_pairs] 0: the pair failed the input check and is
+                                   // reported FS1_EINVAL without solving; null: all valid
 };
+
+// Largest team: the team reduction stages one slot per CTA in shared memory.
+constexpr int kMaxTeamCtas = 256;
 
 enum KernelKind {
   KK_PLAIN_F64 = 0,   // plain FS-1 (Algorithm 1 as written), FP64

@@ -60,7 +60,6 @@ struct DecayTables {
   int narrow;      // 1 if c * 32 * Eeff <= 40 (a warp's decay fits one FP32 frame)
 };
 
-constexpr int kMaxTeamCtas = 256;   // the team reduction serves up to 256 CTAs
 
 // where a CTA sits: its team, rank, team size and the team's slots
 struct TeamCtx {
@@ -519,6 +518,11 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
       if (item >= L.class_off[cls + 1] - L.class_off[cls]) break;
       pid = L.order[L.class_off[cls] + item];
     }
+    if (L.valid != nullptr && !L.valid[pid]) {
+      if (rank == 0 && tid == 0) L.results[pid] = PairResult{NAN, NAN, 0, FS1_EINVAL, 0};
+      __syncthreads();   // sm_item is rewritten by the next ticket
+      continue;
+    }
     const PairDesc P = L.pairs[pid];
     const int64_t N = P.n;
     const double c = P.h_fast / P.eps;
@@ -605,18 +609,22 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
     }
     __syncthreads();
 
-    // aggregates of the initial u
+    // aggregates of the initial u, in the same operation order as the
+    // u-half's aggregates: a warm start from the potentials of a run stopped
+    // after l iterations then reproduces that run's carries exactly (the
+    // frames differ by a power of two, which scales every rounding exactly)
     PT cf, cb;
     {
-      V r = 0, s = 0;
-#pragma unroll
-      for (int k = 0; k < E; ++k)
-        if (k < Eeff) r = lam * r + xu[k];
+      V af = 0, ab = 0, pw = 1;
 #pragma unroll
       for (int k = E - 1; k >= 0; --k)
-        if (k < Eeff) s = lam * (s + xu[k]);
+        if (k < Eeff) {
+          af = af + pw * xu[k];
+          pw = pw * lam;
+          ab = lam * (ab + xu[k]);
+        }
       int dec;
-      if (!exchange<OpP, C>(L, tc, epoch, xc, c_from(r, fu, C{}), c_from(s, fu, C{}), (V)0, Eeff, tb, XP,
+      if (!exchange<OpP, C>(L, tc, epoch, xc, c_from(af, fu, C{}), c_from(ab, fu, C{}), (V)0, Eeff, tb, XP,
                             cf, cb, 0.f, 0.f, dec, nullptr, nullptr, compact))
         goto timed_out;
     }
@@ -835,8 +843,14 @@ template <class V, class C, int E>
 static cudaError_t launch_kind(const TeamLaunch& L, int mode, cudaStream_t st) {
   auto kfn = fs1_team_kernel<V, C, E>;
   const size_t smem = 3 * sizeof(V) * (size_t)E * kThreads;
-  cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  // under stream capture the attribute was already set by an eager launch of
+  // the same signature (graphs are captured on a signature's second call)
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cs);
+  if (cs == cudaStreamCaptureStatusNone) {
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   // heterogeneous launches carry their grid; team_size is then the largest team
   const int grid = L.grid > 0 ? L.grid : L.num_teams * L.team_size;
   if (L.team_size > 1) {

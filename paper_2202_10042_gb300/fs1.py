@@ -31,7 +31,8 @@ FS1_MEM_DEVICE, FS1_MEM_HOST = 0, 1
 class fs1_config(Structure):
     _fields_ = [("variant", c_int), ("precision", c_int), ("check_every", c_int),
                 ("team_size", c_int), ("spin_cap", c_longlong), ("hbm_budget", c_size_t),
-                ("stream", c_void_p)]
+                ("stream", c_void_p), ("autotune", c_int), ("trial_iters", c_int),
+                ("use_graph", c_int)]
 
 
 class fs1_problem(Structure):
@@ -49,7 +50,7 @@ class fs1_info(Structure):
 
 EXPORTED = ["fs1_config_default", "fs1_create", "fs1_w1", "fs1_solve_batch",
             "fs1_kernel_apply_log", "fs1_destroy", "fs1_status_string", "fs1_version",
-            "fs1_launch_count", "fs1_w1_noalloc"]
+            "fs1_launch_count", "fs1_w1_noalloc", "fs1_handle_stats"]
 
 _lib = None
 
@@ -85,6 +86,8 @@ def load(path: str = LIB_PATH):
     L.fs1_w1_noalloc.argtypes = [POINTER(fs1_config), POINTER(fs1_problem), POINTER(c_double),
                                  POINTER(fs1_info)]
     L.fs1_w1_noalloc.restype = c_int
+    L.fs1_handle_stats.argtypes = [c_void_p, POINTER(c_int64)]
+    L.fs1_handle_stats.restype = c_int
     _lib = L
     return L
 
@@ -141,6 +144,13 @@ def fs1_launch_count() -> int:
     return int(load().fs1_launch_count())
 
 
+def fs1_handle_stats(h) -> dict:
+    out = (c_int64 * 4)()
+    _check(load().fs1_handle_stats(h, out))
+    return {"graph_replays": out[0], "graphs_captured": out[1], "tuned_classes": out[2],
+            "trial_launches": out[3]}
+
+
 def fs1_w1_noalloc(cfg: Optional[fs1_config], prob: fs1_problem):
     """One device-located 1D problem through the allocation-free entry point."""
     w = c_double()
@@ -162,7 +172,8 @@ class Solver:
     `precision` "fp32" or "fp64" (plain only)."""
 
     def __init__(self, variant: str = "log", precision: str = "fp32", team_size: int = 0,
-                 stream=None, spin_cap: int = 0, hbm_budget: int = 0):
+                 stream=None, spin_cap: int = 0, hbm_budget: int = 0, autotune: bool = True,
+                 use_graph: bool = True, trial_iters: int = 0):
         cfg = fs1_config_default()
         cfg.variant = FS1_VARIANT_LOG if variant == "log" else FS1_VARIANT_PLAIN
         cfg.precision = FS1_FP32 if precision == "fp32" else FS1_FP64
@@ -170,6 +181,10 @@ class Solver:
         if spin_cap:
             cfg.spin_cap = int(spin_cap)
         cfg.hbm_budget = int(hbm_budget)
+        cfg.autotune = 1 if autotune else 0
+        cfg.use_graph = 1 if use_graph else 0
+        if trial_iters:
+            cfg.trial_iters = int(trial_iters)
         if stream is not None:
             cfg.stream = c_void_p(int(stream))
         self.cfg = cfg
@@ -223,3 +238,6 @@ class Solver:
     def solve(self, probs: Sequence[fs1_problem]):
         st, w, infos = fs1_solve_batch(self.h, probs)
         return st, w, infos
+
+    def stats(self) -> dict:
+        return fs1_handle_stats(self.h)

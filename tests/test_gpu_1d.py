@@ -205,11 +205,12 @@ def test_host_location_equals_device(fs1mod, torch_cuda):
     assert w1[0] == w2[0] and i1[0].iters == i2[0].iters
 
 
-def test_warm_start_resume_bit_identical(fs1mod, torch_cuda):
+@pytest.mark.parametrize("team", [0, 4, 16, 79])   # 20, 5 and 1 points per thread; 0: autotuned
+def test_warm_start_resume_bit_identical(fs1mod, torch_cuda, team):
     torch = torch_cuda
     p = inputs.workload2(11, n=40000, eps=1e-3, itr_max=60)
     ta, tb = _dev(torch, p.a), _dev(torch, p.b)
-    s = fs1mod.Solver("log", "fp32")
+    s = fs1mod.Solver("log", "fp32", team_size=team)
     st, w_full, i_full = s.solve([fs1mod.Solver.problem(ta, tb, p.h[0], p.eps, 0.0, 60)])
     f = torch.empty(p.a.size, dtype=torch.float64, device="cuda")
     g = torch.empty_like(f)

@@ -37,7 +37,9 @@ def test_noalloc_matches_w1_twice(env, variant, prec, n, eps, itr, tol):
     a = torch.tensor(p.a, dtype=torch.float64, device="cuda")
     b = torch.tensor(p.b, dtype=torch.float64, device="cuda")
     prob = fs1.Solver.problem(a, b, p.h[0], p.eps, p.tol, p.itr_max)
-    s = fs1.Solver(variant, prec)
+    # the allocation-free path has no handle and so no autotuner table: compare
+    # with fs1_w1 at the same (heuristic) team size
+    s = fs1.Solver(variant, prec, autotune=False)
     st, w_ref, info_ref = fs1.fs1_w1(s.h, prob)
     cfg = s.cfg
     s.close()
