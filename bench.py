@@ -1,22 +1,34 @@
 """Benchmark of the FS-1 hot path on GB300.
 
-Workload (one "step"): a batch of 256 independent 1D pairs, N = 2^20 grid points
-each (h = 2^-20), eps = 1e-4, 3-component Gaussian-mixture histograms with a
-1e-6 floor, stabilised FP32 iteration with FP64 reductions, run to a marginal
-L1 error of 1e-6 or 5000 iterations.  Every step solves the whole batch through
-the library's C ABI (fs1_solve_batch).
+Workloads (one "step" solves the whole batch through the library's C ABI,
+fs1_solve_batch; --workload picks one, 2 is the default and the headline):
+  1  one 1D pair, N = 1000 (h = 1e-3), eps = 1e-2, 2-component Gaussian
+     mixtures + 1e-4 floor, plain FS-1 (Algorithm 1 as written) in FP64,
+     1000 iterations
+  2  256 1D pairs, N = 2^20 (h = 2^-20), eps = 1e-4, 3-component Gaussian
+     mixtures + 1e-6 floor, stabilised FP32 iteration with FP64 reductions,
+     marginal L1 error 1e-6 or 5000 iterations
+  3  4096 uneven 1D pairs, N log-uniform in [256, 65536], eps log-uniform in
+     [1e-3, 1e-1], Dirichlet(1) weights smoothed by a width-5 box + 1e-6
+     floor, stabilised FP32, one persistent launch
+  4  64 2D pairs on a 512 x 512 grid (h = 1/512), eps = 1e-3, images of 1-5
+     anisotropic Gaussian blobs + 1e-7 floor, stabilised FP32 (Algorithm 2)
+The serving workload is measured by `python -m paper_2202_10042_gb300.serve`.
 
-Metric: N*iterations per second (sum over pairs of N * iterations / wall time).
+Metric: N*iterations per second (sum over pairs of grid points x iterations /
+device time of the steps).
 
 Arms
   default               the CUDA library, inputs resident in HBM (value), plus an
-                        end-to-end pass from pinned host buffers (e2e).
+                        end-to-end pass from pinned host buffers (e2e), and the
+                        same pairs solved one fs1_w1 call each on a sample
+                        (one_pair_per_launch).
   --impl reference      the CPU FP64 oracle (the paper's sequential FS-1
                         recurrences in plain C) on the host cores, on a bounded
                         sample of the same workload.
 
 Multi-GPU (torchrun): pairs are independent, so every rank solves its own batch
-of 256 pairs (weak scaling); the only collective is the barrier and max-reduce
+(weak scaling); the only collectives are the barrier and the max / sum reduce
 of the timing.
 """
 from __future__ import annotations
@@ -41,10 +53,32 @@ if ROOT not in sys.path:
 
 from paper_2202_10042_gb300 import inputs  # noqa: E402
 
-WORKLOAD = dict(name="fs1_1d_log_fp32_batch256_n2^20_eps1e-4", n=1 << 20, pairs=256, eps=1e-4,
-                tol=1e-6, itr_max=5000)
 METRIC = "N*iters/s"
-BYTES_PER_NIT = 28.0  # algorithmic HBM bytes per N*iteration of a streaming realisation
+L2_BYTES = 129 << 20
+
+# Streaming-equivalent HBM bytes per N*iteration: what a realisation that
+# streams the state through HBM would move.  1D FP32: the v-half reads u, b and
+# the accepted v and writes v (16 B), the u-half reads v, a and writes u
+# (12 B); FP64 doubles it; 2D adds, per half-step, the write and read of the
+# fast-axis partial sums (8 B).
+WORKLOADS = {
+    1: dict(name="fs1_1d_plain_fp64_n1000_eps1e-2_it1000", pairs=1, variant="plain", precision="fp64",
+            dtype="f64", bytes_per_nit=56.0, kw={}, sample_pairs=1, sample_iters=1000, solo=0),
+    2: dict(name="fs1_1d_log_fp32_batch256_n2^20_eps1e-4", pairs=256, variant="log", precision="fp32",
+            dtype="f32", bytes_per_nit=28.0, kw=dict(n=1 << 20, eps=1e-4, tol=1e-6, itr_max=5000),
+            sample_pairs=8, sample_iters=300, solo=8),
+    3: dict(name="fs1_1d_log_fp32_uneven4096_n256-65536", pairs=4096, variant="log", precision="fp32",
+            dtype="f32", bytes_per_nit=28.0, kw={}, sample_pairs=64, sample_iters=200, solo=64),
+    4: dict(name="fs1_2d_log_fp32_batch64_512x512_eps1e-3", pairs=64, variant="log", precision="fp32",
+            dtype="f32", bytes_per_nit=44.0, kw={}, sample_pairs=4, sample_iters=40, solo=4),
+}
+
+
+def gen_problem(workload: int, index: int, **over):
+    W = WORKLOADS[workload]
+    kw = dict(W["kw"])
+    kw.update({k: v for k, v in over.items() if v is not None})
+    return getattr(inputs, f"workload{workload}")(index, **kw)
 
 
 # ---------------------------------------------------------------------------
@@ -150,12 +184,9 @@ class Clocks:
 # workload construction
 # ---------------------------------------------------------------------------
 
-def make_pairs(indices, n, eps, tol, itr_max, workers=16):
-    def one(i):
-        p = inputs.workload2(i, n=n, eps=eps, tol=tol, itr_max=itr_max)
-        return p.a.astype(np.float32), p.b.astype(np.float32)
+def make_problems(workload, indices, itr_max=None, workers=16):
     with cf.ThreadPoolExecutor(max_workers=workers) as ex:
-        return list(ex.map(one, indices))
+        return list(ex.map(lambda i: gen_problem(workload, i, itr_max=itr_max), indices))
 
 
 def host_cores() -> int:
@@ -169,45 +200,52 @@ def host_cores() -> int:
 # the oracle arm (CPU)
 # ---------------------------------------------------------------------------
 
-def oracle_sample(n, eps, pairs_idx, iters, workers):
-    """Time the CPU FP64 oracle (stabilised sequential FS-1 in C) on a sample:
-    len(pairs_idx) pairs x `iters` iterations, one pair per host thread."""
+def oracle_sample(workload, pairs_idx, iters, workers):
+    """Time the CPU FP64 oracle (sequential FS-1 in C: the plain form for the
+    plain workload, the stabilised one otherwise) on a sample: the given pairs
+    x `iters` iterations with tol = 0, one pair per host thread."""
     from oracle import cref
     cref.build()
-    data = [inputs.workload2(i, n=n, eps=eps) for i in pairs_idx]
+    W = WORKLOADS[workload]
+    data = [gen_problem(workload, i) for i in pairs_idx]
+    tau = math.inf if W["variant"] == "plain" else 1e10
     t0 = time.perf_counter()
-    res = cref.solve_many([(p.a, p.b, p.h[0], p.eps, 0.0, iters) for p in data], workers=workers)
+    res = cref.solve_many([(p.a, p.b, p.h if p.ndim == 2 else p.h[0], p.eps, 0.0, iters) for p in data],
+                          workers=workers, tau=tau)
     dt = time.perf_counter() - t0
     nit = sum(p.a.size * r.iters for p, r in zip(data, res))
     return nit / dt, dt, nit
+
+
+def cpu_sample_desc(W, npairs, iters, dt=None):
+    what = f"{npairs} pair(s) of the workload x {iters} iterations (FP64 " + \
+        ("plain" if W["variant"] == "plain" else "stabilised") + " sequential FS-1, one pair per thread, tol=0)"
+    return what + (f", {dt:.1f} s" if dt is not None else "")
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
+    W = WORKLOADS[args.workload]
     cores = host_cores()
-    npairs = max(1, min(8, cores))
-    iters = 40
-    W = WORKLOAD
+    npairs = max(1, min(W["sample_pairs"], cores))
+    iters = max(1, W["sample_iters"] // 4)
     for _ in range(args.warmup):
-        oracle_sample(W["n"], W["eps"], list(range(npairs)), 5, npairs)
-    vals, t_tot, nit_tot = [], 0.0, 0
+        oracle_sample(args.workload, list(range(npairs)), max(1, iters // 8), npairs)
+    t_tot, nit_tot = 0.0, 0
     for _ in range(args.steps):
-        v, dt, nit = oracle_sample(W["n"], W["eps"], list(range(npairs)), iters, npairs)
-        vals.append(v)
+        v, dt, nit = oracle_sample(args.workload, list(range(npairs)), iters, npairs)
         t_tot += dt
         nit_tot += nit
     value = nit_tot / t_tot
-    sample = f"{npairs} pairs of the workload x {iters} iterations per step (FP64, tol=0)"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "N*iters/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * t_tot / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": W["name"], "n": W["n"], "pairs": W["pairs"], "eps": W["eps"],
-                       "tol": W["tol"], "itr_max": W["itr_max"], "parallelism": "host threads"},
+            "config": {"workload": W["name"], "pairs": W["pairs"], "parallelism": "host threads"},
             "cpu_baseline": {"value": value, "unit": "N*iters/s", "cores": npairs, "kind": "oracle",
-                             "sample": sample},
+                             "sample": cpu_sample_desc(W, npairs, iters) + " per step"},
             "e2e": {"value": value, "unit": "N*iters/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -232,62 +270,75 @@ def run_gpu(args):
     __graft_entry__.build()
     from paper_2202_10042_gb300 import fs1
 
-    W = dict(WORKLOAD)
-    if args.pairs:
-        W["pairs"] = args.pairs
-    if args.itr_max is not None:
-        W["itr_max"] = args.itr_max
-    idx = shard_pairs(W["pairs"], rank)
-    host = make_pairs(idx, W["n"], W["eps"], W["tol"], W["itr_max"])
-    h = 1.0 / W["n"]
+    W = WORKLOADS[args.workload]
+    npairs = args.pairs or W["pairs"]
+    idx = shard_pairs(npairs, rank)
+    host = make_problems(args.workload, idx, itr_max=args.itr_max)
+    tdt = torch.float64 if W["precision"] == "fp64" else torch.float32
     stream = torch.cuda.current_stream(dev)
-    solver = fs1.Solver("log", "fp32", stream=stream.cuda_stream, team_size=args.team_size,
+    solver = fs1.Solver(W["variant"], W["precision"], stream=stream.cuda_stream, team_size=args.team_size,
                         autotune=not args.no_autotune, use_graph=not args.no_graph)
 
+    def hgrid(p):
+        return tuple(p.h) if p.ndim == 2 else p.h[0]
+
     # device-resident inputs
-    dev_t = [(torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)) for a, b in host]
-    probs = [fs1.Solver.problem(a, b, h, W["eps"], W["tol"], W["itr_max"]) for a, b in dev_t]
+    dev_t = [(torch.from_numpy(p.a).to(dev, tdt), torch.from_numpy(p.b).to(dev, tdt)) for p in host]
+    probs = [fs1.Solver.problem(a, b, hgrid(p), p.eps, p.tol, p.itr_max) for p, (a, b) in zip(host, dev_t)]
     # pinned host inputs for the end-to-end pass
-    pin_t = [(torch.from_numpy(a).pin_memory(), torch.from_numpy(b).pin_memory()) for a, b in host]
-    probs_h = [fs1.Solver.problem(a, b, h, W["eps"], W["tol"], W["itr_max"]) for a, b in pin_t]
+    pin_t = [(torch.from_numpy(p.a).to(tdt).pin_memory(), torch.from_numpy(p.b).to(tdt).pin_memory())
+             for p in host]
+    probs_h = [fs1.Solver.problem(a, b, hgrid(p), p.eps, p.tol, p.itr_max) for p, (a, b) in zip(host, pin_t)]
+    in_bytes = sum(a.numel() * a.element_size() + b.numel() * b.element_size() for a, b in dev_t)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev) if in_bytes < 2 * L2_BYTES else None
     torch.cuda.synchronize()
+
+    def check(infos):
+        bad = [fs1.STATUS_NAMES.get(i.status) for i in infos if i.status not in (fs1.FS1_OK, fs1.FS1_ENOTCONV)]
+        if bad:
+            raise RuntimeError(f"solve failed: {bad[:4]}")
 
     def step(ps):
         st, w, infos = solver.solve(ps)
-        bad = [fs1.STATUS_NAMES.get(i.status) for i in infos
-               if i.status not in (fs1.FS1_OK, fs1.FS1_ENOTCONV)]
-        if bad:
-            raise RuntimeError(f"solve failed: {bad[:4]}")
+        check(infos)
         return w, infos
+
+    def nit_of(infos):
+        return sum(int(p.a.size) * int(i.iters) for p, i in zip(host, infos))
 
     for _ in range(args.warmup):
         step(probs)
 
-    # ---- timed region: device-resident inputs
+    # ---- timed region: device-resident inputs; each step between its own
+    # events on the launching stream, the L2 flush (small inputs) outside them
     barrier(world)
     torch.cuda.synchronize()
     l0 = fs1.fs1_launch_count()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     nit = 0
     kern_ms = []
     with Clocks(dev.index if dev.index is not None else 0) as clk:
-        ev0.record(stream)
-        for _ in range(args.steps):
+        for e0, e1 in evs:
+            if flush is not None:
+                flush.fill_(1.0)
+            e0.record(stream)
             w, infos = step(probs)
-            nit += sum(int(p.n[0]) * int(i.iters) for p, i in zip(probs, infos))
-            kern_ms.append(infos[0].ms)
-        ev1.record(stream)
+            e1.record(stream)
+            nit += nit_of(infos)
+            kern_ms.append(statistics.mean(i.ms for i in infos[:1]))
         torch.cuda.synchronize()
     launches = fs1.fs1_launch_count() - l0
     barrier(world)
-    ms = ev0.elapsed_time(ev1)
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
     ms_max = reduce_max(ms, world, dev)
     nit_all = reduce_sum(float(nit), world, dev)
     value = nit_all / (ms_max / 1000.0)
     iters = [int(i.iters) for i in infos]
     errs = [float(i.marginal_err) for i in infos]
+    teams = sorted({int(i.team_size) for i in infos})
     kernel_ms = statistics.mean(kern_ms)
     nit_step = nit / args.steps
+    graph = solver.stats()["graph_replays"] > 0
 
     # ---- end to end: pinned host buffers, H2D + solve + D2H each step
     barrier(world)
@@ -296,15 +347,27 @@ def run_gpu(args):
     t0 = time.perf_counter()
     e_nit = 0
     for _ in range(e_steps):
-        w, infos = step(probs_h)
-        e_nit += sum(int(p.n[0]) * int(i.iters) for p, i in zip(probs_h, infos))
+        w_h, infos_h = step(probs_h)
+        e_nit += nit_of(infos_h)
     torch.cuda.synchronize()
     e_s = reduce_max(time.perf_counter() - t0, world, dev)
     e_val = reduce_sum(float(e_nit), world, dev) / e_s
     h2d = sum(a.numel() * a.element_size() + b.numel() * b.element_size() for a, b in pin_t)
-    d2h = len(probs_h) * (32 + 24)  # per-pair result record + mass-check record
+    d2h = len(probs_h) * 32   # one result record per pair
 
-    achieved = BYTES_PER_NIT * nit_step / (kernel_ms / 1000.0) / 1e9
+    # ---- the same pairs one fs1_w1 call each (sample), for comparison
+    solo = None
+    if W["solo"] and not args.no_solo:
+        k = min(W["solo"], len(probs))
+        s_nit, t0 = 0, time.perf_counter()
+        for p, q in zip(host[:k], probs[:k]):
+            st, w1, info = fs1.fs1_w1(solver.h, q)
+            s_nit += int(p.a.size) * int(info.iters)
+        solo_s = time.perf_counter() - t0
+        solo = {"value": s_nit / solo_s, "unit": METRIC, "pairs": k,
+                "note": "the first pairs of the batch solved one fs1_w1 call (one launch) each, wall clock"}
+
+    achieved = W["bytes_per_nit"] * nit_step / (kernel_ms / 1000.0) / 1e9
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -325,31 +388,33 @@ def run_gpu(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cores = host_cores()
-        npairs = max(1, min(8, cores))
-        v, dt, onit = oracle_sample(W["n"], W["eps"], list(range(npairs)), args.cpu_iters, npairs)
-        cpu = {"value": v, "unit": "N*iters/s", "cores": npairs, "kind": "oracle",
-               "sample": f"{npairs} pairs of the workload x {args.cpu_iters} iterations "
-                         f"(FP64 stabilised sequential FS-1, one pair per thread), {dt:.1f} s"}
+        n_s = max(1, min(W["sample_pairs"], cores))
+        v, dt, onit = oracle_sample(args.workload, list(range(n_s)), W["sample_iters"], n_s)
+        cpu = {"value": v, "unit": METRIC, "cores": n_s, "kind": "oracle",
+               "sample": cpu_sample_desc(W, n_s, W["sample_iters"], dt)}
 
     if rank == 0:
+        p0 = host[0]
+        cfg = {"workload": W["name"], "pairs": len(idx), "variant": W["variant"], "precision": W["precision"],
+               "parallelism": f"dp{world} (pairs)",
+               "l2": ("inputs larger than L2 (%.2f GB per step)" % (in_bytes / 1e9)) if flush is None
+               else "L2 flushed between steps (%.0f MB write)" % (flush.numel() * 4 / 1e6),
+               "team_size": teams[0] if len(teams) == 1 else teams,
+               "launch": "graph replay" if graph else "direct",
+               "iters_min": min(iters), "iters_max": max(iters), "err_median": statistics.median(errs)}
+        if args.workload == 2:
+            cfg.update({"n": p0.a.size, "eps": p0.eps, "tol": p0.tol, "itr_max": p0.itr_max})
         line = {"metric": METRIC, "value": value, "unit": "N*iters/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-                "data": "synthetic",
-                "config": {"workload": W["name"], "n": W["n"], "pairs": len(idx), "eps": W["eps"],
-                           "tol": W["tol"], "itr_max": W["itr_max"], "parallelism": f"dp{world} (pairs)",
-                           "l2": "inputs larger than L2 (%.1f GB per step)" % (h2d / 1e9),
-                           "team_size": int(infos[0].team_size),
-                           "launch": "graph replay" if solver.stats()["graph_replays"] else "direct",
-                           "iters_min": min(iters), "iters_max": max(iters),
-                           "err_median": statistics.median(errs)},
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": W["dtype"],
+                "data": "synthetic", "config": cfg,
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "traffic": traffic,
-                             "peak_source": peak_src,
-                             "note": "achieved = 28 B per N*iteration (streaming-equivalent bytes) "
-                                     "/ team-kernel time; the kernel keeps state on chip"},
+                             "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                             "note": "achieved = %.0f B per N*iteration (streaming-equivalent bytes) "
+                                     "/ solve-kernel time; the kernel keeps state on chip" % W["bytes_per_nit"]},
                 "e2e": {"value": e_val, "unit": "N*iters/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
+                "one_pair_per_launch": solo,
                 "gpu_launches": launches,
                 "clocks": clk.summary(),
                 "cpu_baseline": cpu}
@@ -372,13 +437,14 @@ def kernel_revision() -> str:
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--workload", type=int, default=2, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-solo", action="store_true", help="skip the one-pair-per-launch sample")
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fs1", choices=["fs1", "reference"])
     ap.add_argument("--pairs", type=int, default=0, help="override pairs per rank (testing)")
     ap.add_argument("--itr-max", type=int, default=None, help="override the cap (testing)")
     ap.add_argument("--e2e-steps", type=int, default=1)
-    ap.add_argument("--cpu-iters", type=int, default=300)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--team-size", type=int, default=0, help="CTAs per pair (0: autotuned)")
     ap.add_argument("--no-autotune", action="store_true", help="fixed team-size heuristic")

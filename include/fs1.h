@@ -92,7 +92,8 @@ typedef struct fs1_problem {
   int64_t n[2];         /* n[0]: points along the fast (contiguous) axis; n[1]: along
                            the slow axis (1 in 1D).  2D arrays are n[1] rows of n[0]
                            contiguous values: the paper's column-major flattening with
-                           its first index (spacing h[0]) running fastest */
+                           its first index (spacing h[0]) running fastest.  2D sides
+                           above 1024 give FS1_EUNSUPPORTED */
   double h[2];          /* grid spacings (h[1] unused in 1D) */
   double eps;           /* entropic regularisation, > 0 */
   double tol;           /* stop when the column-marginal L1 error <= tol (>= 0) */

@@ -194,6 +194,7 @@ fs1_status check_problem(const fs1_problem& p) {
   if (p.itr_max < 0) return FS1_EINVAL;
   if (!p.a || !p.b) return FS1_EINVAL;
   if ((p.f_init == nullptr) != (p.g_init == nullptr)) return FS1_EINVAL;
+  if (p.ndim == 2 && (p.n[0] > kMaxLine2D || p.n[1] > kMaxLine2D)) return FS1_EUNSUPPORTED;
   return FS1_OK;
 }
 

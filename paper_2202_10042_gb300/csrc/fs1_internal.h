@@ -78,6 +78,7 @@ enum KernelKind {
 
 // 2D solver (fs1_solve2d.cu): up to kMaxImg2D images per launch.
 constexpr int kMaxImg2D = 64;
+constexpr int kMaxLine2D = 1024;   // longest row or column (staged in shared memory)
 size_t solve2d_workspace(const PairDesc* host_descs, int count);
 int launch_solve_2d(const PairDesc* host_descs, int count, int in_f32, PairResult* d_results, void* ws,
                     size_t ws_bytes, long long spin_cap, void* stream);

@@ -6,16 +6,22 @@
 // (lam_2 = e^{-h_slow/eps}); this is the "2d recursion" of Section 4 with the
 // K_0 products done row by row.  One half-step of Algorithm 2 is
 //   fast pass : Y = (I (x) K_fast) X                  one warp per row
-//   slow pass : y = (K_slow (x) I) Y, z = mass / y,    one warp per column
-//               and (v-half) the column-marginal error partials
+//   slow pass : y = (K_slow (x) I) Y, z = mass / y,    one CTA per tile of 8
+//               and (v-half) the marginal error        columns, one warp per
+//                                                      column of the tile
 // executed by one persistent cooperative kernel over a batch of images, with a
 // bounded grid barrier after every pass.  The state is stored per point in
 // extended range (FP32 mantissa and int exponent, struct XF), so any eps and
 // grid spacing are covered with FP32 relative precision.  A line of L <= 1024
-// points is split over the 32 lanes of a warp: each lane runs the recurrences
-// serially over its points and the lanes are joined by a Kogge-Stone scan of
+// points is staged in shared memory (rows: one coalesced read of the row;
+// columns: the CTA reads the tile's rows, 64 contiguous bytes each) and split
+// over the 32 lanes of a warp: each lane runs the recurrences serially over
+// its P = ceil(L / 32) points, the lanes are joined by a Kogge-Stone scan of
 // the lane aggregates with the same associative (decay, value) operators as
-// the 1D kernel.
+// the 1D kernel, and the result leaves shared memory with coalesced stores
+// (columns: fused with the pointwise division and the error).  In shared
+// memory lane l's chunk starts at l P' with P' = P | 1 (odd), so the lanes'
+// 8-byte accesses to their k-th points fall in distinct banks.
 //
 // Stop rule per image (the while condition of Algorithm 2): the error partials
 // of the image's column warps are summed in a fixed order by every CTA, so all
@@ -42,6 +48,7 @@ namespace {
 
 constexpr int kThreads2 = 256;
 constexpr int kWarps2 = kThreads2 / 32;
+constexpr int kTileCols = kWarps2;   // columns of a slow-pass tile (one warp each)
 constexpr int kTab = 38;   // lam^0..lam^32, then lam^{P 2^i}, i < 5
 
 struct Img2D {
@@ -60,7 +67,8 @@ struct Img2D {
   const double* g_init;
   double* f_out;          // optional potentials out
   double* g_out;
-  float* errp;         // [2 nf] column error partials (compensated pairs)
+  float* errp;         // [2 ceil(nf / 8)] error partials of the column tiles
+                       // (compensated pairs)
   double* wp;          // [nf] column cost partials
   int* stop;           // 0 while active; 1 + k once stopped with the final v in V[k]
 };
@@ -72,6 +80,8 @@ struct Launch2D {
   int in_f32;
   const int* row_off;  // [nimg + 1] prefix sums of ns
   const int* col_off;  // [nimg + 1] prefix sums of nf
+  const int* tile_off; // [nimg + 1] prefix sums of ceil(nf / 8)
+  int line_stride;     // per-warp shared-memory region (XF): two chunked lines + 2
   unsigned long long* bar;   // zeroed per launch
   int* abort_flag;
   long long spin_cap;
@@ -121,13 +131,15 @@ __device__ __forceinline__ int owner(const int* off, int nimg, int t) {
 }
 
 // ---------------------------------------------------------------------------
-// warp line scan along L points at `stride`: out = K x (plain) or the
-// distance-weighted sum (WEIGHTED).  Lane l owns points [l P, l P + P).  The
-// lane's backward sums are parked in `tmp` (written and read back by the same
-// lane; tmp may alias out).  tab: lam^j (j <= 32) and lam^{P 2^i} at 33 + i.
+// warp line scan of L points: out = K x (plain) or the distance-weighted sum
+// (WEIGHTED).  Lane l owns points [l P, l P + P); its k-th point is at
+// index base + k step of in / out / tmp (base chosen by the caller for this
+// lane).  The lane's backward sums are parked in `tmp` (written and read back
+// by the same lane; tmp may alias out, and out may alias in).  tab: lam^j
+// (j <= 32) and lam^{P 2^i} at 33 + i.
 // ---------------------------------------------------------------------------
 template <bool WEIGHTED>
-__device__ void line_scan(const XF* in, XF* out, XF* tmp, int64_t stride, int L, const XF* tab) {
+__device__ void line_scan(const XF* in, XF* out, XF* tmp, int64_t base, int64_t step, int L, const XF* tab) {
   using Op = typename std::conditional<WEIGHTED, OpDist<XF>, OpPlain<XF>>::type;
   using T = typename Op::T;
   const int lane = threadIdx.x & 31;
@@ -140,12 +152,12 @@ __device__ void line_scan(const XF* in, XF* out, XF* tmp, int64_t stride, int L,
   {
     XF p = zero, A = zero, s = zero, B = zero;
     for (int k = 0; k < P; ++k) {
-      const XF x = k < n ? in[(int64_t)(i0 + k) * stride] : zero;
+      const XF x = k < n ? in[base + k * step] : zero;
       if (WEIGHTED) A = c_mul(c_add(A, p), lam);
       p = c_add(c_mul(p, lam), x);
     }
     for (int k = P - 1; k >= 0; --k) {
-      const XF x = k < n ? in[(int64_t)(i0 + k) * stride] : zero;
+      const XF x = k < n ? in[base + k * step] : zero;
       if (WEIGHTED) B = c_mul(c_add(c_add(B, s), x), lam);
       s = c_mul(c_add(s, x), lam);
     }
@@ -184,8 +196,8 @@ __device__ void line_scan(const XF* in, XF* out, XF* tmp, int64_t stride, int L,
       s = c_mul(s, lam);
     }
     for (int k = n - 1; k >= 0; --k) {
-      const XF xk = in[(int64_t)(i0 + k) * stride];
-      tmp[(int64_t)(i0 + k) * stride] = WEIGHTED ? B : s;
+      const XF xk = in[base + k * step];
+      tmp[base + k * step] = WEIGHTED ? B : s;
       if (WEIGHTED) B = c_mul(c_add(c_add(B, s), xk), lam);
       s = c_mul(c_add(s, xk), lam);
     }
@@ -200,16 +212,103 @@ __device__ void line_scan(const XF* in, XF* out, XF* tmp, int64_t stride, int L,
       A = zero;
     }
     for (int k = 0; k < n; ++k) {
-      const XF xk = in[(int64_t)(i0 + k) * stride];
+      const XF xk = in[base + k * step];
       if (WEIGHTED) A = c_mul(c_add(A, p), lam);
       p = c_add(c_mul(p, lam), xk);
-      const XF bk = tmp[(int64_t)(i0 + k) * stride];
-      out[(int64_t)(i0 + k) * stride] = c_add(WEIGHTED ? A : p, bk);
+      const XF bk = tmp[base + k * step];
+      out[base + k * step] = c_add(WEIGHTED ? A : p, bk);
     }
   }
 }
 
+// line scan over global memory with the line's points at `stride`
+template <bool WEIGHTED>
+__device__ void line_scan_global(const XF* in, XF* out, XF* tmp, int64_t stride, int L, const XF* tab) {
+  const int P = (L + 31) >> 5;
+  line_scan<WEIGHTED>(in, out, tmp, (int64_t)(threadIdx.x & 31) * P * stride, stride, L, tab);
+}
+
+// Walks j = j0, j0 + 32, j0 + 64, ... of a line of P-point lane chunks and
+// yields j's shared-memory index (j / P) P' + j % P without a division per
+// step.
+struct ChunkPos {
+  int d, m, dq, mq, P, Pp;
+  __device__ ChunkPos(int j0, int P_) : P(P_), Pp(P_ | 1) {
+    d = j0 / P;
+    m = j0 - d * P;
+    dq = 32 / P;
+    mq = 32 - dq * P;
+  }
+  __device__ int pos() const { return d * Pp + m; }
+  __device__ void next() {
+    d += dq;
+    m += mq;
+    if (m >= P) {
+      m -= P;
+      ++d;
+    }
+  }
+};
+
+// fast pass of one row (one warp): stage, scan in shared memory, store
+__device__ void row_pass(const XF* in, XF* out, int L, const XF* tab, XF* s, XF* t) {
+  const int lane = threadIdx.x & 31;
+  const int P = (L + 31) >> 5;
+  {
+    ChunkPos q(lane, P);
+    for (int j = lane; j < L; j += 32, q.next()) s[q.pos()] = in[j];
+  }
+  __syncwarp();
+  line_scan<false>(s, s, t, (int64_t)lane * (P | 1), 1, L, tab);
+  __syncwarp();
+  {
+    ChunkPos q(lane, P);
+    for (int j = lane; j < L; j += 32, q.next()) out[j] = s[q.pos()];
+  }
+  __syncwarp();
+}
+
+// slow pass of one tile of columns col0 .. col0 + 7 (the whole CTA): stage the
+// tile (thread -> column threadIdx % 8, rows threadIdx / 8 + 32 k), then warp
+// w scans column col0 + w in its shared-memory region; the caller's epilogue
+// reads the results through the same thread -> (row, column) map.
+__device__ void col_tile_scan(const XF* Y, int nf, int ns, int col0, const XF* tab, XF* sbuf, int stride) {
+  const int c = threadIdx.x & (kTileCols - 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int P = (ns + 31) >> 5;
+  const int CH = 32 * (P | 1);
+  if (col0 + c < nf) {
+    XF* s = sbuf + c * stride;
+    ChunkPos q(threadIdx.x / kTileCols, P);
+    for (int r = threadIdx.x / kTileCols; r < ns; r += kThreads2 / kTileCols, q.next())
+      s[q.pos()] = Y[(int64_t)r * nf + col0 + c];
+  }
+  __syncthreads();
+  if (col0 + warp < nf) {
+    XF* s = sbuf + warp * stride;
+    line_scan<false>(s, s, s + CH, (int64_t)lane * (P | 1), 1, ns, tab);
+  }
+  __syncthreads();
+}
+
+// CTA sum of a compensated pair in a fixed order (every thread returns it)
+__device__ void cta_sum_df(float& h, float& l, float* red) {
+  warp_sum_df(h, l);
+  if ((threadIdx.x & 31) == 0) {
+    red[2 * (threadIdx.x >> 5)] = h;
+    red[2 * (threadIdx.x >> 5) + 1] = l;
+  }
+  __syncthreads();
+  h = 0.f;
+  l = 0.f;
+  for (int w = 0; w < kWarps2; ++w) df_add(h, l, red[2 * w], red[2 * w + 1]);
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(kThreads2) fs1_solve2d_kernel(Launch2D L) {
+  extern __shared__ XF sline[];   // kWarps2 regions of L.line_stride XF
+  __shared__ float sred[2 * kWarps2];
+  __shared__ int stile[kMaxImg2D + 1];
   __shared__ XF tab[kMaxImg2D][2][kTab];   // [image][axis: 0 fast, 1 slow]
   __shared__ int srow[kMaxImg2D + 1], scol[kMaxImg2D + 1];
   __shared__ signed char sstate[kMaxImg2D];  // 0 active, 1 stops this iteration, 2 stopped earlier
@@ -223,7 +322,10 @@ __global__ void __launch_bounds__(kThreads2) fs1_solve2d_kernel(Launch2D L) {
   for (int i = threadIdx.x; i <= nimg; i += blockDim.x) {
     srow[i] = L.row_off[i];
     scol[i] = L.col_off[i];
+    stile[i] = L.tile_off[i];
   }
+  XF* const s_own = sline + warp * L.line_stride;            // this warp's region
+  XF* const t_own = s_own + (L.line_stride - 2) / 2;
   for (int t = threadIdx.x; t < nimg * 2 * kTab; t += blockDim.x) {
     const int i = t / (2 * kTab), ax = (t / kTab) & 1, j = t % kTab;
     const Img2D& I = L.imgs[i];
@@ -245,7 +347,7 @@ __global__ void __launch_bounds__(kThreads2) fs1_solve2d_kernel(Launch2D L) {
   }
   if (!grid_barrier(L, gen, &sok)) return;
 
-  const int rows = srow[nimg], cols = scol[nimg];
+  const int rows = srow[nimg], cols = scol[nimg], tiles = stile[nimg];
   for (int64_t ell = 0;; ++ell) {
     const int par = (int)(ell & 1);
     __syncthreads();
@@ -260,32 +362,37 @@ __global__ void __launch_bounds__(kThreads2) fs1_solve2d_kernel(Launch2D L) {
       if (sstate[i]) continue;
       const Img2D& I = L.imgs[i];
       const int64_t o = (int64_t)(t - srow[i]) * I.nf;
-      line_scan<false>(I.U + o, I.Y + o, I.R + o, 1, I.nf, tab[i][0]);
+      row_pass(I.U + o, I.Y + o, I.nf, tab[i][0], s_own, t_own);
     }
     if (!grid_barrier(L, gen, &sok)) return;
     // ---- v-half, slow pass: y = (K_s (x) I) Y, v_new = b / y, error partials
-    for (int t = gw; t < cols; t += nw) {
-      const int i = owner(scol, nimg, t);
-      if (sstate[i]) continue;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+      const int i = owner(stile, nimg, t);
+      if (sstate[i]) continue;   // CTA-uniform
       const Img2D& I = L.imgs[i];
-      const int col = t - scol[i];
+      const int tile = t - stile[i];
+      const int col0 = tile * kTileCols;
+      col_tile_scan(I.Y, I.nf, I.ns, col0, tab[i][1], sline, L.line_stride);
       XF* Vn = I.V[par ^ 1];
-      line_scan<false>(I.Y + col, I.R + col, Vn + col, I.nf, I.ns, tab[i][1]);
-      __syncwarp();
       float eh = 0.f, el = 0.f;
-      for (int r = lane; r < I.ns; r += 32) {
-        const int64_t p = (int64_t)r * I.nf + col;
-        const XF y = I.R[p];
-        const float m = load_m(I.b, p, L.in_f32);
-        const XF vo = I.V[par][p];
-        Vn[p] = m > 0.f ? xf_norm(__fdividef(m, y.m), -y.e) : XF{0.f, kZeroExp};
-        const float pv = c_to(c_mul(vo, y), 0);   // v_old (K^T u) at p
-        df_add(eh, el, fabsf(pv - m), 0.f);
+      const int c = threadIdx.x & (kTileCols - 1);
+      if (col0 + c < I.nf) {
+        const XF* s = sline + c * L.line_stride;
+        ChunkPos q(threadIdx.x / kTileCols, (I.ns + 31) >> 5);
+        for (int r = threadIdx.x / kTileCols; r < I.ns; r += kThreads2 / kTileCols, q.next()) {
+          const int64_t p = (int64_t)r * I.nf + col0 + c;
+          const XF y = s[q.pos()];
+          const float m = load_m(I.b, p, L.in_f32);
+          const XF vo = I.V[par][p];
+          Vn[p] = m > 0.f ? xf_norm(__fdividef(m, y.m), -y.e) : XF{0.f, kZeroExp};
+          const float pv = c_to(c_mul(vo, y), 0);   // v_old (K^T u) at p
+          df_add(eh, el, fabsf(pv - m), 0.f);
+        }
       }
-      warp_sum_df(eh, el);
-      if (lane == 0) {
-        I.errp[2 * col] = eh;
-        I.errp[2 * col + 1] = el;
+      cta_sum_df(eh, el, sred);
+      if (threadIdx.x == 0) {
+        I.errp[2 * tile] = eh;
+        I.errp[2 * tile + 1] = el;
       }
     }
     if (!grid_barrier(L, gen, &sok)) return;
@@ -294,7 +401,8 @@ __global__ void __launch_bounds__(kThreads2) fs1_solve2d_kernel(Launch2D L) {
       if (sstate[i]) continue;
       const Img2D& I = L.imgs[i];
       float h = 0.f, l = 0.f;
-      for (int c = lane; c < I.nf; c += 32) df_add(h, l, __ldcg(I.errp + 2 * c), __ldcg(I.errp + 2 * c + 1));
+      const int nt = (I.nf + kTileCols - 1) / kTileCols;
+      for (int c = lane; c < nt; c += 32) df_add(h, l, __ldcg(I.errp + 2 * c), __ldcg(I.errp + 2 * c + 1));
       warp_sum_df(h, l);
       if (lane == 0) {
         const double err = (double)h + (double)l;
@@ -317,23 +425,28 @@ __global__ void __launch_bounds__(kThreads2) fs1_solve2d_kernel(Launch2D L) {
       if (sstate[i]) continue;
       const Img2D& I = L.imgs[i];
       const int64_t o = (int64_t)(t - srow[i]) * I.nf;
-      line_scan<false>(I.V[par ^ 1] + o, I.Y + o, I.R + o, 1, I.nf, tab[i][0]);
+      row_pass(I.V[par ^ 1] + o, I.Y + o, I.nf, tab[i][0], s_own, t_own);
     }
     if (!grid_barrier(L, gen, &sok)) return;
     // ---- u-half, slow pass: u = a / ((K_s (x) I) Y)
-    for (int t = gw; t < cols; t += nw) {
-      const int i = owner(scol, nimg, t);
-      if (sstate[i]) continue;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+      const int i = owner(stile, nimg, t);
+      if (sstate[i]) continue;   // CTA-uniform
       const Img2D& I = L.imgs[i];
-      const int col = t - scol[i];
-      line_scan<false>(I.Y + col, I.R + col, I.U + col, I.nf, I.ns, tab[i][1]);
-      __syncwarp();
-      for (int r = lane; r < I.ns; r += 32) {
-        const int64_t p = (int64_t)r * I.nf + col;
-        const XF y = I.R[p];
-        const float m = load_m(I.a, p, L.in_f32);
-        I.U[p] = m > 0.f ? xf_norm(__fdividef(m, y.m), -y.e) : XF{0.f, kZeroExp};
+      const int col0 = (t - stile[i]) * kTileCols;
+      col_tile_scan(I.Y, I.nf, I.ns, col0, tab[i][1], sline, L.line_stride);
+      const int c = threadIdx.x & (kTileCols - 1);
+      if (col0 + c < I.nf) {
+        const XF* s = sline + c * L.line_stride;
+        ChunkPos q(threadIdx.x / kTileCols, (I.ns + 31) >> 5);
+        for (int r = threadIdx.x / kTileCols; r < I.ns; r += kThreads2 / kTileCols, q.next()) {
+          const int64_t p = (int64_t)r * I.nf + col0 + c;
+          const XF y = s[q.pos()];
+          const float m = load_m(I.a, p, L.in_f32);
+          I.U[p] = m > 0.f ? xf_norm(__fdividef(m, y.m), -y.e) : XF{0.f, kZeroExp};
+        }
       }
+      __syncthreads();   // the tile's shared memory is reused by the next tile
     }
     // images that stop here keep v_old = V[par]
     if (blockIdx.x == 0)
@@ -350,9 +463,9 @@ __global__ void __launch_bounds__(kThreads2) fs1_solve2d_kernel(Launch2D L) {
     const Img2D& I = L.imgs[i];
     const int k = (ld_relaxed(I.stop) - 1) & 1;
     const int64_t o = (int64_t)(t - srow[i]) * I.nf;
-    line_scan<true>(I.V[k] + o, I.Y + o, I.R + o, 1, I.nf, tab[i][0]);
+    line_scan_global<true>(I.V[k] + o, I.Y + o, I.R + o, 1, I.nf, tab[i][0]);
     __syncwarp();
-    line_scan<false>(I.V[k] + o, I.V[k ^ 1] + o, I.R + o, 1, I.nf, tab[i][0]);
+    line_scan_global<false>(I.V[k] + o, I.V[k ^ 1] + o, I.R + o, 1, I.nf, tab[i][0]);
   }
   if (!grid_barrier(L, gen, &sok)) return;
   // columns: h_fast u.(K_s (x) I) Y + h_slow u.(K_s^(c) (x) I) V[k^1]
@@ -362,7 +475,7 @@ __global__ void __launch_bounds__(kThreads2) fs1_solve2d_kernel(Launch2D L) {
     const int k = (ld_relaxed(I.stop) - 1) & 1;
     const int col = t - scol[i];
     double acc = 0.0;
-    line_scan<false>(I.Y + col, I.R + col, I.R + col, I.nf, I.ns, tab[i][1]);
+    line_scan_global<false>(I.Y + col, I.R + col, I.R + col, I.nf, I.ns, tab[i][1]);
     __syncwarp();
     for (int r = lane; r < I.ns; r += 32) {
       const int64_t p = (int64_t)r * I.nf + col;
@@ -370,7 +483,7 @@ __global__ void __launch_bounds__(kThreads2) fs1_solve2d_kernel(Launch2D L) {
       acc += I.hf * ldexp((double)u.m * (double)w.m, u.e + w.e);
     }
     __syncwarp();
-    line_scan<true>(I.V[k ^ 1] + col, I.R + col, I.R + col, I.nf, I.ns, tab[i][1]);
+    line_scan_global<true>(I.V[k ^ 1] + col, I.R + col, I.R + col, I.nf, I.ns, tab[i][1]);
     __syncwarp();
     for (int r = lane; r < I.ns; r += 32) {
       const int64_t p = (int64_t)r * I.nf + col;
@@ -410,7 +523,7 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 }  // namespace
 
 size_t solve2d_workspace(const PairDesc* d, int count) {
-  size_t b = align256(sizeof(Img2D) * count) + 2 * align256(sizeof(int) * (count + 1)) + 256 + 256;
+  size_t b = align256(sizeof(Img2D) * count) + 3 * align256(sizeof(int) * (count + 1)) + 256 + 256;
   for (int i = 0; i < count; ++i) {
     const size_t n = (size_t)d[i].n_fast * d[i].n_slow;
     b += 5 * align256(sizeof(XF) * n) + align256(sizeof(float) * 2 * d[i].n_fast) +
@@ -423,6 +536,8 @@ int launch_solve_2d(const PairDesc* d, int count, int in_f32, PairResult* result
                     long long spin_cap, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   if (count < 1 || count > kMaxImg2D) return FS1_EINVAL;
+  for (int i = 0; i < count; ++i)
+    if (d[i].n_fast > kMaxLine2D || d[i].n_slow > kMaxLine2D) return FS1_EUNSUPPORTED;
   if (solve2d_workspace(d, count) > ws_bytes) return FS1_ENOMEM;
   char* p = (char*)ws;
   Img2D* d_imgs = (Img2D*)p;
@@ -431,12 +546,15 @@ int launch_solve_2d(const PairDesc* d, int count, int in_f32, PairResult* result
   p += align256(sizeof(int) * (count + 1));
   int* d_col = (int*)p;
   p += align256(sizeof(int) * (count + 1));
+  int* d_tile = (int*)p;
+  p += align256(sizeof(int) * (count + 1));
   unsigned long long* d_bar = (unsigned long long*)p;
   p += 256;
   int* d_abort = (int*)p;
   p += 256;
   std::vector<Img2D> imgs(count);
-  std::vector<int> row(count + 1, 0), col(count + 1, 0);
+  std::vector<int> row(count + 1, 0), col(count + 1, 0), tile(count + 1, 0);
+  int pp_max = 1;
   char* stops = nullptr;
   for (int i = 0; i < count; ++i) {
     const PairDesc& D = d[i];
@@ -469,25 +587,36 @@ int launch_solve_2d(const PairDesc* d, int count, int in_f32, PairResult* result
     imgs[i] = I;
     row[i + 1] = row[i] + I.ns;
     col[i + 1] = col[i] + I.nf;
+    tile[i + 1] = tile[i] + (I.nf + kTileCols - 1) / kTileCols;
+    pp_max = std::max(pp_max, std::max((I.nf + 31) / 32, (I.ns + 31) / 32) | 1);
   }
   cudaError_t e = cudaSuccess;
   for (int i = 0; i < count && e == cudaSuccess; ++i) e = cudaMemsetAsync(imgs[i].stop, 0, sizeof(int), st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_imgs, imgs.data(), sizeof(Img2D) * count, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_row, row.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_col, col.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_tile, tile.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_bar, 0, 512, st);
   if (e != cudaSuccess) {
     fprintf(stderr, "fs1: 2D setup failed: %s\n", cudaGetErrorString(e));
     return FS1_ECUDA;
   }
-  Launch2D L{d_imgs, results, count, in_f32, d_row, d_col, d_bar, d_abort, spin_cap};
+  const int line_stride = 2 * 32 * pp_max + 2;   // == 2 (mod 16): the tile's warps start in different banks
+  const size_t smem = sizeof(XF) * (size_t)kWarps2 * line_stride;
+  Launch2D L{d_imgs, results, count, in_f32, d_row, d_col, d_tile, line_stride, d_bar, d_abort, spin_cap};
+  e = cudaFuncSetAttribute(fs1_solve2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0, dev = 0, sms = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fs1_solve2d_kernel, kThreads2, 0);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fs1_solve2d_kernel, kThreads2, smem);
+  if (e != cudaSuccess || per_sm < 1) {
+    fprintf(stderr, "fs1: 2D kernel does not fit (%zu B shared memory): %s\n", smem, cudaGetErrorString(e));
+    return FS1_EUNSUPPORTED;
+  }
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = std::max(1, per_sm) * sms;
+  const int grid = per_sm * sms;
   void* args[] = {&L};
-  e = cudaLaunchCooperativeKernel((const void*)fs1_solve2d_kernel, dim3(grid), dim3(kThreads2), args, 0, st);
+  e = cudaLaunchCooperativeKernel((const void*)fs1_solve2d_kernel, dim3(grid), dim3(kThreads2), args, smem, st);
   if (e != cudaSuccess) {
     fprintf(stderr, "fs1: 2D launch failed: %s\n", cudaGetErrorString(e));
     return FS1_ECUDA;

@@ -123,3 +123,22 @@ def test_2d_warm_start_resume_bit_identical(env):
     assert i_res[0].iters == 30
     assert w_res[0] == w_full[0]
     assert i_res[0].marginal_err == i_full[0].marginal_err
+
+
+@pytest.mark.parametrize("ns,nf", [(300, 1024), (1024, 200)])
+def test_2d_longest_lines_against_oracle(env, ns, nf):
+    """Rows or columns of 1024 points, the longest a line may be."""
+    a2, b2 = _rand2d(ns + 7 * nf, ns, nf)
+    h, eps, itr = (1.0 / nf, 1.0 / ns), 2e-3, 12
+    w, infos = _solve(env, [(a2, b2, h, eps, 0.0, itr)])
+    ref = cref.solve(a2, b2, h, eps, 0.0, itr, tau=1e10)
+    assert infos[0].iters == ref.iters == itr
+    assert abs(w[0] - ref.w) <= TOL32 * abs(ref.w)
+    assert abs(infos[0].marginal_err - ref.err) <= 1e-3 * ref.err
+
+
+def test_2d_side_above_limit_unsupported(env):
+    _, fs1 = env
+    a2, b2 = _rand2d(3, 1025, 4)
+    w, infos = _solve(env, [(a2, b2, (0.25, 1 / 1025), 0.05, 0.0, 5)])
+    assert infos[0].status == fs1.FS1_EUNSUPPORTED
