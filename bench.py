@@ -57,10 +57,10 @@ METRIC = "N*iters/s"
 L2_BYTES = 129 << 20
 
 # Streaming-equivalent HBM bytes per N*iteration: what a realisation that
-# streams the state through HBM would move.  1D FP32: the v-half reads u, b and
+# streams the state through HBM would move.  FP32: the v-half reads u, b and
 # the accepted v and writes v (16 B), the u-half reads v, a and writes u
-# (12 B); FP64 doubles it; 2D adds, per half-step, the write and read of the
-# fast-axis partial sums (8 B).
+# (12 B); FP64 doubles it.  2D counts the same 28 B per point (a two-pass
+# realisation also writes and reads the fast-axis partial sums, 44 B).
 WORKLOADS = {
     1: dict(name="fs1_1d_plain_fp64_n1000_eps1e-2_it1000", pairs=1, variant="plain", precision="fp64",
             dtype="f64", bytes_per_nit=56.0, kw={}, sample_pairs=1, sample_iters=1000, solo=0),
@@ -70,7 +70,7 @@ WORKLOADS = {
     3: dict(name="fs1_1d_log_fp32_uneven4096_n256-65536", pairs=4096, variant="log", precision="fp32",
             dtype="f32", bytes_per_nit=28.0, kw={}, sample_pairs=64, sample_iters=200, solo=64),
     4: dict(name="fs1_2d_log_fp32_batch64_512x512_eps1e-3", pairs=64, variant="log", precision="fp32",
-            dtype="f32", bytes_per_nit=44.0, kw={}, sample_pairs=4, sample_iters=40, solo=4),
+            dtype="f32", bytes_per_nit=28.0, kw={}, sample_pairs=4, sample_iters=40, solo=4),
 }
 
 

@@ -49,6 +49,7 @@ namespace {
 constexpr int kThreads2 = 256;
 constexpr int kWarps2 = kThreads2 / 32;
 constexpr int kTileCols = kWarps2;   // columns of a slow-pass tile (one warp each)
+constexpr int kBatch = 6;            // global loads a thread keeps in flight when staging
 constexpr int kTab = 38;   // lam^0..lam^32, then lam^{P 2^i}, i < 5
 
 struct Img2D {
@@ -221,6 +222,69 @@ __device__ void line_scan(const XF* in, XF* out, XF* tmp, int64_t base, int64_t 
   }
 }
 
+// Fast plain line scan for a line staged in shared memory (lane chunk at
+// in[base + k], k < P): the lane's values are taken into one power-of-two
+// frame (the largest exponent of the chunk) and all four sweeps run in FP32,
+// as in the 1D kernel's per-thread frames; only the lane aggregates and the
+// 5-level Kogge-Stone use extended range.  A value below 2^-126 of the frame
+// is dropped; every output k is at least lam^P times the largest term it
+// sums, so with c P <= 40 (c = h / eps of the axis) the dropped part stays
+// below FP32 rounding.  Backward partials go to the float array tf at the
+// same indices.  out may alias in.
+__device__ void line_scan_frame(const XF* in, XF* out, float* tf, int64_t base, int L, const XF* tab) {
+  const int lane = threadIdx.x & 31;
+  const int P = (L + 31) >> 5;
+  const int n = max(0, min(P, L - lane * P));
+  const float lam = tab[1].m * pow2f(tab[1].e);   // lam as FP32 (lam >= e^-40)
+  int emax = kZeroExp;
+#pragma unroll 4
+  for (int k = 0; k < n; ++k) emax = max(emax, in[base + k].e);
+  // lane aggregates in frame emax: forward sum lam^{P-1-k} x_k (Horner, then
+  // the empty tail), backward sum lam^{k+1} x_k
+  float r = 0.f, q = 0.f;
+#pragma unroll 4
+  for (int k = 0; k < n; ++k) {
+    const XF x = in[base + k];
+    r = fmaf(lam, r, x.m * pow2f(x.e - emax));
+  }
+#pragma unroll 4
+  for (int k = n - 1; k >= 0; --k) {
+    const XF x = in[base + k];
+    q = lam * (q + x.m * pow2f(x.e - emax));
+  }
+  XF x = xf_norm(r, emax), z = xf_norm(q, emax);
+  if (n < P) x = c_mul(x, tab[P - n]);
+#pragma unroll
+  for (int lv = 0; lv < 5; ++lv) {
+    const int o = 1 << lv;
+    const XF y = shfl_up(x, o);
+    const XF w = shfl_down(z, o);
+    if (lane >= o) x = c_add(c_mul(y, tab[33 + lv]), x);
+    if (lane + o < 32) z = c_add(z, c_mul(w, tab[33 + lv]));
+  }
+  XF cfw = shfl_up(x, 1), cbw = shfl_down(z, 1);
+  if (lane == 0) cfw = XF{0.f, kZeroExp};
+  if (lane == 31) cbw = XF{0.f, kZeroExp};
+  if (n <= 0) return;
+  // final sweeps in frame F: room for P terms of the chunk plus the carries
+  const int F = max(emax, max(cfw.e, cbw.e)) + 6;
+  const float sc_tail = n < P ? tab[P - n].m * pow2f(tab[P - n].e) : 1.f;
+  float sb = c_to(cbw, F) * sc_tail;
+#pragma unroll 4
+  for (int k = n - 1; k >= 0; --k) {
+    const XF xk = in[base + k];
+    tf[base + k] = sb;
+    sb = lam * (sb + xk.m * pow2f(xk.e - F));
+  }
+  float p = c_to(cfw, F);
+#pragma unroll 4
+  for (int k = 0; k < n; ++k) {
+    const XF xk = in[base + k];
+    p = fmaf(lam, p, xk.m * pow2f(xk.e - F));
+    out[base + k] = xf_norm(p + tf[base + k], F);
+  }
+}
+
 // line scan over global memory with the line's points at `stride`
 template <bool WEIGHTED>
 __device__ void line_scan_global(const XF* in, XF* out, XF* tmp, int64_t stride, int L, const XF* tab) {
@@ -251,15 +315,27 @@ struct ChunkPos {
 };
 
 // fast pass of one row (one warp): stage, scan in shared memory, store
-__device__ void row_pass(const XF* in, XF* out, int L, const XF* tab, XF* s, XF* t) {
+__device__ void row_pass(const XF* in, XF* out, int L, const XF* tab, bool frame, XF* s, XF* t) {
   const int lane = threadIdx.x & 31;
   const int P = (L + 31) >> 5;
   {
+    // batches of kBatch loads in flight before their shared-memory stores
     ChunkPos q(lane, P);
-    for (int j = lane; j < L; j += 32, q.next()) s[q.pos()] = in[j];
+    for (int j0 = lane; j0 < L; j0 += 32 * kBatch) {
+      XF v[kBatch];
+#pragma unroll
+      for (int b = 0; b < kBatch; ++b)
+        if (j0 + 32 * b < L) v[b] = in[j0 + 32 * b];
+#pragma unroll
+      for (int b = 0; b < kBatch; ++b, q.next())
+        if (j0 + 32 * b < L) s[q.pos()] = v[b];
+    }
   }
   __syncwarp();
-  line_scan<false>(s, s, t, (int64_t)lane * (P | 1), 1, L, tab);
+  if (frame)
+    line_scan_frame(s, s, reinterpret_cast<float*>(t), (int64_t)lane * (P | 1), L, tab);
+  else
+    line_scan<false>(s, s, t, (int64_t)lane * (P | 1), 1, L, tab);
   __syncwarp();
   {
     ChunkPos q(lane, P);
@@ -272,21 +348,34 @@ __device__ void row_pass(const XF* in, XF* out, int L, const XF* tab, XF* s, XF*
 // tile (thread -> column threadIdx % 8, rows threadIdx / 8 + 32 k), then warp
 // w scans column col0 + w in its shared-memory region; the caller's epilogue
 // reads the results through the same thread -> (row, column) map.
-__device__ void col_tile_scan(const XF* Y, int nf, int ns, int col0, const XF* tab, XF* sbuf, int stride) {
+__device__ void col_tile_scan(const XF* Y, int nf, int ns, int col0, const XF* tab, bool frame, XF* sbuf,
+                              int stride) {
   const int c = threadIdx.x & (kTileCols - 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int P = (ns + 31) >> 5;
   const int CH = 32 * (P | 1);
   if (col0 + c < nf) {
     XF* s = sbuf + c * stride;
-    ChunkPos q(threadIdx.x / kTileCols, P);
-    for (int r = threadIdx.x / kTileCols; r < ns; r += kThreads2 / kTileCols, q.next())
-      s[q.pos()] = Y[(int64_t)r * nf + col0 + c];
+    const int r0 = threadIdx.x / kTileCols;
+    constexpr int dr = kThreads2 / kTileCols;
+    ChunkPos q(r0, P);
+    for (int rb = r0; rb < ns; rb += dr * kBatch) {
+      XF v[kBatch];
+#pragma unroll
+      for (int b = 0; b < kBatch; ++b)
+        if (rb + dr * b < ns) v[b] = Y[(int64_t)(rb + dr * b) * nf + col0 + c];
+#pragma unroll
+      for (int b = 0; b < kBatch; ++b, q.next())
+        if (rb + dr * b < ns) s[q.pos()] = v[b];
+    }
   }
   __syncthreads();
   if (col0 + warp < nf) {
     XF* s = sbuf + warp * stride;
-    line_scan<false>(s, s, s + CH, (int64_t)lane * (P | 1), 1, ns, tab);
+    if (frame)
+      line_scan_frame(s, s, reinterpret_cast<float*>(s + CH), (int64_t)lane * (P | 1), ns, tab);
+    else
+      line_scan<false>(s, s, s + CH, (int64_t)lane * (P | 1), 1, ns, tab);
   }
   __syncthreads();
 }
@@ -305,13 +394,14 @@ __device__ void cta_sum_df(float& h, float& l, float* red) {
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kThreads2) fs1_solve2d_kernel(Launch2D L) {
+__global__ void __launch_bounds__(kThreads2, 2) fs1_solve2d_kernel(Launch2D L) {
   extern __shared__ XF sline[];   // kWarps2 regions of L.line_stride XF
   __shared__ float sred[2 * kWarps2];
   __shared__ int stile[kMaxImg2D + 1];
   __shared__ XF tab[kMaxImg2D][2][kTab];   // [image][axis: 0 fast, 1 slow]
   __shared__ int srow[kMaxImg2D + 1], scol[kMaxImg2D + 1];
   __shared__ signed char sstate[kMaxImg2D];  // 0 active, 1 stops this iteration, 2 stopped earlier
+  __shared__ bool sframe[kMaxImg2D][2];      // the axis takes the FP32-frame line scan (c P <= 40)
   __shared__ int sok;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gw = blockIdx.x * kWarps2 + warp;
@@ -326,6 +416,11 @@ __global__ void __launch_bounds__(kThreads2) fs1_solve2d_kernel(Launch2D L) {
   }
   XF* const s_own = sline + warp * L.line_stride;            // this warp's region
   XF* const t_own = s_own + (L.line_stride - 2) / 2;
+  for (int t = threadIdx.x; t < nimg * 2; t += blockDim.x) {
+    const Img2D& I = L.imgs[t >> 1];
+    const int len = (t & 1) ? I.ns : I.nf;
+    sframe[t >> 1][t & 1] = ((t & 1) ? I.cs : I.cf) * (double)((len + 31) >> 5) <= 40.0;
+  }
   for (int t = threadIdx.x; t < nimg * 2 * kTab; t += blockDim.x) {
     const int i = t / (2 * kTab), ax = (t / kTab) & 1, j = t % kTab;
     const Img2D& I = L.imgs[i];
@@ -362,7 +457,7 @@ __global__ void __launch_bounds__(kThreads2) fs1_solve2d_kernel(Launch2D L) {
       if (sstate[i]) continue;
       const Img2D& I = L.imgs[i];
       const int64_t o = (int64_t)(t - srow[i]) * I.nf;
-      row_pass(I.U + o, I.Y + o, I.nf, tab[i][0], s_own, t_own);
+      row_pass(I.U + o, I.Y + o, I.nf, tab[i][0], sframe[i][0], s_own, t_own);
     }
     if (!grid_barrier(L, gen, &sok)) return;
     // ---- v-half, slow pass: y = (K_s (x) I) Y, v_new = b / y, error partials
@@ -372,21 +467,35 @@ __global__ void __launch_bounds__(kThreads2) fs1_solve2d_kernel(Launch2D L) {
       const Img2D& I = L.imgs[i];
       const int tile = t - stile[i];
       const int col0 = tile * kTileCols;
-      col_tile_scan(I.Y, I.nf, I.ns, col0, tab[i][1], sline, L.line_stride);
+      col_tile_scan(I.Y, I.nf, I.ns, col0, tab[i][1], sframe[i][1], sline, L.line_stride);
       XF* Vn = I.V[par ^ 1];
       float eh = 0.f, el = 0.f;
       const int c = threadIdx.x & (kTileCols - 1);
       if (col0 + c < I.nf) {
         const XF* s = sline + c * L.line_stride;
-        ChunkPos q(threadIdx.x / kTileCols, (I.ns + 31) >> 5);
-        for (int r = threadIdx.x / kTileCols; r < I.ns; r += kThreads2 / kTileCols, q.next()) {
-          const int64_t p = (int64_t)r * I.nf + col0 + c;
-          const XF y = s[q.pos()];
-          const float m = load_m(I.b, p, L.in_f32);
-          const XF vo = I.V[par][p];
-          Vn[p] = m > 0.f ? xf_norm(__fdividef(m, y.m), -y.e) : XF{0.f, kZeroExp};
-          const float pv = c_to(c_mul(vo, y), 0);   // v_old (K^T u) at p
-          df_add(eh, el, fabsf(pv - m), 0.f);
+        const int r0 = threadIdx.x / kTileCols;
+        constexpr int dr = kThreads2 / kTileCols;
+        ChunkPos q(r0, (I.ns + 31) >> 5);
+        for (int rb = r0; rb < I.ns; rb += dr * kBatch) {
+          float mb[kBatch];
+          XF vb[kBatch];
+#pragma unroll
+          for (int b = 0; b < kBatch; ++b)
+            if (rb + dr * b < I.ns) {
+              const int64_t p = (int64_t)(rb + dr * b) * I.nf + col0 + c;
+              mb[b] = load_m(I.b, p, L.in_f32);
+              vb[b] = I.V[par][p];
+            }
+#pragma unroll
+          for (int b = 0; b < kBatch; ++b, q.next())
+            if (rb + dr * b < I.ns) {
+              const int64_t p = (int64_t)(rb + dr * b) * I.nf + col0 + c;
+              const XF y = s[q.pos()];
+              const float m = mb[b];
+              Vn[p] = m > 0.f ? xf_norm(__fdividef(m, y.m), -y.e) : XF{0.f, kZeroExp};
+              const float pv = c_to(c_mul(vb[b], y), 0);   // v_old (K^T u) at p
+              df_add(eh, el, fabsf(pv - m), 0.f);
+            }
         }
       }
       cta_sum_df(eh, el, sred);
@@ -425,7 +534,7 @@ __global__ void __launch_bounds__(kThreads2) fs1_solve2d_kernel(Launch2D L) {
       if (sstate[i]) continue;
       const Img2D& I = L.imgs[i];
       const int64_t o = (int64_t)(t - srow[i]) * I.nf;
-      row_pass(I.V[par ^ 1] + o, I.Y + o, I.nf, tab[i][0], s_own, t_own);
+      row_pass(I.V[par ^ 1] + o, I.Y + o, I.nf, tab[i][0], sframe[i][0], s_own, t_own);
     }
     if (!grid_barrier(L, gen, &sok)) return;
     // ---- u-half, slow pass: u = a / ((K_s (x) I) Y)
@@ -434,16 +543,25 @@ __global__ void __launch_bounds__(kThreads2) fs1_solve2d_kernel(Launch2D L) {
       if (sstate[i]) continue;   // CTA-uniform
       const Img2D& I = L.imgs[i];
       const int col0 = (t - stile[i]) * kTileCols;
-      col_tile_scan(I.Y, I.nf, I.ns, col0, tab[i][1], sline, L.line_stride);
+      col_tile_scan(I.Y, I.nf, I.ns, col0, tab[i][1], sframe[i][1], sline, L.line_stride);
       const int c = threadIdx.x & (kTileCols - 1);
       if (col0 + c < I.nf) {
         const XF* s = sline + c * L.line_stride;
-        ChunkPos q(threadIdx.x / kTileCols, (I.ns + 31) >> 5);
-        for (int r = threadIdx.x / kTileCols; r < I.ns; r += kThreads2 / kTileCols, q.next()) {
-          const int64_t p = (int64_t)r * I.nf + col0 + c;
-          const XF y = s[q.pos()];
-          const float m = load_m(I.a, p, L.in_f32);
-          I.U[p] = m > 0.f ? xf_norm(__fdividef(m, y.m), -y.e) : XF{0.f, kZeroExp};
+        const int r0 = threadIdx.x / kTileCols;
+        constexpr int dr = kThreads2 / kTileCols;
+        ChunkPos q(r0, (I.ns + 31) >> 5);
+        for (int rb = r0; rb < I.ns; rb += dr * kBatch) {
+          float mb[kBatch];
+#pragma unroll
+          for (int b = 0; b < kBatch; ++b)
+            if (rb + dr * b < I.ns) mb[b] = load_m(I.a, (int64_t)(rb + dr * b) * I.nf + col0 + c, L.in_f32);
+#pragma unroll
+          for (int b = 0; b < kBatch; ++b, q.next())
+            if (rb + dr * b < I.ns) {
+              const int64_t p = (int64_t)(rb + dr * b) * I.nf + col0 + c;
+              const XF y = s[q.pos()];
+              I.U[p] = mb[b] > 0.f ? xf_norm(__fdividef(mb[b], y.m), -y.e) : XF{0.f, kZeroExp};
+            }
         }
       }
       __syncthreads();   // the tile's shared memory is reused by the next tile
