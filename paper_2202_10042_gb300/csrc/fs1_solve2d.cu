@@ -49,7 +49,7 @@ namespace {
 constexpr int kThreads2 = 256;
 constexpr int kWarps2 = kThreads2 / 32;
 constexpr int kTileCols = kWarps2;   // columns of a slow-pass tile (one warp each)
-constexpr int kBatch = 6;            // global loads a thread keeps in flight when staging
+constexpr int kBatch = 4;            // epilogue loads a thread keeps in flight
 constexpr int kTab = 38;   // lam^0..lam^32, then lam^{P 2^i}, i < 5
 
 struct Img2D {
@@ -82,7 +82,10 @@ struct Launch2D {
   const int* row_off;  // [nimg + 1] prefix sums of ns
   const int* col_off;  // [nimg + 1] prefix sums of nf
   const int* tile_off; // [nimg + 1] prefix sums of ceil(nf / 8)
-  int line_stride;     // per-warp shared-memory region (XF): two chunked lines + 2
+  int line_stride;     // per-warp shared-memory region (XF): a staged line, its
+                       // backward partials, + 2 (== 2 mod 16)
+  int line_ch;         // XF of the longest staged line (32 P' of the longest line)
+  XF* tab;             // [nimg][2][kTab] decay tables, written by CTA 0 at start
   unsigned long long* bar;   // zeroed per launch
   int* abort_flag;
   long long spin_cap;
@@ -91,6 +94,13 @@ struct Launch2D {
 __device__ __forceinline__ float load_m(const void* p, int64_t i, int f32) {
   return f32 ? reinterpret_cast<const float*>(p)[i] : (float)reinterpret_cast<const double*>(p)[i];
 }
+
+// asynchronous 8-byte global -> shared copy (both addresses 8-byte aligned)
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ bool grid_barrier(const Launch2D& L, unsigned long long& gen, int* sm_ok) {
   __syncthreads();
@@ -319,17 +329,10 @@ __device__ void row_pass(const XF* in, XF* out, int L, const XF* tab, bool frame
   const int lane = threadIdx.x & 31;
   const int P = (L + 31) >> 5;
   {
-    // batches of kBatch loads in flight before their shared-memory stores
+    // every point of the row in flight at once (asynchronous copies)
     ChunkPos q(lane, P);
-    for (int j0 = lane; j0 < L; j0 += 32 * kBatch) {
-      XF v[kBatch];
-#pragma unroll
-      for (int b = 0; b < kBatch; ++b)
-        if (j0 + 32 * b < L) v[b] = in[j0 + 32 * b];
-#pragma unroll
-      for (int b = 0; b < kBatch; ++b, q.next())
-        if (j0 + 32 * b < L) s[q.pos()] = v[b];
-    }
+    for (int j = lane; j < L; j += 32, q.next()) cp_async8(s + q.pos(), in + j);
+    cp_async_wait_all();
   }
   __syncwarp();
   if (frame)
@@ -356,18 +359,10 @@ __device__ void col_tile_scan(const XF* Y, int nf, int ns, int col0, const XF* t
   const int CH = 32 * (P | 1);
   if (col0 + c < nf) {
     XF* s = sbuf + c * stride;
-    const int r0 = threadIdx.x / kTileCols;
-    constexpr int dr = kThreads2 / kTileCols;
-    ChunkPos q(r0, P);
-    for (int rb = r0; rb < ns; rb += dr * kBatch) {
-      XF v[kBatch];
-#pragma unroll
-      for (int b = 0; b < kBatch; ++b)
-        if (rb + dr * b < ns) v[b] = Y[(int64_t)(rb + dr * b) * nf + col0 + c];
-#pragma unroll
-      for (int b = 0; b < kBatch; ++b, q.next())
-        if (rb + dr * b < ns) s[q.pos()] = v[b];
-    }
+    ChunkPos q(threadIdx.x / kTileCols, P);
+    for (int r = threadIdx.x / kTileCols; r < ns; r += kThreads2 / kTileCols, q.next())
+      cp_async8(s + q.pos(), Y + (int64_t)r * nf + col0 + c);
+    cp_async_wait_all();
   }
   __syncthreads();
   if (col0 + warp < nf) {
@@ -394,11 +389,10 @@ __device__ void cta_sum_df(float& h, float& l, float* red) {
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kThreads2, 2) fs1_solve2d_kernel(Launch2D L) {
+__global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
   extern __shared__ XF sline[];   // kWarps2 regions of L.line_stride XF
   __shared__ float sred[2 * kWarps2];
   __shared__ int stile[kMaxImg2D + 1];
-  __shared__ XF tab[kMaxImg2D][2][kTab];   // [image][axis: 0 fast, 1 slow]
   __shared__ int srow[kMaxImg2D + 1], scol[kMaxImg2D + 1];
   __shared__ signed char sstate[kMaxImg2D];  // 0 active, 1 stops this iteration, 2 stopped earlier
   __shared__ bool sframe[kMaxImg2D][2];      // the axis takes the FP32-frame line scan (c P <= 40)
@@ -415,21 +409,24 @@ __global__ void __launch_bounds__(kThreads2, 2) fs1_solve2d_kernel(Launch2D L) {
     stile[i] = L.tile_off[i];
   }
   XF* const s_own = sline + warp * L.line_stride;            // this warp's region
-  XF* const t_own = s_own + (L.line_stride - 2) / 2;
+  XF* const t_own = s_own + L.line_ch;
   for (int t = threadIdx.x; t < nimg * 2; t += blockDim.x) {
     const Img2D& I = L.imgs[t >> 1];
     const int len = (t & 1) ? I.ns : I.nf;
     sframe[t >> 1][t & 1] = ((t & 1) ? I.cs : I.cf) * (double)((len + 31) >> 5) <= 40.0;
   }
-  for (int t = threadIdx.x; t < nimg * 2 * kTab; t += blockDim.x) {
+  // decay tables [image][axis: 0 fast, 1 slow][j] in global memory (CTA 0;
+  // the grid barrier below publishes them)
+  for (int t = threadIdx.x; blockIdx.x == 0 && t < nimg * 2 * kTab; t += blockDim.x) {
     const int i = t / (2 * kTab), ax = (t / kTab) & 1, j = t % kTab;
     const Img2D& I = L.imgs[i];
     const double c = ax == 0 ? I.cf : I.cs;
     const int len = ax == 0 ? I.nf : I.ns;
     const int P = (len + 31) >> 5;
     const double k = j <= 32 ? (double)j : (double)P * (double)(1 << (j - 33));
-    tab[i][ax][j] = c_decay(k, c, XF{});
+    L.tab[t] = c_decay(k, c, XF{});
   }
+  auto tab = [&](int i, int ax) -> const XF* { return L.tab + (i * 2 + ax) * kTab; };
   // u = v = 1 / (n_fast n_slow)  (Algorithm 2, line 1), or a warm start
   for (int i = 0; i < nimg; ++i) {
     const Img2D& I = L.imgs[i];
@@ -457,7 +454,7 @@ __global__ void __launch_bounds__(kThreads2, 2) fs1_solve2d_kernel(Launch2D L) {
       if (sstate[i]) continue;
       const Img2D& I = L.imgs[i];
       const int64_t o = (int64_t)(t - srow[i]) * I.nf;
-      row_pass(I.U + o, I.Y + o, I.nf, tab[i][0], sframe[i][0], s_own, t_own);
+      row_pass(I.U + o, I.Y + o, I.nf, tab(i, 0), sframe[i][0], s_own, t_own);
     }
     if (!grid_barrier(L, gen, &sok)) return;
     // ---- v-half, slow pass: y = (K_s (x) I) Y, v_new = b / y, error partials
@@ -467,7 +464,7 @@ __global__ void __launch_bounds__(kThreads2, 2) fs1_solve2d_kernel(Launch2D L) {
       const Img2D& I = L.imgs[i];
       const int tile = t - stile[i];
       const int col0 = tile * kTileCols;
-      col_tile_scan(I.Y, I.nf, I.ns, col0, tab[i][1], sframe[i][1], sline, L.line_stride);
+      col_tile_scan(I.Y, I.nf, I.ns, col0, tab(i, 1), sframe[i][1], sline, L.line_stride);
       XF* Vn = I.V[par ^ 1];
       float eh = 0.f, el = 0.f;
       const int c = threadIdx.x & (kTileCols - 1);
@@ -534,7 +531,7 @@ __global__ void __launch_bounds__(kThreads2, 2) fs1_solve2d_kernel(Launch2D L) {
       if (sstate[i]) continue;
       const Img2D& I = L.imgs[i];
       const int64_t o = (int64_t)(t - srow[i]) * I.nf;
-      row_pass(I.V[par ^ 1] + o, I.Y + o, I.nf, tab[i][0], sframe[i][0], s_own, t_own);
+      row_pass(I.V[par ^ 1] + o, I.Y + o, I.nf, tab(i, 0), sframe[i][0], s_own, t_own);
     }
     if (!grid_barrier(L, gen, &sok)) return;
     // ---- u-half, slow pass: u = a / ((K_s (x) I) Y)
@@ -543,7 +540,7 @@ __global__ void __launch_bounds__(kThreads2, 2) fs1_solve2d_kernel(Launch2D L) {
       if (sstate[i]) continue;   // CTA-uniform
       const Img2D& I = L.imgs[i];
       const int col0 = (t - stile[i]) * kTileCols;
-      col_tile_scan(I.Y, I.nf, I.ns, col0, tab[i][1], sframe[i][1], sline, L.line_stride);
+      col_tile_scan(I.Y, I.nf, I.ns, col0, tab(i, 1), sframe[i][1], sline, L.line_stride);
       const int c = threadIdx.x & (kTileCols - 1);
       if (col0 + c < I.nf) {
         const XF* s = sline + c * L.line_stride;
@@ -581,9 +578,9 @@ __global__ void __launch_bounds__(kThreads2, 2) fs1_solve2d_kernel(Launch2D L) {
     const Img2D& I = L.imgs[i];
     const int k = (ld_relaxed(I.stop) - 1) & 1;
     const int64_t o = (int64_t)(t - srow[i]) * I.nf;
-    line_scan_global<true>(I.V[k] + o, I.Y + o, I.R + o, 1, I.nf, tab[i][0]);
+    line_scan_global<true>(I.V[k] + o, I.Y + o, I.R + o, 1, I.nf, tab(i, 0));
     __syncwarp();
-    line_scan_global<false>(I.V[k] + o, I.V[k ^ 1] + o, I.R + o, 1, I.nf, tab[i][0]);
+    line_scan_global<false>(I.V[k] + o, I.V[k ^ 1] + o, I.R + o, 1, I.nf, tab(i, 0));
   }
   if (!grid_barrier(L, gen, &sok)) return;
   // columns: h_fast u.(K_s (x) I) Y + h_slow u.(K_s^(c) (x) I) V[k^1]
@@ -593,7 +590,7 @@ __global__ void __launch_bounds__(kThreads2, 2) fs1_solve2d_kernel(Launch2D L) {
     const int k = (ld_relaxed(I.stop) - 1) & 1;
     const int col = t - scol[i];
     double acc = 0.0;
-    line_scan_global<false>(I.Y + col, I.R + col, I.R + col, I.nf, I.ns, tab[i][1]);
+    line_scan_global<false>(I.Y + col, I.R + col, I.R + col, I.nf, I.ns, tab(i, 1));
     __syncwarp();
     for (int r = lane; r < I.ns; r += 32) {
       const int64_t p = (int64_t)r * I.nf + col;
@@ -601,7 +598,7 @@ __global__ void __launch_bounds__(kThreads2, 2) fs1_solve2d_kernel(Launch2D L) {
       acc += I.hf * ldexp((double)u.m * (double)w.m, u.e + w.e);
     }
     __syncwarp();
-    line_scan_global<true>(I.V[k ^ 1] + col, I.R + col, I.R + col, I.nf, I.ns, tab[i][1]);
+    line_scan_global<true>(I.V[k ^ 1] + col, I.R + col, I.R + col, I.nf, I.ns, tab(i, 1));
     __syncwarp();
     for (int r = lane; r < I.ns; r += 32) {
       const int64_t p = (int64_t)r * I.nf + col;
@@ -641,7 +638,8 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 }  // namespace
 
 size_t solve2d_workspace(const PairDesc* d, int count) {
-  size_t b = align256(sizeof(Img2D) * count) + 3 * align256(sizeof(int) * (count + 1)) + 256 + 256;
+  size_t b = align256(sizeof(Img2D) * count) + 3 * align256(sizeof(int) * (count + 1)) + 256 + 256 +
+             align256(sizeof(XF) * 2 * kTab * count);
   for (int i = 0; i < count; ++i) {
     const size_t n = (size_t)d[i].n_fast * d[i].n_slow;
     b += 5 * align256(sizeof(XF) * n) + align256(sizeof(float) * 2 * d[i].n_fast) +
@@ -670,9 +668,12 @@ int launch_solve_2d(const PairDesc* d, int count, int in_f32, PairResult* result
   p += 256;
   int* d_abort = (int*)p;
   p += 256;
+  XF* d_tab = (XF*)p;
+  p += align256(sizeof(XF) * 2 * kTab * count);
   std::vector<Img2D> imgs(count);
   std::vector<int> row(count + 1, 0), col(count + 1, 0), tile(count + 1, 0);
   int pp_max = 1;
+  bool any_ext = false;   // some axis takes the per-point extended-range scan (XF partials)
   char* stops = nullptr;
   for (int i = 0; i < count; ++i) {
     const PairDesc& D = d[i];
@@ -707,6 +708,7 @@ int launch_solve_2d(const PairDesc* d, int count, int in_f32, PairResult* result
     col[i + 1] = col[i] + I.nf;
     tile[i + 1] = tile[i] + (I.nf + kTileCols - 1) / kTileCols;
     pp_max = std::max(pp_max, std::max((I.nf + 31) / 32, (I.ns + 31) / 32) | 1);
+    any_ext = any_ext || I.cf * ((I.nf + 31) / 32) > 40.0 || I.cs * ((I.ns + 31) / 32) > 40.0;
   }
   cudaError_t e = cudaSuccess;
   for (int i = 0; i < count && e == cudaSuccess; ++i) e = cudaMemsetAsync(imgs[i].stop, 0, sizeof(int), st);
@@ -720,9 +722,14 @@ int launch_solve_2d(const PairDesc* d, int count, int in_f32, PairResult* result
     fprintf(stderr, "fs1: 2D setup failed: %s\n", cudaGetErrorString(e));
     return FS1_ECUDA;
   }
-  const int line_stride = 2 * 32 * pp_max + 2;   // == 2 (mod 16): the tile's warps start in different banks
+  // per-warp region: the staged line (CH XF) and its backward partials (CH XF
+  // for the extended-range scan, CH floats for the frame scan), + 2 so that
+  // the stride is 2 mod 16 and the tile's warps start in different banks
+  const int line_ch = 32 * pp_max;
+  const int line_stride = line_ch + (any_ext ? line_ch : line_ch / 2) + 2;
   const size_t smem = sizeof(XF) * (size_t)kWarps2 * line_stride;
-  Launch2D L{d_imgs, results, count, in_f32, d_row, d_col, d_tile, line_stride, d_bar, d_abort, spin_cap};
+  Launch2D L{d_imgs, results, count, in_f32, d_row, d_col, d_tile, line_stride, line_ch, d_tab, d_bar, d_abort,
+             spin_cap};
   e = cudaFuncSetAttribute(fs1_solve2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0, dev = 0, sms = 0;
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fs1_solve2d_kernel, kThreads2, smem);
