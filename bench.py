@@ -13,6 +13,14 @@ fs1_solve_batch; --workload picks one, 2 is the default and the headline):
      floor, stabilised FP32, one persistent launch
   4  64 2D pairs on a 512 x 512 grid (h = 1/512), eps = 1e-3, images of 1-5
      anisotropic Gaussian blobs + 1e-7 floor, stabilised FP32 (Algorithm 2)
+  6  replay of the paper's Section 5.1 (Table 1): 100 pairs of U[0, 1]
+     histograms on [-3, 3], N = 8000, eps = 1e-3, 1000 iterations
+  7  replay of Section 5.2 (Table 2): the Ricker pair, N = 8000, eps = 1e-2,
+     500 iterations, 100 repeats
+  8  replay of Section 5.3 (Table 3): 64 pairs of 160 x 160 U[0, 1] images,
+     h = 1, eps = 1e-2, 1000 iterations
+For 6-8 vs_baseline is the ratio to the FS-1 rate the paper's tables imply on
+its CPU (context: another machine).
 The serving workload is measured by `python -m paper_2202_10042_gb300.serve`.
 
 Metric: N*iterations per second (sum over pairs of grid points x iterations /
@@ -71,14 +79,28 @@ WORKLOADS = {
             dtype="f32", bytes_per_nit=28.0, kw={}, sample_pairs=64, sample_iters=200, solo=64),
     4: dict(name="fs1_2d_log_fp32_batch64_512x512_eps1e-3", pairs=64, variant="log", precision="fp32",
             dtype="f32", bytes_per_nit=28.0, kw={}, sample_pairs=4, sample_iters=40, solo=4),
+    # replays of the paper's Section 5 experiments; `paper` is the FS-1 rate its
+    # tables imply on its CPU (grid points x iterations / printed time)
+    6: dict(name="paper_e1_1d_random_n8000_eps1e-3_it1000", pairs=100, variant="log", precision="fp32",
+            dtype="f32", bytes_per_nit=28.0, kw={}, sample_pairs=4, sample_iters=1000, solo=8,
+            paper=8000 * 1000 / 1.53e-1),
+    7: dict(name="paper_e2_ricker_n8000_eps1e-2_it500", pairs=100, variant="log", precision="fp32",
+            dtype="f32", bytes_per_nit=28.0, kw={}, sample_pairs=4, sample_iters=500, solo=8,
+            paper=8000 * 500 / 5.96e-2),
+    8: dict(name="paper_e3_2d_random_160x160_h1_eps1e-2_it1000", pairs=64, variant="log", precision="fp32",
+            dtype="f32", bytes_per_nit=28.0, kw={}, sample_pairs=4, sample_iters=200, solo=4,
+            paper=160 * 160 * 1000 / 1.08),
 }
+
+GENERATORS = {1: inputs.workload1, 2: inputs.workload2, 3: inputs.workload3, 4: inputs.workload4,
+              6: inputs.paper_e1, 7: inputs.paper_e2, 8: inputs.paper_e3}
 
 
 def gen_problem(workload: int, index: int, **over):
     W = WORKLOADS[workload]
     kw = dict(W["kw"])
     kw.update({k: v for k, v in over.items() if v is not None})
-    return getattr(inputs, f"workload{workload}")(index, **kw)
+    return GENERATORS[workload](index, **kw)
 
 
 # ---------------------------------------------------------------------------
@@ -406,7 +428,8 @@ def run_gpu(args):
             cfg.update({"n": p0.a.size, "eps": p0.eps, "tol": p0.tol, "itr_max": p0.itr_max})
         line = {"metric": METRIC, "value": value, "unit": "N*iters/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": W["dtype"],
+                "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": value / W["paper"] if "paper" in W else None, "dtype": W["dtype"],
                 "data": "synthetic", "config": cfg,
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,

@@ -28,6 +28,19 @@ Workloads (ids match the order in which they are listed in the design doc):
      log-uniform in [1e3, 1e6], half 2D with side log-uniform in [64, 1024];
      smooth Gaussian-mixture histograms; eps log-uniform in [1e-4, 1e-2];
      tol 1e-6, cap 5000.
+
+Replays of the paper's own synthetic experiments (Section 5; their grid is
+the node grid x_i = (i - 1) dx - 3, dx = 6 / (N - 1) on [-3, 3] of Section 5.1):
+  6  1D random distributions (Section 5.1, Table 1): u_i, v_j ~ U[0, 1],
+     normalised to mass 1; eps = 1e-3; 1000 iterations.
+  7  Ricker wavelets (Section 5.2, Table 2): R(t) = A (1 - 2 pi^2 f0^2 t^2)
+     exp(-pi^2 f0^2 t^2) with f0 = A = 1 and its translate R(t - s),
+     s = -1.2032, squared and normalised by eq. "ricker" with delta = 1e-3 and
+     L = N (the value that makes the total mass 1); eps = 1e-2; 500
+     iterations.  The paper does not state the t-range: the Section 5.1 grid
+     is used.
+  8  2D random distributions (Section 5.3, Table 3): N x N U[0, 1] values
+     normalised to mass 1, h_1 = h_2 = 1, eps = 1e-2; 1000 iterations.
 """
 from __future__ import annotations
 
@@ -196,6 +209,50 @@ def workload5(index: int, arrival: float = 0.0, tol: float = 1e-6, itr_max: int 
     return p
 
 
+def paper_grid(n: int):
+    """Node grid of Section 5.1: x_i = (i - 1) dx - 3, dx = 6 / (N - 1)."""
+    dx = 6.0 / (n - 1)
+    return -3.0 + dx * np.arange(n, dtype=np.float64), dx
+
+
+def paper_e1(index: int = 0, n: int = 8000, eps: float = 1e-3, itr_max: int = 1000) -> Problem:
+    """Section 5.1: U[0, 1] weights on the node grid of [-3, 3], normalised."""
+    ra, rb, _ = _rng_pair(6, index)
+    a = _normalise(ra.uniform(0.0, 1.0, size=n))
+    b = _normalise(rb.uniform(0.0, 1.0, size=n))
+    return Problem(a, b, (6.0 / (n - 1),), eps, 0.0, itr_max, 1, (n,), 6, index)
+
+
+def ricker(t: np.ndarray, f0: float = 1.0, amp: float = 1.0) -> np.ndarray:
+    """Ricker wavelet of Section 5.2."""
+    q = (math.pi * f0 * t) ** 2
+    return amp * (1.0 - 2.0 * q) * np.exp(-q)
+
+
+def ricker_normalise(f: np.ndarray, delta: float) -> np.ndarray:
+    """Eq. "ricker": (f^2 / ||f^2||_1 + delta) / (1 + L delta) with L = N."""
+    f2 = f * f
+    return (f2 / f2.sum(dtype=np.float64) + delta) / (1.0 + f.size * delta)
+
+
+def paper_e2(index: int = 0, n: int = 8000, eps: float = 1e-2, itr_max: int = 500,
+             shift: float = -1.2032, delta: float = 1e-3) -> Problem:
+    """Section 5.2: the Ricker wavelet and its translate (deterministic; the
+    index only labels repeats)."""
+    x, dx = paper_grid(n)
+    a = ricker_normalise(ricker(x), delta)
+    b = ricker_normalise(ricker(x - shift), delta)
+    return Problem(a, b, (dx,), eps, 0.0, itr_max, 1, (n,), 7, index)
+
+
+def paper_e3(index: int = 0, side: int = 160, eps: float = 1e-2, itr_max: int = 1000) -> Problem:
+    """Section 5.3: N x N U[0, 1] values, h_1 = h_2 = 1, normalised."""
+    ra, rb, _ = _rng_pair(8, index)
+    a = _normalise(ra.uniform(0.0, 1.0, size=(side, side)))
+    b = _normalise(rb.uniform(0.0, 1.0, size=(side, side)))
+    return Problem(a, b, (1.0, 1.0), eps, 0.0, itr_max, 2, (side, side), 8, index)
+
+
 def product_pair_2d(index: int, nx: int, ny: int, floor: float = 1e-3):
     """Separable 2D pair a = a_y (x) a_x, b = b_y (x) b_x, with its 1D factors.
 
@@ -227,5 +284,6 @@ def random_pair_1d(index: int, n: int, floor: float = 0.0, zeros: int = 0):
 
 
 def batch(workload: int, indices, **kw) -> List[Problem]:
-    fn = {1: workload1, 2: workload2, 3: workload3, 4: workload4}[workload]
+    fn = {1: workload1, 2: workload2, 3: workload3, 4: workload4, 6: paper_e1, 7: paper_e2,
+          8: paper_e3}[workload]
     return [fn(i, **kw) for i in indices]
