@@ -12,7 +12,8 @@ arithmetic.
 Contents
   dense       the plain definitions: Gibbs kernel, ground cost, dense Sinkhorn
               (plain and log-domain twin) in the loop order of Algorithm 1 / 2,
-              marginal error, transport cost.  FP64, O(N^2) per iteration.
+              marginal error, transport cost, in 1D, 2D and 3D (the third axis
+              of Section 4's closing remark).  FP64, O(N^2) per iteration.
   exact       closed forms that pin the above: exact 1D W1 from the CDFs,
               brute-force LP, entropy.
   recurrence  Algorithm 1 and Algorithm 2 with the Horner / Qin Jiushao
@@ -21,8 +22,9 @@ Contents
               recurrences, and the O(N) transport-cost recurrence.
   cref        ctypes wrapper of fs1_ref.c: the same sequential recurrences in
               plain C99 FP64 (plain form and the stabilised form of the Remark
-              in Section 3), fast enough for N = 2^20 and 512 x 512 grids.
+              in Section 3), in 1D, 2D and 3D, fast enough for N = 2^20 and
+              512 x 512 grids.
 
-Every function states the passage of the paper it follows.  Readings of
-passages that are silent, ambiguous or garbled are listed in the design doc.
+Every function states the passage of the paper it follows, and where the
+paper is silent or ambiguous, the reading it takes.
 """

@@ -6,9 +6,9 @@ Notation: a, b are the two histograms (the paper's u, v of Section 2); u, v
 are the Sinkhorn scalings (the paper's phi, psi); f = log u, g = log v are the
 dimensionless log potentials.
 
-Parity: pinned by tests/test_oracle_dense.py against the exact W1 (CDF), a
-brute-force LP, the entropic gap bound, marginal invariants and the 2D
-product factorisation.
+Parity: pinned by tests/test_oracle_pins.py against the exact W1 (CDF), a
+brute-force LP (1D, 2D and 3D grids), the entropic gap bound, marginal
+invariants, and the 2D and 3D product factorisations.
 """
 from __future__ import annotations
 
@@ -62,6 +62,27 @@ def gibbs_kernel_2d(n_fast: int, n_slow: int, h_fast: float, h_slow: float, eps:
     k0 = gibbs_kernel_1d(n_fast, h_fast, eps)
     k2 = gibbs_kernel_1d(n_slow, h_slow, eps)
     return np.kron(k2, k0)
+
+
+def ground_cost_3d(n_fast: int, n_mid: int, n_slow: int, h_fast: float, h_mid: float,
+                   h_slow: float) -> np.ndarray:
+    """Cost |di| h1 + |dj| h2 + |dk| h3 on an n_fast x n_mid x n_slow grid: the
+    L1 cost of Section 4 extended to a third axis (its closing remark).
+    Points are flattened fast axis first, as numpy's C order of an
+    (n_slow, n_mid, n_fast) array."""
+    cf = ground_cost_1d(n_fast, h_fast)
+    cm = ground_cost_1d(n_mid, h_mid)
+    cs = ground_cost_1d(n_slow, h_slow)
+    n = n_fast * n_mid * n_slow
+    return (cs[:, None, None, :, None, None] + cm[None, :, None, None, :, None] +
+            cf[None, None, :, None, None, :]).reshape(n, n)
+
+
+def gibbs_kernel_3d(n_fast: int, n_mid: int, n_slow: int, h_fast: float, h_mid: float,
+                    h_slow: float, eps: float) -> np.ndarray:
+    """K = K_slow (x) K_mid (x) K_fast, the separable kernel of the 3D cost."""
+    return np.kron(gibbs_kernel_1d(n_slow, h_slow, eps),
+                   np.kron(gibbs_kernel_1d(n_mid, h_mid, eps), gibbs_kernel_1d(n_fast, h_fast, eps)))
 
 
 # ---------------------------------------------------------------------------
@@ -159,6 +180,18 @@ def solve_2d(a2, b2, h_fast: float, h_slow: float, eps: float, tol: float, itr_m
     C = ground_cost_2d(nf, ns, h_fast, h_slow)
     a = np.asarray(a2, dtype=np.float64).reshape(-1)
     b = np.asarray(b2, dtype=np.float64).reshape(-1)
+    if log:
+        return sinkhorn_dense_log(a, b, C, eps, tol, itr_max)
+    return sinkhorn_dense(a, b, np.exp(-C / eps), C, tol, itr_max)
+
+
+def solve_3d(a3, b3, h, eps: float, tol: float, itr_max: int, log: bool = False) -> SinkhornResult:
+    """a3, b3: (n_slow, n_mid, n_fast) arrays (fast axis contiguous);
+    h = (h_fast, h_mid, h_slow)."""
+    ns, nm, nf = a3.shape
+    C = ground_cost_3d(nf, nm, ns, h[0], h[1], h[2])
+    a = np.asarray(a3, dtype=np.float64).reshape(-1)
+    b = np.asarray(b3, dtype=np.float64).reshape(-1)
     if log:
         return sinkhorn_dense_log(a, b, C, eps, tol, itr_max)
     return sinkhorn_dense(a, b, np.exp(-C / eps), C, tol, itr_max)

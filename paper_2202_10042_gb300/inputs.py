@@ -13,7 +13,7 @@ Grids are cell centred: x_i = (i + 1/2) h with h = 1/N on [0, 1] (2D: h = 1/side
 on both axes).  Densities are evaluated at the cell centres, a floor is added in
 density units, and the histogram is normalised to total mass 1 in float64.
 
-Workloads (ids match the order in which they are listed in the design doc):
+Workloads (ids are the ones bench.py takes with --workload):
   1  1D, N = 1000, eps = 1e-2: 2-component Gaussian mixtures,
      mu ~ U[0.2, 0.8], sigma ~ U[0.03, 0.1], floor 1e-4; 1000 iterations.
   2  1D, N = 2^20, eps = 1e-4: 3-component Gaussian mixtures, floor 1e-6;
@@ -266,6 +266,17 @@ def product_pair_2d(index: int, nx: int, ny: int, floor: float = 1e-3):
     bx = gaussian_mixture_1d(rb, nx, 2, floor)
     by = gaussian_mixture_1d(rb, ny, 2, floor)
     return np.outer(ay, ax), np.outer(by, bx), (ax, bx), (ay, by)
+
+
+def product_pair_3d(index: int, nx: int, ny: int, nz: int, floor: float = 1e-3):
+    """Separable 3D pair a = a_z (x) a_y (x) a_x (and b likewise) with its 1D
+    factors; 3D arrays are (nz, ny, nx), the x axis contiguous."""
+    ra, rb, _ = _rng_pair(42, index)
+    fa = [gaussian_mixture_1d(ra, n, 2, floor) for n in (nx, ny, nz)]
+    fb = [gaussian_mixture_1d(rb, n, 2, floor) for n in (nx, ny, nz)]
+    a3 = np.einsum("k,j,i->kji", fa[2], fa[1], fa[0])
+    b3 = np.einsum("k,j,i->kji", fb[2], fb[1], fb[0])
+    return a3, b3, tuple(zip(fa, fb))
 
 
 def random_pair_1d(index: int, n: int, floor: float = 0.0, zeros: int = 0):

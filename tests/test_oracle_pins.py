@@ -365,3 +365,103 @@ def test_cref_workload1_full():
     assert _rel(rc.w, rd.w) < 1e-12
     W1 = exact.w1_exact_1d(p.a, p.b, h)
     assert rc.w >= W1 - (p.a.size - 1) * h * rc.err - 1e-12
+
+
+# ---------------------------------------------------------------------------
+# 3D: the extension to a third axis stated by Section 4's closing remark
+# ---------------------------------------------------------------------------
+
+def test_3d_ground_cost_and_kernel_structure():
+    """The 3D cost is the sum of the axis distances (brute force over the
+    coordinates of the fast-first flattening) and K = exp(-C / eps) is the
+    Kronecker product of the three 1D kernels."""
+    nf, nm, ns, h = 3, 4, 2, (0.1, 0.2, 0.3)
+    C = dense.ground_cost_3d(nf, nm, ns, *h)
+    pts = [(i, j, k) for k in range(ns) for j in range(nm) for i in range(nf)]
+    for p, (i1, j1, k1) in enumerate(pts):
+        for q, (i2, j2, k2) in enumerate(pts):
+            assert C[p, q] == pytest.approx(abs(i1 - i2) * h[0] + abs(j1 - j2) * h[1] + abs(k1 - k2) * h[2],
+                                            abs=1e-15)
+    assert np.allclose(np.exp(-C / 0.7), dense.gibbs_kernel_3d(nf, nm, ns, *h, 0.7), rtol=1e-13, atol=0)
+
+
+def test_lp_3d_small_grid():
+    """3D L1 cost on a 3 x 2 x 2 grid: the entropic value approaches the LP."""
+    rng = np.random.default_rng(17)
+    a3 = rng.uniform(0.1, 1, (2, 2, 3)); a3 /= a3.sum()
+    b3 = rng.uniform(0.1, 1, (2, 2, 3)); b3 /= b3.sum()
+    h = (1 / 3, 0.5, 0.5)
+    C = dense.ground_cost_3d(3, 2, 2, *h)
+    lp = exact.w1_lp(a3.reshape(-1), b3.reshape(-1), C)
+    r = dense.solve_3d(a3, b3, h, 0.01, 1e-13, 200000, log=True)
+    H = min(exact.entropy(a3), exact.entropy(b3))
+    gap = r.w - lp
+    assert -1e-9 <= gap <= 0.01 * H + 1e-9
+
+
+def test_3d_product_factorisation():
+    """Separable inputs keep the iterates in product form at every l, so
+    W_3D = m_y m_z W_x + m_x m_z W_y + m_x m_y W_z with m the 1D plan masses;
+    after the first u-update every mass is 1."""
+    a3, b3, ((ax, bx), (ay, by), (az, bz)) = inputs.product_pair_3d(0, 7, 5, 4)
+    h, eps = (1 / 7, 1 / 5, 1 / 4), 0.1
+    Ks = [dense.gibbs_kernel_1d(n, hh, eps) for n, hh in zip((7, 5, 4), h)]
+    for it in (0, 1, 3, 10):
+        r3 = dense.solve_3d(a3, b3, h, eps, 0.0, it)
+        rs = [dense.solve_1d(p, q, hh, eps, 0.0, it) for (p, q), hh in zip(((ax, bx), (ay, by), (az, bz)), h)]
+        u = np.einsum("k,j,i->kji", rs[2].u, rs[1].u, rs[0].u)
+        assert np.allclose(r3.u.reshape(4, 5, 7), u, rtol=1e-12, atol=0)
+        m = [float(r.u @ K @ r.v) for r, K in zip(rs, Ks)]
+        want = m[1] * m[2] * rs[0].w + m[0] * m[2] * rs[1].w + m[0] * m[1] * rs[2].w
+        assert _rel(r3.w, want) < 1e-12
+        if it >= 1:
+            assert _rel(r3.w, rs[0].w + rs[1].w + rs[2].w) < 1e-12
+
+
+def test_3d_single_slab_is_2d():
+    rng = np.random.default_rng(19)
+    a2 = rng.uniform(0.05, 1, (5, 6)); a2 /= a2.sum()
+    b2 = rng.uniform(0.05, 1, (5, 6)); b2 /= b2.sum()
+    r3 = dense.solve_3d(a2[None], b2[None], (1 / 6, 1 / 5, 0.7), 0.05, 0.0, 25)
+    r2 = dense.solve_2d(a2, b2, 1 / 6, 1 / 5, 0.05, 0.0, 25)
+    assert _rel(r3.w, r2.w) < 1e-13 and r3.iters == r2.iters
+
+
+def test_cref_matvec_3d():
+    rng = np.random.default_rng(23)
+    x3 = rng.uniform(0, 1, (3, 4, 5))
+    h, eps = (0.1, 0.2, 0.3), 0.25
+    K3 = dense.gibbs_kernel_3d(5, 4, 3, *h, eps)
+    assert np.allclose(cref.matvec(x3, h, eps).reshape(-1), K3 @ x3.reshape(-1), rtol=1e-13, atol=0)
+    for ax in range(3):
+        unit = [0.0, 0.0, 0.0]
+        unit[ax] = 1.0
+        D = dense.ground_cost_3d(5, 4, 3, *unit)
+        got = cref.matvec(x3, h, eps, weighted_axes=1 << ax).reshape(-1)
+        assert np.allclose(got, (K3 * D) @ x3.reshape(-1), rtol=1e-12, atol=1e-300)
+
+
+@pytest.mark.parametrize("tau", [math.inf, 10.0])
+def test_cref_3d_equals_dense(tau):
+    rng = np.random.default_rng(29)
+    a3 = rng.uniform(0.05, 1, (4, 5, 6)); a3 /= a3.sum()
+    b3 = rng.uniform(0.05, 1, (4, 5, 6)); b3 /= b3.sum()
+    h, eps = (1 / 6, 1 / 5, 1 / 4), 0.04
+    rd = dense.solve_3d(a3, b3, h, eps, 0.0, 30, log=True)
+    rc = cref.solve(a3, b3, h, eps, 0.0, 30, tau=tau)
+    assert rc.status == cref.OK and rc.iters == rd.iters == 30
+    assert _rel(rc.w, rd.w) < 1e-11
+    assert abs(rc.err - rd.err) <= 1e-11 * max(1.0, rd.err)
+    # the stop rule on the 3D marginal error
+    rt = cref.solve(a3, b3, h, eps, 1e-6, 5000, tau=tau)
+    rdt = dense.solve_3d(a3, b3, h, eps, 1e-6, 5000, log=True)
+    assert rt.iters == rdt.iters and rt.err <= 1e-6
+
+
+def test_cref_3d_product_equals_three_1d():
+    a3, b3, ((ax, bx), (ay, by), (az, bz)) = inputs.product_pair_3d(1, 9, 6, 5)
+    h, eps = (1 / 9, 1 / 6, 1 / 5), 0.05
+    r3 = cref.solve(a3, b3, h, eps, 0.0, 40, tau=math.inf)
+    r1 = [cref.solve(p, q, hh, eps, 0.0, 40, tau=math.inf)
+          for (p, q), hh in zip(((ax, bx), (ay, by), (az, bz)), h)]
+    assert _rel(r3.w, sum(r.w for r in r1)) < 1e-12
