@@ -19,6 +19,8 @@ fs1_solve_batch; --workload picks one, 2 is the default and the headline):
      500 iterations, 100 repeats
   8  replay of Section 5.3 (Table 3): 64 pairs of 160 x 160 U[0, 1] images,
      h = 1, eps = 1e-2, 1000 iterations
+  9  32 3D grids of 64^3 cells, eps = 2e-3, 1-3 Gaussian blobs + 1e-7 floor,
+     stabilised FP32, marginal error 1e-6 or 2000 iterations
 For 6-8 vs_baseline is the ratio to the FS-1 rate the paper's tables imply on
 its CPU (context: another machine).
 The serving workload is measured by `python -m paper_2202_10042_gb300.serve`.
@@ -90,10 +92,12 @@ WORKLOADS = {
     8: dict(name="paper_e3_2d_random_160x160_h1_eps1e-2_it1000", pairs=64, variant="log", precision="fp32",
             dtype="f32", bytes_per_nit=28.0, kw={}, sample_pairs=4, sample_iters=200, solo=4,
             paper=160 * 160 * 1000 / 1.08),
+    9: dict(name="fs1_3d_log_fp32_batch32_64^3_eps2e-3", pairs=32, variant="log", precision="fp32",
+            dtype="f32", bytes_per_nit=28.0, kw={}, sample_pairs=4, sample_iters=20, solo=2),
 }
 
 GENERATORS = {1: inputs.workload1, 2: inputs.workload2, 3: inputs.workload3, 4: inputs.workload4,
-              6: inputs.paper_e1, 7: inputs.paper_e2, 8: inputs.paper_e3}
+              6: inputs.paper_e1, 7: inputs.paper_e2, 8: inputs.paper_e3, 9: inputs.workload9}
 
 
 def gen_problem(workload: int, index: int, **over):
@@ -232,7 +236,7 @@ def oracle_sample(workload, pairs_idx, iters, workers):
     data = [gen_problem(workload, i) for i in pairs_idx]
     tau = math.inf if W["variant"] == "plain" else 1e10
     t0 = time.perf_counter()
-    res = cref.solve_many([(p.a, p.b, p.h if p.ndim == 2 else p.h[0], p.eps, 0.0, iters) for p in data],
+    res = cref.solve_many([(p.a, p.b, p.h if p.ndim >= 2 else p.h[0], p.eps, 0.0, iters) for p in data],
                           workers=workers, tau=tau)
     dt = time.perf_counter() - t0
     nit = sum(p.a.size * r.iters for p, r in zip(data, res))
@@ -302,7 +306,7 @@ def run_gpu(args):
                         autotune=not args.no_autotune, use_graph=not args.no_graph)
 
     def hgrid(p):
-        return tuple(p.h) if p.ndim == 2 else p.h[0]
+        return tuple(p.h) if p.ndim >= 2 else p.h[0]
 
     # device-resident inputs
     dev_t = [(torch.from_numpy(p.a).to(dev, tdt), torch.from_numpy(p.b).to(dev, tdt)) for p in host]

@@ -85,16 +85,20 @@ typedef struct fs1_config {
 } fs1_config;
 
 typedef struct fs1_problem {
-  int ndim;             /* 1 (Algorithm 1) or 2 (Algorithm 2) */
+  int ndim;             /* 1 (Algorithm 1), 2 (Algorithm 2) or 3 (Algorithm 2 with a
+                           third axis: the extension the closing remark of Section 4
+                           states, K = K_slow (x) K_mid (x) K_fast) */
   int dtype;            /* enum fs1_precision of a and b */
   int location;         /* enum fs1_location of a, b and the optional arrays */
   int reserved;
-  int64_t n[2];         /* n[0]: points along the fast (contiguous) axis; n[1]: along
-                           the slow axis (1 in 1D).  2D arrays are n[1] rows of n[0]
-                           contiguous values: the paper's column-major flattening with
-                           its first index (spacing h[0]) running fastest.  2D sides
-                           above 1024 give FS1_EUNSUPPORTED */
-  double h[2];          /* grid spacings (h[1] unused in 1D) */
+  int64_t n[3];         /* n[0]: points along the fast (contiguous) axis.  2D: n[1]
+                           along the slow axis; arrays are n[1] rows of n[0] contiguous
+                           values, the paper's column-major flattening with its first
+                           index (spacing h[0]) running fastest.  3D: n[1] along the
+                           middle axis, n[2] along the slow one; arrays are n[2] slabs
+                           of n[1] rows of n[0].  Unused entries are ignored.  2D / 3D
+                           axes longer than 1024 give FS1_EUNSUPPORTED */
+  double h[3];          /* grid spacings of the axes in the order of n */
   double eps;           /* entropic regularisation, > 0 */
   double tol;           /* stop when the column-marginal L1 error <= tol (>= 0) */
   int64_t itr_max;      /* iteration cap (>= 0) */
@@ -135,7 +139,7 @@ fs1_status fs1_config_default(fs1_config* cfg);
  * when that environment variable names a readable file). */
 fs1_status fs1_create(const fs1_config* cfg, fs1_handle** out);
 
-/* Solve one problem (Algorithm 1 in 1D, Algorithm 2 in 2D).
+/* Solve one problem (Algorithm 1 in 1D, Algorithm 2 in 2D and 3D).
  * w1_out: host double, may be NULL.  info_out: host, may be NULL.
  * Returns the problem's status (FS1_ENOTCONV is a warning; w1 is valid). */
 fs1_status fs1_w1(fs1_handle* h, const fs1_problem* prob, double* w1_out, fs1_info* info_out);
@@ -144,8 +148,8 @@ fs1_status fs1_w1(fs1_handle* h, const fs1_problem* prob, double* w1_out, fs1_in
  * ONE persistent launch whatever their sizes: they are put in classes by the
  * fewest CTAs that hold a pair on chip, the GPU's CTAs are split over the
  * classes in proportion to their work (N * itr_max), and each class's teams
- * take its pairs from a queue in decreasing cost.  2D problems run in
- * launches of up to 64 images.  Each problem's inputs are checked on the
+ * take its pairs from a queue in decreasing cost.  2D and 3D problems run
+ * in launches of up to 64 grids.  Each problem's inputs are checked on the
  * device first; a failing problem gets FS1_EINVAL and is not solved.
  * w1_out (count doubles) and infos (count entries) are host arrays and may be
  * NULL.  Returns the worst status over the batch. */

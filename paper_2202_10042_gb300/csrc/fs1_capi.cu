@@ -183,22 +183,26 @@ int kind_of(const fs1_config& c) {
 }
 
 fs1_status check_problem(const fs1_problem& p) {
-  if (p.ndim != 1 && p.ndim != 2) return FS1_EINVAL;
+  if (p.ndim < 1 || p.ndim > 3) return FS1_EINVAL;
   if (p.dtype != FS1_FP64 && p.dtype != FS1_FP32) return FS1_EINVAL;
   if (p.location != FS1_MEM_DEVICE && p.location != FS1_MEM_HOST) return FS1_EINVAL;
-  if (p.n[0] < 1 || (p.ndim == 2 && p.n[1] < 1)) return FS1_EINVAL;
-  if (!(p.h[0] > 0.0) || !std::isfinite(p.h[0])) return FS1_EINVAL;
-  if (p.ndim == 2 && (!(p.h[1] > 0.0) || !std::isfinite(p.h[1]))) return FS1_EINVAL;
+  for (int a = 0; a < p.ndim; ++a) {
+    if (p.n[a] < 1) return FS1_EINVAL;
+    if (!(p.h[a] > 0.0) || !std::isfinite(p.h[a])) return FS1_EINVAL;
+  }
   if (!(p.eps > 0.0) || !std::isfinite(p.eps)) return FS1_EINVAL;
   if (!(p.tol >= 0.0) || std::isnan(p.tol)) return FS1_EINVAL;
   if (p.itr_max < 0) return FS1_EINVAL;
   if (!p.a || !p.b) return FS1_EINVAL;
   if ((p.f_init == nullptr) != (p.g_init == nullptr)) return FS1_EINVAL;
-  if (p.ndim == 2 && (p.n[0] > kMaxLine2D || p.n[1] > kMaxLine2D)) return FS1_EUNSUPPORTED;
+  for (int a = 0; p.ndim >= 2 && a < p.ndim; ++a)
+    if (p.n[a] > kMaxLine2D) return FS1_EUNSUPPORTED;
   return FS1_OK;
 }
 
-int64_t npoints(const fs1_problem& p) { return p.n[0] * (p.ndim == 2 ? p.n[1] : 1); }
+int64_t npoints(const fs1_problem& p) {
+  return p.n[0] * (p.ndim >= 2 ? p.n[1] : 1) * (p.ndim == 3 ? p.n[2] : 1);
+}
 
 // team geometry for a group of problems of one kind
 struct Geometry {
@@ -509,7 +513,7 @@ std::string graph_key(int kind, int mode, int in_f32, int count, int grid, int T
 fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const fs1_problem*>& ps,
                      std::vector<PairResult>& res, Geometry& geo, float* ms, bool validate) {
   const int count = (int)ps.size();
-  const bool two_d = ps[0]->ndim == 2;
+  const bool two_d = ps[0]->ndim >= 2;   // 2D and 3D grids share the grid kernel
   fs1_status st = FS1_OK;
   if (two_d) {
     if (kind != KK_LOG_F32) return FS1_EUNSUPPORTED;   // 2D runs the stabilised FP32 variant
@@ -555,9 +559,11 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
     d.b = p.b;
     d.n = npoints(p);
     d.n_fast = p.n[0];
-    d.n_slow = p.ndim == 2 ? p.n[1] : 1;
+    d.n_mid = p.ndim == 3 ? p.n[1] : 1;
+    d.n_slow = p.ndim == 3 ? p.n[2] : (p.ndim == 2 ? p.n[1] : 1);
     d.h_fast = p.h[0];
-    d.h_slow = p.ndim == 2 ? p.h[1] : 0.0;
+    d.h_mid = p.ndim == 3 ? p.h[1] : 0.0;
+    d.h_slow = p.ndim == 3 ? p.h[2] : (p.ndim == 2 ? p.h[1] : 0.0);
     d.eps = p.eps;
     d.tol = p.tol;
     d.itr_max = p.itr_max;
@@ -902,15 +908,15 @@ fs1_status fs1_solve_batch(fs1_handle* h, const fs1_problem* probs, int64_t coun
       s.location = FS1_MEM_DEVICE;
     }
   }
-  // group by dimension and input dtype (a launch reads one dtype); 2D groups
-  // are cut into launches of at most kMaxImg2D images
+  // group by kernel (1D or grid) and input dtype (a launch reads one dtype);
+  // grid groups are cut into launches of at most kMaxImg2D grids
   std::vector<std::pair<std::vector<const fs1_problem*>, std::vector<int64_t>>> groups;
   for (int nd = 1; nd <= 2; ++nd)
     for (int dt = 0; dt < 2; ++dt) {
       std::vector<const fs1_problem*> grp;
       std::vector<int64_t> idx;
       for (int64_t i = 0; i < count; ++i)
-        if (pst[i] == FS1_OK && staged[i].dtype == dt && staged[i].ndim == nd) {
+        if (pst[i] == FS1_OK && staged[i].dtype == dt && (staged[i].ndim >= 2 ? 2 : 1) == nd) {
           grp.push_back(&staged[i]);
           idx.push_back(i);
           if (nd == 2 && (int)grp.size() == kMaxImg2D) {

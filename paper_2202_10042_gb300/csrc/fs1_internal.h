@@ -10,10 +10,11 @@ namespace fs1 {
 struct PairDesc {
   const void* a;          // histogram a (dtype of the launch), n[0]*n[1] values
   const void* b;          // histogram b
-  int64_t n;              // number of grid points (1D: N; 2D: n_fast*n_slow)
-  int64_t n_fast;         // 2D: fast-axis length; 1D: n
-  int64_t n_slow;         // 2D: slow-axis length; 1D: 1
-  double h_fast, h_slow;  // grid spacings
+  int64_t n;              // number of grid points (1D: N; 2D / 3D: the product of the axes)
+  int64_t n_fast;         // fast-axis (contiguous) length; 1D: n
+  int64_t n_mid;          // middle-axis length (3D); 1 otherwise
+  int64_t n_slow;         // slow-axis length (2D, 3D); 1D: 1
+  double h_fast, h_mid, h_slow;  // grid spacings
   double eps, tol;
   int64_t itr_max;
   double* f_out;          // optional log potentials out (FP64), may be null
@@ -76,9 +77,9 @@ enum KernelKind {
   KK_LOG_F32 = 2,     // stabilised FS-1: FP32 mantissas in extended range
 };
 
-// 2D solver (fs1_solve2d.cu): up to kMaxImg2D images per launch.
+// 2D / 3D solver (fs1_solve2d.cu): up to kMaxImg2D grids per launch.
 constexpr int kMaxImg2D = 64;
-constexpr int kMaxLine2D = 1024;   // longest row or column (staged in shared memory)
+constexpr int kMaxLine2D = 1024;   // longest line along any axis (staged in shared memory)
 size_t solve2d_workspace(const PairDesc* host_descs, int count);
 int launch_solve_2d(const PairDesc* host_descs, int count, int in_f32, PairResult* d_results, void* ws,
                     size_t ws_bytes, long long spin_cap, void* stream);

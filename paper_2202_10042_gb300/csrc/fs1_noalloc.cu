@@ -170,6 +170,7 @@ extern "C" fs1_status fs1_w1_noalloc(const fs1_config* cfg_in, const fs1_problem
   d.b = p.b;
   d.n = n;
   d.n_fast = n;
+  d.n_mid = 1;
   d.n_slow = 1;
   d.h_fast = p.h[0];
   d.h_slow = 0.0;

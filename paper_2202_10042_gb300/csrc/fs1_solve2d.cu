@@ -1,4 +1,5 @@
-// fs1_solve2d.cu -- 2D FS-1 (Algorithm 2) for sm_103a.
+// fs1_solve2d.cu -- 2D FS-1 (Algorithm 2) and its extension to three axes
+// (the closing remark of Section 4) for sm_103a.
 //
 // The 2D kernel K = K_slow (x) K_fast (Section 4, block form of K) is applied
 // as two passes of the 1D recurrences of eq. "recursion": along every row (the
@@ -55,9 +56,9 @@ constexpr int kTab = 38;   // lam^0..lam^32, then lam^{P 2^i}, i < 5
 struct Img2D {
   const void* a;
   const void* b;
-  int nf, ns;          // fast (contiguous) and slow lengths
-  double cf, cs;       // h / eps per axis
-  double hf, hs;
+  int nf, nm, ns;      // fast (contiguous), middle (1 in 2D) and slow lengths
+  double cf, cm, cs;   // h / eps per axis
+  double hf, hm, hs;
   double tol;
   int64_t itr_max;
   XF* U;               // u
@@ -68,9 +69,9 @@ struct Img2D {
   const double* g_init;
   double* f_out;          // optional potentials out
   double* g_out;
-  float* errp;         // [2 ceil(nf / 8)] error partials of the column tiles
-                       // (compensated pairs)
-  double* wp;          // [nf] column cost partials
+  float* errp;         // [2 ceil(nf nm / 8)] error partials of the slow-pass
+                       // tiles (compensated pairs)
+  double* wp;          // [nf nm] cost partials of the slow lines
   int* stop;           // 0 while active; 1 + k once stopped with the final v in V[k]
 };
 
@@ -79,13 +80,17 @@ struct Launch2D {
   PairResult* results;
   int nimg;
   int in_f32;
-  const int* row_off;  // [nimg + 1] prefix sums of ns
-  const int* col_off;  // [nimg + 1] prefix sums of nf
-  const int* tile_off; // [nimg + 1] prefix sums of ceil(nf / 8)
+  const int* row_off;  // [nimg + 1] prefix sums of nm ns (rows)
+  const int* col_off;  // [nimg + 1] prefix sums of nf nm (slow lines)
+  const int* tile_off; // [nimg + 1] prefix sums of ceil(nf nm / 8) (slow-pass tiles)
+  const int* mid_off;  // [nimg + 1] prefix sums of ns ceil(nf / 8) (middle-pass tiles; 0 in 2D)
+  const int* midl_off; // [nimg + 1] prefix sums of nf ns (middle lines; 0 in 2D)
+  int any3d;           // some image has a middle axis
   int line_stride;     // per-warp shared-memory region (XF): a staged line, its
                        // backward partials, + 2 (== 2 mod 16)
   int line_ch;         // XF of the longest staged line (32 P' of the longest line)
-  XF* tab;             // [nimg][2][kTab] decay tables, written by CTA 0 at start
+  XF* tab;             // [nimg][3][kTab] decay tables (axis 0 fast, 1 slow, 2 middle),
+                       // written by CTA 0 at start
   unsigned long long* bar;   // zeroed per launch
   int* abort_flag;
   long long spin_cap;
@@ -392,10 +397,10 @@ __device__ void cta_sum_df(float& h, float& l, float* red) {
 __global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
   extern __shared__ XF sline[];   // kWarps2 regions of L.line_stride XF
   __shared__ float sred[2 * kWarps2];
-  __shared__ int stile[kMaxImg2D + 1];
-  __shared__ int srow[kMaxImg2D + 1], scol[kMaxImg2D + 1];
+  __shared__ int srow[kMaxImg2D + 1], scol[kMaxImg2D + 1], stile[kMaxImg2D + 1];
+  __shared__ int smid[kMaxImg2D + 1], smidl[kMaxImg2D + 1];
   __shared__ signed char sstate[kMaxImg2D];  // 0 active, 1 stops this iteration, 2 stopped earlier
-  __shared__ bool sframe[kMaxImg2D][2];      // the axis takes the FP32-frame line scan (c P <= 40)
+  __shared__ bool sframe[kMaxImg2D][3];      // the axis takes the FP32-frame line scan (c P <= 40)
   __shared__ int sok;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gw = blockIdx.x * kWarps2 + warp;
@@ -407,30 +412,34 @@ __global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
     srow[i] = L.row_off[i];
     scol[i] = L.col_off[i];
     stile[i] = L.tile_off[i];
+    smid[i] = L.mid_off[i];
+    smidl[i] = L.midl_off[i];
   }
   XF* const s_own = sline + warp * L.line_stride;            // this warp's region
   XF* const t_own = s_own + L.line_ch;
-  for (int t = threadIdx.x; t < nimg * 2; t += blockDim.x) {
-    const Img2D& I = L.imgs[t >> 1];
-    const int len = (t & 1) ? I.ns : I.nf;
-    sframe[t >> 1][t & 1] = ((t & 1) ? I.cs : I.cf) * (double)((len + 31) >> 5) <= 40.0;
+  for (int t = threadIdx.x; t < nimg * 3; t += blockDim.x) {
+    const Img2D& I = L.imgs[t / 3];
+    const int ax = t % 3;
+    const int len = ax == 0 ? I.nf : (ax == 1 ? I.ns : I.nm);
+    const double c = ax == 0 ? I.cf : (ax == 1 ? I.cs : I.cm);
+    sframe[t / 3][ax] = c * (double)((len + 31) >> 5) <= 40.0;
   }
-  // decay tables [image][axis: 0 fast, 1 slow][j] in global memory (CTA 0;
-  // the grid barrier below publishes them)
-  for (int t = threadIdx.x; blockIdx.x == 0 && t < nimg * 2 * kTab; t += blockDim.x) {
-    const int i = t / (2 * kTab), ax = (t / kTab) & 1, j = t % kTab;
+  // decay tables [image][axis][j] in global memory (CTA 0; the grid barrier
+  // below publishes them)
+  for (int t = threadIdx.x; blockIdx.x == 0 && t < nimg * 3 * kTab; t += blockDim.x) {
+    const int i = t / (3 * kTab), ax = (t / kTab) % 3, j = t % kTab;
     const Img2D& I = L.imgs[i];
-    const double c = ax == 0 ? I.cf : I.cs;
-    const int len = ax == 0 ? I.nf : I.ns;
+    const double c = ax == 0 ? I.cf : (ax == 1 ? I.cs : I.cm);
+    const int len = ax == 0 ? I.nf : (ax == 1 ? I.ns : I.nm);
     const int P = (len + 31) >> 5;
     const double k = j <= 32 ? (double)j : (double)P * (double)(1 << (j - 33));
     L.tab[t] = c_decay(k, c, XF{});
   }
-  auto tab = [&](int i, int ax) -> const XF* { return L.tab + (i * 2 + ax) * kTab; };
-  // u = v = 1 / (n_fast n_slow)  (Algorithm 2, line 1), or a warm start
+  auto tab = [&](int i, int ax) -> const XF* { return L.tab + (i * 3 + ax) * kTab; };
+  // u = v = 1 / N  (Algorithm 2, line 1), or a warm start
   for (int i = 0; i < nimg; ++i) {
     const Img2D& I = L.imgs[i];
-    const int64_t N = (int64_t)I.nf * I.ns;
+    const int64_t N = (int64_t)I.nf * I.nm * I.ns;
     const XF init = xf_norm((float)(1.0 / (double)N), 0);
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
       I.U[p] = I.f_init ? xf_from_log(I.f_init[p]) : init;
@@ -439,7 +448,31 @@ __global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
   }
   if (!grid_barrier(L, gen, &sok)) return;
 
-  const int rows = srow[nimg], cols = scol[nimg], tiles = stile[nimg];
+  const int rows = srow[nimg], tiles = stile[nimg], mids = smid[nimg];
+  // middle pass of a half-step (3D images): Z = (I (x) K_m (x) I) Y, one CTA
+  // per tile of 8 columns of one slab; Z is the image's R buffer
+  auto mid_pass = [&]() -> bool {
+    for (int t = blockIdx.x; t < mids; t += gridDim.x) {
+      const int i = owner(smid, nimg, t);
+      if (sstate[i]) continue;   // CTA-uniform
+      const Img2D& I = L.imgs[i];
+      const int ntf = (I.nf + kTileCols - 1) / kTileCols;
+      const int tt = t - smid[i];
+      const int64_t base = (int64_t)(tt / ntf) * I.nf * I.nm;   // the slab
+      const int col0 = (tt % ntf) * kTileCols;
+      col_tile_scan(I.Y + base, I.nf, I.nm, col0, tab(i, 2), sframe[i][2], sline, L.line_stride);
+      const int c = threadIdx.x & (kTileCols - 1);
+      if (col0 + c < I.nf) {
+        const XF* sc = sline + c * L.line_stride;
+        ChunkPos q(threadIdx.x / kTileCols, (I.nm + 31) >> 5);
+        for (int r = threadIdx.x / kTileCols; r < I.nm; r += kThreads2 / kTileCols, q.next())
+          I.R[base + (int64_t)r * I.nf + col0 + c] = sc[q.pos()];
+      }
+      __syncthreads();   // the tile's shared memory is reused by the next tile
+    }
+    return grid_barrier(L, gen, &sok);
+  };
+
   for (int64_t ell = 0;; ++ell) {
     const int par = (int)(ell & 1);
     __syncthreads();
@@ -457,19 +490,21 @@ __global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
       row_pass(I.U + o, I.Y + o, I.nf, tab(i, 0), sframe[i][0], s_own, t_own);
     }
     if (!grid_barrier(L, gen, &sok)) return;
-    // ---- v-half, slow pass: y = (K_s (x) I) Y, v_new = b / y, error partials
+    if (L.any3d && !mid_pass()) return;
+    // ---- v-half, slow pass: y = (K_s (x) I) Z, v_new = b / y, error partials
     for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
       const int i = owner(stile, nimg, t);
       if (sstate[i]) continue;   // CTA-uniform
       const Img2D& I = L.imgs[i];
+      const int W = I.nf * I.nm;   // points of a slab: the slow lines' stride
       const int tile = t - stile[i];
       const int col0 = tile * kTileCols;
-      col_tile_scan(I.Y, I.nf, I.ns, col0, tab(i, 1), sframe[i][1], sline, L.line_stride);
+      col_tile_scan(I.nm > 1 ? I.R : I.Y, W, I.ns, col0, tab(i, 1), sframe[i][1], sline, L.line_stride);
       XF* Vn = I.V[par ^ 1];
       float eh = 0.f, el = 0.f;
       const int c = threadIdx.x & (kTileCols - 1);
-      if (col0 + c < I.nf) {
-        const XF* s = sline + c * L.line_stride;
+      if (col0 + c < W) {
+        const XF* sc = sline + c * L.line_stride;
         const int r0 = threadIdx.x / kTileCols;
         constexpr int dr = kThreads2 / kTileCols;
         ChunkPos q(r0, (I.ns + 31) >> 5);
@@ -479,15 +514,15 @@ __global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
 #pragma unroll
           for (int b = 0; b < kBatch; ++b)
             if (rb + dr * b < I.ns) {
-              const int64_t p = (int64_t)(rb + dr * b) * I.nf + col0 + c;
+              const int64_t p = (int64_t)(rb + dr * b) * W + col0 + c;
               mb[b] = load_m(I.b, p, L.in_f32);
               vb[b] = I.V[par][p];
             }
 #pragma unroll
           for (int b = 0; b < kBatch; ++b, q.next())
             if (rb + dr * b < I.ns) {
-              const int64_t p = (int64_t)(rb + dr * b) * I.nf + col0 + c;
-              const XF y = s[q.pos()];
+              const int64_t p = (int64_t)(rb + dr * b) * W + col0 + c;
+              const XF y = sc[q.pos()];
               const float m = mb[b];
               Vn[p] = m > 0.f ? xf_norm(__fdividef(m, y.m), -y.e) : XF{0.f, kZeroExp};
               const float pv = c_to(c_mul(vb[b], y), 0);   // v_old (K^T u) at p
@@ -507,7 +542,7 @@ __global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
       if (sstate[i]) continue;
       const Img2D& I = L.imgs[i];
       float h = 0.f, l = 0.f;
-      const int nt = (I.nf + kTileCols - 1) / kTileCols;
+      const int nt = (I.nf * I.nm + kTileCols - 1) / kTileCols;
       for (int c = lane; c < nt; c += 32) df_add(h, l, __ldcg(I.errp + 2 * c), __ldcg(I.errp + 2 * c + 1));
       warp_sum_df(h, l);
       if (lane == 0) {
@@ -534,16 +569,18 @@ __global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
       row_pass(I.V[par ^ 1] + o, I.Y + o, I.nf, tab(i, 0), sframe[i][0], s_own, t_own);
     }
     if (!grid_barrier(L, gen, &sok)) return;
-    // ---- u-half, slow pass: u = a / ((K_s (x) I) Y)
+    if (L.any3d && !mid_pass()) return;
+    // ---- u-half, slow pass: u = a / ((K_s (x) I) Z)
     for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
       const int i = owner(stile, nimg, t);
       if (sstate[i]) continue;   // CTA-uniform
       const Img2D& I = L.imgs[i];
+      const int W = I.nf * I.nm;
       const int col0 = (t - stile[i]) * kTileCols;
-      col_tile_scan(I.Y, I.nf, I.ns, col0, tab(i, 1), sframe[i][1], sline, L.line_stride);
+      col_tile_scan(I.nm > 1 ? I.R : I.Y, W, I.ns, col0, tab(i, 1), sframe[i][1], sline, L.line_stride);
       const int c = threadIdx.x & (kTileCols - 1);
-      if (col0 + c < I.nf) {
-        const XF* s = sline + c * L.line_stride;
+      if (col0 + c < W) {
+        const XF* sc = sline + c * L.line_stride;
         const int r0 = threadIdx.x / kTileCols;
         constexpr int dr = kThreads2 / kTileCols;
         ChunkPos q(r0, (I.ns + 31) >> 5);
@@ -551,12 +588,12 @@ __global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
           float mb[kBatch];
 #pragma unroll
           for (int b = 0; b < kBatch; ++b)
-            if (rb + dr * b < I.ns) mb[b] = load_m(I.a, (int64_t)(rb + dr * b) * I.nf + col0 + c, L.in_f32);
+            if (rb + dr * b < I.ns) mb[b] = load_m(I.a, (int64_t)(rb + dr * b) * W + col0 + c, L.in_f32);
 #pragma unroll
           for (int b = 0; b < kBatch; ++b, q.next())
             if (rb + dr * b < I.ns) {
-              const int64_t p = (int64_t)(rb + dr * b) * I.nf + col0 + c;
-              const XF y = s[q.pos()];
+              const int64_t p = (int64_t)(rb + dr * b) * W + col0 + c;
+              const XF y = sc[q.pos()];
               I.U[p] = mb[b] > 0.f ? xf_norm(__fdividef(mb[b], y.m), -y.e) : XF{0.f, kZeroExp};
             }
         }
@@ -570,9 +607,22 @@ __global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
     if (!grid_barrier(L, gen, &sok)) return;
   }
 
-  // ---- transport cost
-  // rows: Y = (I (x) K_f^(c)) v (weighted); then the plain (I (x) K_f) v into
-  // the free v buffer
+  // optional potentials out: log u and log v of the returned iterate (before
+  // the cost passes, which reuse the v buffer in 3D)
+  for (int i = 0; i < nimg; ++i) {
+    const Img2D& I = L.imgs[i];
+    if (!I.f_out && !I.g_out) continue;
+    const int k = (ld_relaxed(I.stop) - 1) & 1;
+    const int64_t N = (int64_t)I.nf * I.nm * I.ns;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+      if (I.f_out) I.f_out[p] = xf_log(I.U[p]);
+      if (I.g_out) I.g_out[p] = xf_log(I.V[k][p]);
+    }
+  }
+
+  // ---- transport cost: sum over axes a of h_a u . (K with the distance-
+  // weighted K_a^(c) on axis a) v
+  // rows: Y = (I (x) K_f^(c)) v (weighted); V1 = (I (x) K_f) v in the free v buffer
   for (int t = gw; t < rows; t += nw) {
     const int i = owner(srow, nimg, t);
     const Img2D& I = L.imgs[i];
@@ -583,49 +633,66 @@ __global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
     line_scan_global<false>(I.V[k] + o, I.V[k ^ 1] + o, I.R + o, 1, I.nf, tab(i, 0));
   }
   if (!grid_barrier(L, gen, &sok)) return;
-  // columns: h_fast u.(K_s (x) I) Y + h_slow u.(K_s^(c) (x) I) V[k^1]
-  for (int t = gw; t < cols; t += nw) {
+  // middle lines (3D): R = K_m Y, V[k] = K_m^(c) V1, Y = K_m V1
+  if (L.any3d) {
+    const int mlines = smidl[nimg];
+    for (int t = gw; t < mlines; t += nw) {
+      const int i = owner(smidl, nimg, t);
+      const Img2D& I = L.imgs[i];
+      const int k = (ld_relaxed(I.stop) - 1) & 1;
+      const int tl = t - smidl[i];
+      const int64_t o = (int64_t)(tl / I.nf) * I.nf * I.nm + tl % I.nf;
+      line_scan_global<false>(I.Y + o, I.R + o, I.R + o, I.nf, I.nm, tab(i, 2));
+      __syncwarp();
+      line_scan_global<true>(I.V[k ^ 1] + o, I.V[k] + o, I.V[k] + o, I.nf, I.nm, tab(i, 2));
+      __syncwarp();
+      line_scan_global<false>(I.V[k ^ 1] + o, I.Y + o, I.Y + o, I.nf, I.nm, tab(i, 2));
+    }
+    if (!grid_barrier(L, gen, &sok)) return;
+  }
+  // slow lines: 2D:  h_f u.(K_s Y) + h_s u.(K_s^(c) V1)
+  //             3D:  h_f u.(K_s R) + h_m u.(K_s V[k]) + h_s u.(K_s^(c) Y)
+  const int slines = scol[nimg];
+  for (int t = gw; t < slines; t += nw) {
     const int i = owner(scol, nimg, t);
     const Img2D& I = L.imgs[i];
     const int k = (ld_relaxed(I.stop) - 1) & 1;
+    const int W = I.nf * I.nm;
     const int col = t - scol[i];
+    XF* const out = I.nm > 1 ? I.V[k ^ 1] : I.R;
     double acc = 0.0;
-    line_scan_global<false>(I.Y + col, I.R + col, I.R + col, I.nf, I.ns, tab(i, 1));
-    __syncwarp();
-    for (int r = lane; r < I.ns; r += 32) {
-      const int64_t p = (int64_t)r * I.nf + col;
-      const XF w = I.R[p], u = I.U[p];
-      acc += I.hf * ldexp((double)u.m * (double)w.m, u.e + w.e);
-    }
-    __syncwarp();
-    line_scan_global<true>(I.V[k ^ 1] + col, I.R + col, I.R + col, I.nf, I.ns, tab(i, 1));
-    __syncwarp();
-    for (int r = lane; r < I.ns; r += 32) {
-      const int64_t p = (int64_t)r * I.nf + col;
-      const XF w = I.R[p], u = I.U[p];
-      acc += I.hs * ldexp((double)u.m * (double)w.m, u.e + w.e);
+    auto accumulate = [&](double hax) {
+      __syncwarp();
+      for (int r = lane; r < I.ns; r += 32) {
+        const int64_t p = (int64_t)r * W + col;
+        const XF w = out[p], u = I.U[p];
+        acc += hax * ldexp((double)u.m * (double)w.m, u.e + w.e);
+      }
+      __syncwarp();
+    };
+    if (I.nm > 1) {
+      line_scan_global<false>(I.R + col, out + col, out + col, W, I.ns, tab(i, 1));
+      accumulate(I.hf);
+      line_scan_global<false>(I.V[k] + col, out + col, out + col, W, I.ns, tab(i, 1));
+      accumulate(I.hm);
+      line_scan_global<true>(I.Y + col, out + col, out + col, W, I.ns, tab(i, 1));
+      accumulate(I.hs);
+    } else {
+      line_scan_global<false>(I.Y + col, out + col, out + col, W, I.ns, tab(i, 1));
+      accumulate(I.hf);
+      line_scan_global<true>(I.V[k ^ 1] + col, out + col, out + col, W, I.ns, tab(i, 1));
+      accumulate(I.hs);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) I.wp[col] = acc;
   }
   if (!grid_barrier(L, gen, &sok)) return;
-  // optional potentials out: log u and log v of the returned iterate
-  for (int i = 0; i < nimg; ++i) {
-    const Img2D& I = L.imgs[i];
-    if (!I.f_out && !I.g_out) continue;
-    const int k = (ld_relaxed(I.stop) - 1) & 1;
-    const int64_t N = (int64_t)I.nf * I.ns;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
-      if (I.f_out) I.f_out[p] = xf_log(I.U[p]);
-      if (I.g_out) I.g_out[p] = xf_log(I.V[k][p]);
-    }
-  }
   if (blockIdx.x == 0) {
     for (int i = warp; i < nimg; i += kWarps2) {
       const Img2D& I = L.imgs[i];
       double s = 0.0;
-      for (int c = lane; c < I.nf; c += 32) s += __ldcg(I.wp + c);
+      for (int c = lane; c < I.nf * I.nm; c += 32) s += __ldcg(I.wp + c);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (lane == 0) L.results[i].w = L.results[i].status == FS1_ENUMERIC ? NAN : s;
@@ -638,12 +705,12 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 }  // namespace
 
 size_t solve2d_workspace(const PairDesc* d, int count) {
-  size_t b = align256(sizeof(Img2D) * count) + 3 * align256(sizeof(int) * (count + 1)) + 256 + 256 +
-             align256(sizeof(XF) * 2 * kTab * count);
+  size_t b = align256(sizeof(Img2D) * count) + 5 * align256(sizeof(int) * (count + 1)) + 256 + 256 +
+             align256(sizeof(XF) * 3 * kTab * count);
   for (int i = 0; i < count; ++i) {
-    const size_t n = (size_t)d[i].n_fast * d[i].n_slow;
-    b += 5 * align256(sizeof(XF) * n) + align256(sizeof(float) * 2 * d[i].n_fast) +
-         align256(sizeof(double) * d[i].n_fast) + 256;
+    const size_t W = (size_t)d[i].n_fast * d[i].n_mid;
+    const size_t n = W * d[i].n_slow;
+    b += 5 * align256(sizeof(XF) * n) + align256(sizeof(float) * 2 * W) + align256(sizeof(double) * W) + 256;
   }
   return b;
 }
@@ -653,7 +720,7 @@ int launch_solve_2d(const PairDesc* d, int count, int in_f32, PairResult* result
   cudaStream_t st = (cudaStream_t)stream;
   if (count < 1 || count > kMaxImg2D) return FS1_EINVAL;
   for (int i = 0; i < count; ++i)
-    if (d[i].n_fast > kMaxLine2D || d[i].n_slow > kMaxLine2D) return FS1_EUNSUPPORTED;
+    if (d[i].n_fast > kMaxLine2D || d[i].n_mid > kMaxLine2D || d[i].n_slow > kMaxLine2D) return FS1_EUNSUPPORTED;
   if (solve2d_workspace(d, count) > ws_bytes) return FS1_ENOMEM;
   char* p = (char*)ws;
   Img2D* d_imgs = (Img2D*)p;
@@ -664,14 +731,19 @@ int launch_solve_2d(const PairDesc* d, int count, int in_f32, PairResult* result
   p += align256(sizeof(int) * (count + 1));
   int* d_tile = (int*)p;
   p += align256(sizeof(int) * (count + 1));
+  int* d_mid = (int*)p;
+  p += align256(sizeof(int) * (count + 1));
+  int* d_midl = (int*)p;
+  p += align256(sizeof(int) * (count + 1));
   unsigned long long* d_bar = (unsigned long long*)p;
   p += 256;
   int* d_abort = (int*)p;
   p += 256;
   XF* d_tab = (XF*)p;
-  p += align256(sizeof(XF) * 2 * kTab * count);
+  p += align256(sizeof(XF) * 3 * kTab * count);
   std::vector<Img2D> imgs(count);
-  std::vector<int> row(count + 1, 0), col(count + 1, 0), tile(count + 1, 0);
+  std::vector<int> row(count + 1, 0), col(count + 1, 0), tile(count + 1, 0), mid(count + 1, 0), midl(count + 1, 0);
+  int any3d = 0;
   int pp_max = 1;
   bool any_ext = false;   // some axis takes the per-point extended-range scan (XF partials)
   char* stops = nullptr;
@@ -681,10 +753,13 @@ int launch_solve_2d(const PairDesc* d, int count, int in_f32, PairResult* result
     I.a = D.a;
     I.b = D.b;
     I.nf = (int)D.n_fast;
+    I.nm = (int)D.n_mid;
     I.ns = (int)D.n_slow;
     I.cf = D.h_fast / D.eps;
+    I.cm = D.n_mid > 1 ? D.h_mid / D.eps : 0.0;
     I.cs = D.h_slow / D.eps;
     I.hf = D.h_fast;
+    I.hm = D.h_mid;
     I.hs = D.h_slow;
     I.tol = D.tol;
     I.itr_max = D.itr_max;
@@ -692,23 +767,28 @@ int launch_solve_2d(const PairDesc* d, int count, int in_f32, PairResult* result
     I.g_init = D.g_init;
     I.f_out = D.f_out;
     I.g_out = D.g_out;
-    const size_t n = (size_t)I.nf * I.ns;
+    const size_t W = (size_t)I.nf * I.nm;
+    const size_t n = W * I.ns;
     I.U = (XF*)p; p += align256(sizeof(XF) * n);
     I.V[0] = (XF*)p; p += align256(sizeof(XF) * n);
     I.V[1] = (XF*)p; p += align256(sizeof(XF) * n);
     I.Y = (XF*)p; p += align256(sizeof(XF) * n);
     I.R = (XF*)p; p += align256(sizeof(XF) * n);
-    I.errp = (float*)p; p += align256(sizeof(float) * 2 * I.nf);
-    I.wp = (double*)p; p += align256(sizeof(double) * I.nf);
+    I.errp = (float*)p; p += align256(sizeof(float) * 2 * W);
+    I.wp = (double*)p; p += align256(sizeof(double) * W);
     I.stop = (int*)p;
     if (!stops) stops = p;
     p += 256;
     imgs[i] = I;
-    row[i + 1] = row[i] + I.ns;
-    col[i + 1] = col[i] + I.nf;
-    tile[i + 1] = tile[i] + (I.nf + kTileCols - 1) / kTileCols;
-    pp_max = std::max(pp_max, std::max((I.nf + 31) / 32, (I.ns + 31) / 32) | 1);
-    any_ext = any_ext || I.cf * ((I.nf + 31) / 32) > 40.0 || I.cs * ((I.ns + 31) / 32) > 40.0;
+    row[i + 1] = row[i] + I.nm * I.ns;
+    col[i + 1] = col[i] + (int)W;
+    tile[i + 1] = tile[i] + ((int)W + kTileCols - 1) / kTileCols;
+    mid[i + 1] = mid[i] + (I.nm > 1 ? I.ns * ((I.nf + kTileCols - 1) / kTileCols) : 0);
+    midl[i + 1] = midl[i] + (I.nm > 1 ? I.nf * I.ns : 0);
+    any3d |= I.nm > 1;
+    pp_max = std::max(pp_max, std::max((I.nf + 31) / 32, std::max((I.nm + 31) / 32, (I.ns + 31) / 32)) | 1);
+    any_ext = any_ext || I.cf * ((I.nf + 31) / 32) > 40.0 || I.cs * ((I.ns + 31) / 32) > 40.0 ||
+              I.cm * ((I.nm + 31) / 32) > 40.0;
   }
   cudaError_t e = cudaSuccess;
   for (int i = 0; i < count && e == cudaSuccess; ++i) e = cudaMemsetAsync(imgs[i].stop, 0, sizeof(int), st);
@@ -717,6 +797,9 @@ int launch_solve_2d(const PairDesc* d, int count, int in_f32, PairResult* result
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_col, col.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_tile, tile.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_mid, mid.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_midl, midl.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(d_bar, 0, 512, st);
   if (e != cudaSuccess) {
     fprintf(stderr, "fs1: 2D setup failed: %s\n", cudaGetErrorString(e));
@@ -728,8 +811,8 @@ int launch_solve_2d(const PairDesc* d, int count, int in_f32, PairResult* result
   const int line_ch = 32 * pp_max;
   const int line_stride = line_ch + (any_ext ? line_ch : line_ch / 2) + 2;
   const size_t smem = sizeof(XF) * (size_t)kWarps2 * line_stride;
-  Launch2D L{d_imgs, results, count, in_f32, d_row, d_col, d_tile, line_stride, line_ch, d_tab, d_bar, d_abort,
-             spin_cap};
+  Launch2D L{d_imgs, results, count, in_f32, d_row, d_col, d_tile, d_mid, d_midl, any3d, line_stride, line_ch,
+             d_tab, d_bar, d_abort, spin_cap};
   e = cudaFuncSetAttribute(fs1_solve2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0, dev = 0, sms = 0;
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fs1_solve2d_kernel, kThreads2, smem);

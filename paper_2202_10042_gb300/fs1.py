@@ -37,7 +37,7 @@ class fs1_config(Structure):
 
 class fs1_problem(Structure):
     _fields_ = [("ndim", c_int), ("dtype", c_int), ("location", c_int), ("reserved", c_int),
-                ("n", c_int64 * 2), ("h", c_double * 2), ("eps", c_double), ("tol", c_double),
+                ("n", c_int64 * 3), ("h", c_double * 3), ("eps", c_double), ("tol", c_double),
                 ("itr_max", c_int64), ("a", c_void_p), ("b", c_void_p), ("f_out", c_void_p),
                 ("g_out", c_void_p), ("f_init", c_void_p), ("g_init", c_void_p)]
 
@@ -206,21 +206,16 @@ class Solver:
                 f_init=None, g_init=None, shape=None) -> fs1_problem:
         """Build an fs1_problem from torch tensors (CUDA: device location; CPU:
         host location).  1D: a, b of shape (n,), h a float.  2D: a, b of shape
-        (n_slow, n_fast), h = (h_fast, h_slow)."""
+        (n_slow, n_fast), h = (h_fast, h_slow).  3D: shape (n_slow, n_mid,
+        n_fast), h = (h_fast, h_mid, h_slow)."""
         import torch
         p = fs1_problem()
-        if a.dim() == 1:
-            p.ndim = 1
-            p.n[0] = a.numel()
-            p.n[1] = 1
-            p.h[0] = float(h[0] if isinstance(h, (tuple, list)) else h)
-            p.h[1] = 0.0
-        else:
-            p.ndim = 2
-            p.n[0] = a.shape[1]
-            p.n[1] = a.shape[0]
-            p.h[0] = float(h[0])
-            p.h[1] = float(h[1])
+        p.ndim = a.dim()
+        assert 1 <= p.ndim <= 3
+        hs = tuple(h) if isinstance(h, (tuple, list)) else (h,)
+        for ax in range(3):
+            p.n[ax] = a.shape[p.ndim - 1 - ax] if ax < p.ndim else 1
+            p.h[ax] = float(hs[ax]) if ax < p.ndim else 0.0
         assert a.dtype == b.dtype and a.is_contiguous() and b.is_contiguous()
         p.dtype = FS1_FP32 if a.dtype == torch.float32 else FS1_FP64
         p.location = FS1_MEM_DEVICE if a.is_cuda else FS1_MEM_HOST

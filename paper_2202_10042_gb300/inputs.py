@@ -41,6 +41,10 @@ the node grid x_i = (i - 1) dx - 3, dx = 6 / (N - 1) on [-3, 3] of Section 5.1):
      is used.
   8  2D random distributions (Section 5.3, Table 3): N x N U[0, 1] values
      normalised to mass 1, h_1 = h_2 = 1, eps = 1e-2; 1000 iterations.
+
+Three axes (the extension stated by the closing remark of Section 4):
+  9  3D, 64^3 cells on [0, 1]^3, eps = 2e-3: 1-3 Gaussian blobs + 1e-7;
+     tol 1e-6, cap 2000; 32 pairs.
 """
 from __future__ import annotations
 
@@ -177,6 +181,34 @@ def workload4(index: int = 0, side: int = 512, eps: float = 1e-3, tol: float = 1
     return Problem(a, b, (h, h), eps, tol, itr_max, 2, (side, side), 4, index)
 
 
+def blobs_3d(rng, side: int, floor: float, max_blobs: int = 3,
+             sigma_range=(0.05, 0.15)) -> np.ndarray:
+    """(side, side, side) grid, fast axis last: 1-max_blobs axis-aligned
+    Gaussian blobs with centres in U[0.2, 0.8]^3, per-axis sigma in
+    sigma_range, amplitudes U[0.5, 1], plus a floor, normalised."""
+    x = cell_centres(side)
+    Z, Y, X = x[:, None, None], x[None, :, None], x[None, None, :]
+    nb = int(rng.integers(1, max_blobs + 1))
+    rho = np.zeros((side, side, side), dtype=np.float64)
+    for _ in range(nb):
+        cx, cy, cz = rng.uniform(0.2, 0.8, size=3)
+        sx, sy, sz = rng.uniform(*sigma_range, size=3)
+        amp = rng.uniform(0.5, 1.0)
+        rho += amp * np.exp(-0.5 * (((X - cx) / sx) ** 2 + ((Y - cy) / sy) ** 2 + ((Z - cz) / sz) ** 2))
+    return _normalise(rho + floor)
+
+
+def workload9(index: int = 0, side: int = 64, eps: float = 2e-3, tol: float = 1e-6,
+              itr_max: int = 2000) -> Problem:
+    """3D grids (the third axis of Section 4's closing remark): side^3 cells on
+    [0, 1]^3, 1-3 Gaussian blobs + 1e-7, h = 1/side on every axis."""
+    ra, rb, _ = _rng_pair(9, index)
+    a = blobs_3d(ra, side, 1e-7)
+    b = blobs_3d(rb, side, 1e-7)
+    h = 1.0 / side
+    return Problem(a, b, (h, h, h), eps, tol, itr_max, 3, (side, side, side), 9, index)
+
+
 def workload5_arrivals(rate: float = 2000.0, duration: float = 60.0) -> np.ndarray:
     """Poisson arrival times (seconds) of the serving workload."""
     r = np.random.default_rng(np.random.SeedSequence([ROOT_SEED, 5, 0x5E7]))
@@ -296,5 +328,5 @@ def random_pair_1d(index: int, n: int, floor: float = 0.0, zeros: int = 0):
 
 def batch(workload: int, indices, **kw) -> List[Problem]:
     fn = {1: workload1, 2: workload2, 3: workload3, 4: workload4, 6: paper_e1, 7: paper_e2,
-          8: paper_e3}[workload]
+          8: paper_e3, 9: workload9}[workload]
     return [fn(i, **kw) for i in indices]

@@ -63,9 +63,9 @@ class Request:
 
 def device_bytes(req: Request) -> int:
     """Device memory a request holds while admitted: a, b (FP32), f, g (FP64)
-    and the solver workspace of its launch (2D keeps 40 B per point)."""
+    and the solver workspace of its launch (2D and 3D keep 40 B per point)."""
     n = req.npoints
-    return n * (4 + 4 + 8 + 8) + (40 * n if req.a.ndim == 2 else 0) + 4096
+    return n * (4 + 4 + 8 + 8) + (40 * n if req.a.ndim >= 2 else 0) + 4096
 
 
 class _Slot:
@@ -89,7 +89,7 @@ def library_solver(solver):
         probs = []
         for s, it in zip(slots, iters):
             warm = s.done_iters > 0
-            probs.append(fs1.Solver.problem(s.a, s.b, s.req.h if s.req.a.ndim == 2 else s.req.h[0],
+            probs.append(fs1.Solver.problem(s.a, s.b, s.req.h if s.req.a.ndim >= 2 else s.req.h[0],
                                             s.req.eps, s.req.tol, it,
                                             f_out=s.f, g_out=s.g,
                                             f_init=s.f if warm else None,
@@ -240,7 +240,7 @@ def serve_one_at_a_time(requests: Sequence[Request], solver=None, clock=time.per
             time.sleep(r.arrival - now)
         a = torch.as_tensor(np.ascontiguousarray(r.a, dtype=np.float32), device="cuda")
         b = torch.as_tensor(np.ascontiguousarray(r.b, dtype=np.float32), device="cuda")
-        st, w, info = fs1.fs1_w1(solver.h, fs1.Solver.problem(a, b, r.h if r.a.ndim == 2 else r.h[0], r.eps,
+        st, w, info = fs1.fs1_w1(solver.h, fs1.Solver.problem(a, b, r.h if r.a.ndim >= 2 else r.h[0], r.eps,
                                                               r.tol, r.itr_max))
         r.admit = r.arrival
         r.finish = clock() - t0
