@@ -49,14 +49,22 @@ namespace {
 
 constexpr int kThreads2 = 256;
 constexpr int kWarps2 = kThreads2 / 32;
-constexpr int kTileCols = kWarps2;   // columns of a slow-pass tile (one warp each)
+constexpr int kTileCols = kWarps2;   // columns of a tile per 32 lanes a line takes
 constexpr int kBatch = 4;            // epilogue loads a thread keeps in flight
-constexpr int kTab = 38;   // lam^0..lam^32, then lam^{P 2^i}, i < 5
+// decay table of an axis: lam^j for j <= 32, then lam^{P 2^i} (i < 5) for the
+// segment scans (P = ceil(L / G) points per lane of a G-lane segment), then
+// lam^{P32 2^i} for the whole-warp scans of the cost phase (P32 = ceil(L / 32))
+constexpr int kTab = 43;
+constexpr int kTabSeg = 33;
+constexpr int kTabWarp = 38;
 
 struct Img2D {
   const void* a;
   const void* b;
   int nf, nm, ns;      // fast (contiguous), middle (1 in 2D) and slow lengths
+  int g[3];            // lanes that share one line, per axis (0 fast, 1 slow, 2 middle)
+  int frame[3];        // 1: the axis takes the FP32-frame line scan
+  int tw_s, tw_m;      // columns of a slow / middle tile (8 x 32 / g)
   double cf, cm, cs;   // h / eps per axis
   double hf, hm, hs;
   double tol;
@@ -80,10 +88,10 @@ struct Launch2D {
   PairResult* results;
   int nimg;
   int in_f32;
-  const int* row_off;  // [nimg + 1] prefix sums of nm ns (rows)
+  const int* row_off;  // [nimg + 1] prefix sums of the row groups (32 / g_fast rows each)
   const int* col_off;  // [nimg + 1] prefix sums of nf nm (slow lines)
-  const int* tile_off; // [nimg + 1] prefix sums of ceil(nf nm / 8) (slow-pass tiles)
-  const int* mid_off;  // [nimg + 1] prefix sums of ns ceil(nf / 8) (middle-pass tiles; 0 in 2D)
+  const int* tile_off; // [nimg + 1] prefix sums of ceil(nf nm / tw_s) (slow-pass tiles)
+  const int* mid_off;  // [nimg + 1] prefix sums of ns ceil(nf / tw_m) (middle-pass tiles; 0 in 2D)
   const int* midl_off; // [nimg + 1] prefix sums of nf ns (middle lines; 0 in 2D)
   int any3d;           // some image has a middle axis
   int line_stride;     // per-warp shared-memory region (XF): a staged line, its
@@ -146,22 +154,39 @@ __device__ __forceinline__ int owner(const int* off, int nimg, int t) {
   return i;
 }
 
+// shuffles within segments of w lanes
+__device__ __forceinline__ XF shw_up(XF a, int o, int w) {
+  return XF{__shfl_up_sync(0xffffffffu, a.m, o, w), __shfl_up_sync(0xffffffffu, a.e, o, w)};
+}
+__device__ __forceinline__ XF shw_down(XF a, int o, int w) {
+  return XF{__shfl_down_sync(0xffffffffu, a.m, o, w), __shfl_down_sync(0xffffffffu, a.e, o, w)};
+}
+__device__ __forceinline__ PairC<XF> shw_up(PairC<XF> a, int o, int w) {
+  return PairC<XF>{shw_up(a.p, o, w), shw_up(a.a, o, w)};
+}
+__device__ __forceinline__ PairC<XF> shw_down(PairC<XF> a, int o, int w) {
+  return PairC<XF>{shw_down(a.p, o, w), shw_down(a.a, o, w)};
+}
+
 // ---------------------------------------------------------------------------
 // warp line scan of L points: out = K x (plain) or the distance-weighted sum
-// (WEIGHTED).  Lane l owns points [l P, l P + P); its k-th point is at
-// index base + k step of in / out / tmp (base chosen by the caller for this
-// lane).  The lane's backward sums are parked in `tmp` (written and read back
-// by the same lane; tmp may alias out, and out may alias in).  tab: lam^j
-// (j <= 32) and lam^{P 2^i} at 33 + i.
+// (WEIGHTED), by a segment of G lanes (G = 8, 16 or 32; the warp's 32 / G
+// segments scan their own lines at once).  Lane l of a segment owns points
+// [l P, l P + P), P = ceil(L / G); its k-th point is at index base + k step of
+// in / out / tmp (base chosen by the caller for this lane).  Lv <= L points
+// are valid (0: the segment has no line).  The lane's backward sums are
+// parked in `tmp` (written and read back by the same lane; tmp may alias out,
+// and out may alias in).  tab: lam^j (j <= 32) and lam^{P 2^i} at ks + i.
 // ---------------------------------------------------------------------------
 template <bool WEIGHTED>
-__device__ void line_scan(const XF* in, XF* out, XF* tmp, int64_t base, int64_t step, int L, const XF* tab) {
+__device__ void line_scan(const XF* in, XF* out, XF* tmp, int64_t base, int64_t step, int L, int Lv, int G,
+                          const XF* tab, int ks) {
   using Op = typename std::conditional<WEIGHTED, OpDist<XF>, OpPlain<XF>>::type;
   using T = typename Op::T;
-  const int lane = threadIdx.x & 31;
-  const int P = (L + 31) >> 5;
+  const int lane = threadIdx.x & (G - 1);
+  const int P = (L + G - 1) / G;
   const int i0 = lane * P;
-  const int n = max(0, min(P, L - i0));
+  const int n = max(0, min(P, Lv - i0));
   const XF lam = tab[1];
   const XF zero = c_zero(XF{});
   T af, ab;
@@ -189,14 +214,15 @@ __device__ void line_scan(const XF* in, XF* out, XF* tmp, int64_t base, int64_t 
 #pragma unroll
   for (int lv = 0; lv < 5; ++lv) {
     const int o = 1 << lv;
-    const T y = Op::up(x, o);
-    const T w = Op::down(z, o);
-    if (lane >= o) x = Op::fwd(y, x, tab[33 + lv], (float)(P * o));
-    if (lane + o < 32) z = Op::bwd(z, w, tab[33 + lv], (float)(P * o));
+    if (o >= G) break;
+    const T y = shw_up(x, o, G);
+    const T w = shw_down(z, o, G);
+    if (lane >= o) x = Op::fwd(y, x, tab[ks + lv], (float)(P * o));
+    if (lane + o < G) z = Op::bwd(z, w, tab[ks + lv], (float)(P * o));
   }
-  T cfw = Op::up(x, 1), cbw = Op::down(z, 1);
+  T cfw = shw_up(x, 1, G), cbw = shw_down(z, 1, G);
   if (lane == 0) cfw = Op::zero();
-  if (lane == 31) cbw = Op::zero();
+  if (lane == G - 1) cbw = Op::zero();
   if (n <= 0) return;
   {
     XF s, B;
@@ -237,8 +263,8 @@ __device__ void line_scan(const XF* in, XF* out, XF* tmp, int64_t base, int64_t 
   }
 }
 
-// Fast plain line scan for a line staged in shared memory (lane chunk at
-// in[base + k], k < P): the lane's values are taken into one power-of-two
+// Fast plain line scan for a line staged in shared memory, by a segment of G
+// lanes (lane chunk at in[base + k], k < P): the lane's values are taken into one power-of-two
 // frame (the largest exponent of the chunk) and all four sweeps run in FP32,
 // as in the 1D kernel's per-thread frames; only the lane aggregates and the
 // 5-level Kogge-Stone use extended range.  A value below 2^-126 of the frame
@@ -246,10 +272,11 @@ __device__ void line_scan(const XF* in, XF* out, XF* tmp, int64_t base, int64_t 
 // sums, so with c P <= 40 (c = h / eps of the axis) the dropped part stays
 // below FP32 rounding.  Backward partials go to the float array tf at the
 // same indices.  out may alias in.
-__device__ void line_scan_frame(const XF* in, XF* out, float* tf, int64_t base, int L, const XF* tab) {
-  const int lane = threadIdx.x & 31;
-  const int P = (L + 31) >> 5;
-  const int n = max(0, min(P, L - lane * P));
+__device__ void line_scan_frame(const XF* in, XF* out, float* tf, int64_t base, int L, int Lv, int G,
+                                const XF* tab) {
+  const int lane = threadIdx.x & (G - 1);
+  const int P = (L + G - 1) / G;
+  const int n = max(0, min(P, Lv - lane * P));
   const float lam = tab[1].m * pow2f(tab[1].e);   // lam as FP32 (lam >= e^-40)
   int emax = kZeroExp;
 #pragma unroll 4
@@ -272,14 +299,15 @@ __device__ void line_scan_frame(const XF* in, XF* out, float* tf, int64_t base, 
 #pragma unroll
   for (int lv = 0; lv < 5; ++lv) {
     const int o = 1 << lv;
-    const XF y = shfl_up(x, o);
-    const XF w = shfl_down(z, o);
-    if (lane >= o) x = c_add(c_mul(y, tab[33 + lv]), x);
-    if (lane + o < 32) z = c_add(z, c_mul(w, tab[33 + lv]));
+    if (o >= G) break;
+    const XF y = shw_up(x, o, G);
+    const XF w = shw_down(z, o, G);
+    if (lane >= o) x = c_add(c_mul(y, tab[kTabSeg + lv]), x);
+    if (lane + o < G) z = c_add(z, c_mul(w, tab[kTabSeg + lv]));
   }
-  XF cfw = shfl_up(x, 1), cbw = shfl_down(z, 1);
+  XF cfw = shw_up(x, 1, G), cbw = shw_down(z, 1, G);
   if (lane == 0) cfw = XF{0.f, kZeroExp};
-  if (lane == 31) cbw = XF{0.f, kZeroExp};
+  if (lane == G - 1) cbw = XF{0.f, kZeroExp};
   if (n <= 0) return;
   // final sweeps in frame F: room for P terms of the chunk plus the carries
   const int F = max(emax, max(cfw.e, cbw.e)) + 6;
@@ -304,19 +332,19 @@ __device__ void line_scan_frame(const XF* in, XF* out, float* tf, int64_t base, 
 template <bool WEIGHTED>
 __device__ void line_scan_global(const XF* in, XF* out, XF* tmp, int64_t stride, int L, const XF* tab) {
   const int P = (L + 31) >> 5;
-  line_scan<WEIGHTED>(in, out, tmp, (int64_t)(threadIdx.x & 31) * P * stride, stride, L, tab);
+  line_scan<WEIGHTED>(in, out, tmp, (int64_t)(threadIdx.x & 31) * P * stride, stride, L, L, 32, tab, kTabWarp);
 }
 
-// Walks j = j0, j0 + 32, j0 + 64, ... of a line of P-point lane chunks and
-// yields j's shared-memory index (j / P) P' + j % P without a division per
-// step.
+// Walks j = j0, j0 + step, j0 + 2 step, ... of a line of P-point lane chunks
+// and yields j's shared-memory index (j / P) P' + j % P without a division
+// per step.
 struct ChunkPos {
   int d, m, dq, mq, P, Pp;
-  __device__ ChunkPos(int j0, int P_) : P(P_), Pp(P_ | 1) {
+  __device__ ChunkPos(int j0, int P_, int step) : P(P_), Pp(P_ | 1) {
     d = j0 / P;
     m = j0 - d * P;
-    dq = 32 / P;
-    mq = 32 - dq * P;
+    dq = step / P;
+    mq = step - dq * P;
   }
   __device__ int pos() const { return d * Pp + m; }
   __device__ void next() {
@@ -329,53 +357,73 @@ struct ChunkPos {
   }
 };
 
-// fast pass of one row (one warp): stage, scan in shared memory, store
-__device__ void row_pass(const XF* in, XF* out, int L, const XF* tab, bool frame, XF* s, XF* t) {
+// fast pass of a group of 32 / G rows (one warp, one G-lane segment per row):
+// stage, scan in shared memory, store.  Rows r0 .. of an image with `nrows`
+// rows of L points; segment q takes row r0 + q.
+__device__ void row_pass(const XF* in, XF* out, int nrows, int r0, int L, int G, const XF* tab, bool frame, XF* s,
+                         XF* t) {
   const int lane = threadIdx.x & 31;
-  const int P = (L + 31) >> 5;
-  {
+  const int seg = lane / G, ls = lane & (G - 1);
+  const int P = (L + G - 1) / G, Pp = P | 1;
+  const int r = r0 + seg;
+  const bool valid = r < nrows;
+  const int64_t o = (int64_t)r * L;
+  XF* const sseg = s + seg * G * Pp;
+  if (valid) {
     // every point of the row in flight at once (asynchronous copies)
-    ChunkPos q(lane, P);
-    for (int j = lane; j < L; j += 32, q.next()) cp_async8(s + q.pos(), in + j);
+    ChunkPos q(ls, P, G);
+    for (int j = ls; j < L; j += G, q.next()) cp_async8(sseg + q.pos(), in + o + j);
     cp_async_wait_all();
   }
   __syncwarp();
   if (frame)
-    line_scan_frame(s, s, reinterpret_cast<float*>(t), (int64_t)lane * (P | 1), L, tab);
+    line_scan_frame(s, s, reinterpret_cast<float*>(t), (int64_t)lane * Pp, L, valid ? L : 0, G, tab);
   else
-    line_scan<false>(s, s, t, (int64_t)lane * (P | 1), 1, L, tab);
+    line_scan<false>(s, s, t, (int64_t)lane * Pp, 1, L, valid ? L : 0, G, tab, kTabSeg);
   __syncwarp();
-  {
-    ChunkPos q(lane, P);
-    for (int j = lane; j < L; j += 32, q.next()) out[j] = s[q.pos()];
+  if (valid) {
+    ChunkPos q(ls, P, G);
+    for (int j = ls; j < L; j += G, q.next()) out[o + j] = sseg[q.pos()];
   }
   __syncwarp();
 }
 
-// slow pass of one tile of columns col0 .. col0 + 7 (the whole CTA): stage the
-// tile (thread -> column threadIdx % 8, rows threadIdx / 8 + 32 k), then warp
-// w scans column col0 + w in its shared-memory region; the caller's epilogue
-// reads the results through the same thread -> (row, column) map.
-__device__ void col_tile_scan(const XF* Y, int nf, int ns, int col0, const XF* tab, bool frame, XF* sbuf,
-                              int stride) {
-  const int c = threadIdx.x & (kTileCols - 1);
+// Column tiles (slow and middle passes, the whole CTA).  A tile holds TW =
+// 8 x 32 / G columns col0 .. col0 + TW - 1 of a plane `width` points wide;
+// column c is scanned by segment c % (32 / G) of warp c / (32 / G), in that
+// warp's shared-memory region.  Thread t stages and (in the caller's
+// epilogue) reads column t % TW at rows t / TW + k (256 / TW), so a warp
+// load covers whole row segments of the tile.
+struct TileMap {
+  int G, spw, TW, dr, P, Pp;
+  __device__ TileMap(int G_, int L) : G(G_), spw(32 / G_), TW(kTileCols * (32 / G_)), dr(kThreads2 / TW),
+                                      P((L + G_ - 1) / G_), Pp(((L + G_ - 1) / G_) | 1) {}
+  __device__ int col() const { return threadIdx.x % TW; }
+  __device__ int row0() const { return threadIdx.x / TW; }
+  // the staged line of tile column c
+  __device__ XF* line(XF* sbuf, int stride, int c) const { return sbuf + (c / spw) * stride + (c % spw) * G * Pp; }
+};
+
+__device__ void col_tile_scan(const XF* Y, int width, int ns, int col0, const TileMap& M, const XF* tab, bool frame,
+                              XF* sbuf, int stride) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int P = (ns + 31) >> 5;
-  const int CH = 32 * (P | 1);
-  if (col0 + c < nf) {
-    XF* s = sbuf + c * stride;
-    ChunkPos q(threadIdx.x / kTileCols, P);
-    for (int r = threadIdx.x / kTileCols; r < ns; r += kThreads2 / kTileCols, q.next())
-      cp_async8(s + q.pos(), Y + (int64_t)r * nf + col0 + c);
+  const int c = M.col();
+  if (col0 + c < width) {
+    XF* sl = M.line(sbuf, stride, c);
+    ChunkPos q(M.row0(), M.P, M.dr);
+    for (int r = M.row0(); r < ns; r += M.dr, q.next()) cp_async8(sl + q.pos(), Y + (int64_t)r * width + col0 + c);
     cp_async_wait_all();
   }
   __syncthreads();
-  if (col0 + warp < nf) {
+  {
+    const int cs = warp * M.spw + lane / M.G;   // the column this lane's segment scans
+    const int Lv = col0 + cs < width ? ns : 0;
     XF* s = sbuf + warp * stride;
+    const int CH = 32 * M.Pp;
     if (frame)
-      line_scan_frame(s, s, reinterpret_cast<float*>(s + CH), (int64_t)lane * (P | 1), ns, tab);
+      line_scan_frame(s, s, reinterpret_cast<float*>(s + CH), (int64_t)lane * M.Pp, ns, Lv, M.G, tab);
     else
-      line_scan<false>(s, s, s + CH, (int64_t)lane * (P | 1), 1, ns, tab);
+      line_scan<false>(s, s, s + CH, (int64_t)lane * M.Pp, 1, ns, Lv, M.G, tab, kTabSeg);
   }
   __syncthreads();
 }
@@ -399,6 +447,7 @@ __global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
   __shared__ float sred[2 * kWarps2];
   __shared__ int srow[kMaxImg2D + 1], scol[kMaxImg2D + 1], stile[kMaxImg2D + 1];
   __shared__ int smid[kMaxImg2D + 1], smidl[kMaxImg2D + 1];
+  __shared__ int srowa[kMaxImg2D + 1];      // prefix sums of the rows (nm ns), one per warp in the cost phase
   __shared__ signed char sstate[kMaxImg2D];  // 0 active, 1 stops this iteration, 2 stopped earlier
   __shared__ bool sframe[kMaxImg2D][3];      // the axis takes the FP32-frame line scan (c P <= 40)
   __shared__ int sok;
@@ -415,14 +464,28 @@ __global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
     smid[i] = L.mid_off[i];
     smidl[i] = L.midl_off[i];
   }
+  // descriptor check (every CTA decides alike): lanes per line must be 8, 16
+  // or 32 and the tile widths must match them, or the loops below would not
+  // advance; a bad descriptor ends the launch (its results stay
+  // FS1_ETIMEOUT) instead of running
+  {
+    bool okd = true;
+    for (int i = 0; i < nimg; ++i) {
+      const Img2D& I = L.imgs[i];
+      for (int ax = 0; ax < 3; ++ax) okd = okd && (I.g[ax] == 8 || I.g[ax] == 16 || I.g[ax] == 32);
+      okd = okd && I.tw_s == kTileCols * (32 / max(1, I.g[1])) && I.tw_m == kTileCols * (32 / max(1, I.g[2]));
+    }
+    if (!okd) {
+      if (threadIdx.x == 0) atomicExch(L.abort_flag, 1);
+      return;
+    }
+  }
   XF* const s_own = sline + warp * L.line_stride;            // this warp's region
   XF* const t_own = s_own + L.line_ch;
-  for (int t = threadIdx.x; t < nimg * 3; t += blockDim.x) {
-    const Img2D& I = L.imgs[t / 3];
-    const int ax = t % 3;
-    const int len = ax == 0 ? I.nf : (ax == 1 ? I.ns : I.nm);
-    const double c = ax == 0 ? I.cf : (ax == 1 ? I.cs : I.cm);
-    sframe[t / 3][ax] = c * (double)((len + 31) >> 5) <= 40.0;
+  for (int t = threadIdx.x; t < nimg * 3; t += blockDim.x) sframe[t / 3][t % 3] = L.imgs[t / 3].frame[t % 3] != 0;
+  if (threadIdx.x == 0) {
+    srowa[0] = 0;
+    for (int i = 0; i < nimg; ++i) srowa[i + 1] = srowa[i] + L.imgs[i].nm * L.imgs[i].ns;
   }
   // decay tables [image][axis][j] in global memory (CTA 0; the grid barrier
   // below publishes them)
@@ -431,8 +494,10 @@ __global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
     const Img2D& I = L.imgs[i];
     const double c = ax == 0 ? I.cf : (ax == 1 ? I.cs : I.cm);
     const int len = ax == 0 ? I.nf : (ax == 1 ? I.ns : I.nm);
-    const int P = (len + 31) >> 5;
-    const double k = j <= 32 ? (double)j : (double)P * (double)(1 << (j - 33));
+    const int Pseg = (len + I.g[ax] - 1) / I.g[ax], Pw = (len + 31) >> 5;
+    const double k = j < kTabSeg ? (double)j
+                   : (j < kTabWarp ? (double)Pseg * (double)(1 << (j - kTabSeg))
+                                   : (double)Pw * (double)(1 << (j - kTabWarp)));
     L.tab[t] = c_decay(k, c, XF{});
   }
   auto tab = [&](int i, int ax) -> const XF* { return L.tab + (i * 3 + ax) * kTab; };
@@ -456,16 +521,17 @@ __global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
       const int i = owner(smid, nimg, t);
       if (sstate[i]) continue;   // CTA-uniform
       const Img2D& I = L.imgs[i];
-      const int ntf = (I.nf + kTileCols - 1) / kTileCols;
+      const TileMap M(I.g[2], I.nm);
+      const int ntf = (I.nf + M.TW - 1) / M.TW;
       const int tt = t - smid[i];
       const int64_t base = (int64_t)(tt / ntf) * I.nf * I.nm;   // the slab
-      const int col0 = (tt % ntf) * kTileCols;
-      col_tile_scan(I.Y + base, I.nf, I.nm, col0, tab(i, 2), sframe[i][2], sline, L.line_stride);
-      const int c = threadIdx.x & (kTileCols - 1);
+      const int col0 = (tt % ntf) * M.TW;
+      col_tile_scan(I.Y + base, I.nf, I.nm, col0, M, tab(i, 2), sframe[i][2], sline, L.line_stride);
+      const int c = M.col();
       if (col0 + c < I.nf) {
-        const XF* sc = sline + c * L.line_stride;
-        ChunkPos q(threadIdx.x / kTileCols, (I.nm + 31) >> 5);
-        for (int r = threadIdx.x / kTileCols; r < I.nm; r += kThreads2 / kTileCols, q.next())
+        const XF* sc = M.line(sline, L.line_stride, c);
+        ChunkPos q(M.row0(), M.P, M.dr);
+        for (int r = M.row0(); r < I.nm; r += M.dr, q.next())
           I.R[base + (int64_t)r * I.nf + col0 + c] = sc[q.pos()];
       }
       __syncthreads();   // the tile's shared memory is reused by the next tile
@@ -486,8 +552,8 @@ __global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
       const int i = owner(srow, nimg, t);
       if (sstate[i]) continue;
       const Img2D& I = L.imgs[i];
-      const int64_t o = (int64_t)(t - srow[i]) * I.nf;
-      row_pass(I.U + o, I.Y + o, I.nf, tab(i, 0), sframe[i][0], s_own, t_own);
+      row_pass(I.U, I.Y, I.nm * I.ns, (t - srow[i]) * (32 / I.g[0]), I.nf, I.g[0], tab(i, 0), sframe[i][0], s_own,
+               t_own);
     }
     if (!grid_barrier(L, gen, &sok)) return;
     if (L.any3d && !mid_pass()) return;
@@ -497,17 +563,18 @@ __global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
       if (sstate[i]) continue;   // CTA-uniform
       const Img2D& I = L.imgs[i];
       const int W = I.nf * I.nm;   // points of a slab: the slow lines' stride
+      const TileMap M(I.g[1], I.ns);
       const int tile = t - stile[i];
-      const int col0 = tile * kTileCols;
-      col_tile_scan(I.nm > 1 ? I.R : I.Y, W, I.ns, col0, tab(i, 1), sframe[i][1], sline, L.line_stride);
+      const int col0 = tile * M.TW;
+      col_tile_scan(I.nm > 1 ? I.R : I.Y, W, I.ns, col0, M, tab(i, 1), sframe[i][1], sline, L.line_stride);
       XF* Vn = I.V[par ^ 1];
       float eh = 0.f, el = 0.f;
-      const int c = threadIdx.x & (kTileCols - 1);
+      const int c = M.col();
       if (col0 + c < W) {
-        const XF* sc = sline + c * L.line_stride;
-        const int r0 = threadIdx.x / kTileCols;
-        constexpr int dr = kThreads2 / kTileCols;
-        ChunkPos q(r0, (I.ns + 31) >> 5);
+        const XF* sc = M.line(sline, L.line_stride, c);
+        const int r0 = M.row0();
+        const int dr = M.dr;
+        ChunkPos q(r0, M.P, dr);
         for (int rb = r0; rb < I.ns; rb += dr * kBatch) {
           float mb[kBatch];
           XF vb[kBatch];
@@ -542,7 +609,7 @@ __global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
       if (sstate[i]) continue;
       const Img2D& I = L.imgs[i];
       float h = 0.f, l = 0.f;
-      const int nt = (I.nf * I.nm + kTileCols - 1) / kTileCols;
+      const int nt = (I.nf * I.nm + I.tw_s - 1) / I.tw_s;
       for (int c = lane; c < nt; c += 32) df_add(h, l, __ldcg(I.errp + 2 * c), __ldcg(I.errp + 2 * c + 1));
       warp_sum_df(h, l);
       if (lane == 0) {
@@ -565,8 +632,8 @@ __global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
       const int i = owner(srow, nimg, t);
       if (sstate[i]) continue;
       const Img2D& I = L.imgs[i];
-      const int64_t o = (int64_t)(t - srow[i]) * I.nf;
-      row_pass(I.V[par ^ 1] + o, I.Y + o, I.nf, tab(i, 0), sframe[i][0], s_own, t_own);
+      row_pass(I.V[par ^ 1], I.Y, I.nm * I.ns, (t - srow[i]) * (32 / I.g[0]), I.nf, I.g[0], tab(i, 0), sframe[i][0],
+               s_own, t_own);
     }
     if (!grid_barrier(L, gen, &sok)) return;
     if (L.any3d && !mid_pass()) return;
@@ -576,14 +643,15 @@ __global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
       if (sstate[i]) continue;   // CTA-uniform
       const Img2D& I = L.imgs[i];
       const int W = I.nf * I.nm;
-      const int col0 = (t - stile[i]) * kTileCols;
-      col_tile_scan(I.nm > 1 ? I.R : I.Y, W, I.ns, col0, tab(i, 1), sframe[i][1], sline, L.line_stride);
-      const int c = threadIdx.x & (kTileCols - 1);
+      const TileMap M(I.g[1], I.ns);
+      const int col0 = (t - stile[i]) * M.TW;
+      col_tile_scan(I.nm > 1 ? I.R : I.Y, W, I.ns, col0, M, tab(i, 1), sframe[i][1], sline, L.line_stride);
+      const int c = M.col();
       if (col0 + c < W) {
-        const XF* sc = sline + c * L.line_stride;
-        const int r0 = threadIdx.x / kTileCols;
-        constexpr int dr = kThreads2 / kTileCols;
-        ChunkPos q(r0, (I.ns + 31) >> 5);
+        const XF* sc = M.line(sline, L.line_stride, c);
+        const int r0 = M.row0();
+        const int dr = M.dr;
+        ChunkPos q(r0, M.P, dr);
         for (int rb = r0; rb < I.ns; rb += dr * kBatch) {
           float mb[kBatch];
 #pragma unroll
@@ -623,11 +691,12 @@ __global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
   // ---- transport cost: sum over axes a of h_a u . (K with the distance-
   // weighted K_a^(c) on axis a) v
   // rows: Y = (I (x) K_f^(c)) v (weighted); V1 = (I (x) K_f) v in the free v buffer
-  for (int t = gw; t < rows; t += nw) {
-    const int i = owner(srow, nimg, t);
+  const int wrows = srowa[nimg];
+  for (int t = gw; t < wrows; t += nw) {
+    const int i = owner(srowa, nimg, t);
     const Img2D& I = L.imgs[i];
     const int k = (ld_relaxed(I.stop) - 1) & 1;
-    const int64_t o = (int64_t)(t - srow[i]) * I.nf;
+    const int64_t o = (int64_t)(t - srowa[i]) * I.nf;
     line_scan_global<true>(I.V[k] + o, I.Y + o, I.R + o, 1, I.nf, tab(i, 0));
     __syncwarp();
     line_scan_global<false>(I.V[k] + o, I.V[k ^ 1] + o, I.R + o, 1, I.nf, tab(i, 0));
@@ -701,6 +770,19 @@ __global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
 }
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Lanes that share a line of L points with c = h / eps: the fewest of 8, 16,
+// 32 that keep P = ceil(L / G) <= 16 points per lane and keep the FP32-frame
+// scan (c P <= 40) when 32 lanes would allow it.  Fewer lanes per line mean a
+// shorter lane scan and more points per lane for short lines.
+int line_lanes(int L, double c) {
+  const bool frame32 = c * ((L + 31) / 32) <= 40.0;
+  for (int G = 8; G < 32; G *= 2) {
+    const int P = (L + G - 1) / G;
+    if (P <= 16 && (!frame32 || c * P <= 40.0)) return G;
+  }
+  return 32;
+}
 
 }  // namespace
 
@@ -779,16 +861,27 @@ int launch_solve_2d(const PairDesc* d, int count, int in_f32, PairResult* result
     I.stop = (int*)p;
     if (!stops) stops = p;
     p += 256;
-    imgs[i] = I;
-    row[i + 1] = row[i] + I.nm * I.ns;
+    const int len[3] = {I.nf, I.ns, I.nm};
+    const double cax[3] = {I.cf, I.cs, I.cm};
+    for (int ax = 0; ax < 3; ++ax) {
+      I.g[ax] = line_lanes(len[ax], cax[ax]);
+      const int P = (len[ax] + I.g[ax] - 1) / I.g[ax];
+      I.frame[ax] = cax[ax] * P <= 40.0 ? 1 : 0;
+      if (ax < 2 || I.nm > 1) {
+        pp_max = std::max(pp_max, P | 1);
+        any_ext = any_ext || !I.frame[ax];
+      }
+    }
+    I.tw_s = kTileCols * (32 / I.g[1]);
+    I.tw_m = kTileCols * (32 / I.g[2]);
+    const int rpw = 32 / I.g[0];   // rows a warp takes at once
+    row[i + 1] = row[i] + (I.nm * I.ns + rpw - 1) / rpw;
     col[i + 1] = col[i] + (int)W;
-    tile[i + 1] = tile[i] + ((int)W + kTileCols - 1) / kTileCols;
-    mid[i + 1] = mid[i] + (I.nm > 1 ? I.ns * ((I.nf + kTileCols - 1) / kTileCols) : 0);
+    tile[i + 1] = tile[i] + ((int)W + I.tw_s - 1) / I.tw_s;
+    mid[i + 1] = mid[i] + (I.nm > 1 ? I.ns * ((I.nf + I.tw_m - 1) / I.tw_m) : 0);
     midl[i + 1] = midl[i] + (I.nm > 1 ? I.nf * I.ns : 0);
     any3d |= I.nm > 1;
-    pp_max = std::max(pp_max, std::max((I.nf + 31) / 32, std::max((I.nm + 31) / 32, (I.ns + 31) / 32)) | 1);
-    any_ext = any_ext || I.cf * ((I.nf + 31) / 32) > 40.0 || I.cs * ((I.ns + 31) / 32) > 40.0 ||
-              I.cm * ((I.nm + 31) / 32) > 40.0;
+    imgs[i] = I;   // after every field is set
   }
   cudaError_t e = cudaSuccess;
   for (int i = 0; i < count && e == cudaSuccess; ++i) e = cudaMemsetAsync(imgs[i].stop, 0, sizeof(int), st);

@@ -176,7 +176,9 @@ class Server:
             s.req.ticks += 1
             r = s.req
             r.w1, r.err, r.iters = w, err, s.done_iters
-            if st == self.ENOTCONV and s.done_iters < r.itr_max:
+            # an unconverged request that made no progress in its tick (only a
+            # failed solve does that) retires instead of looping
+            if st == self.ENOTCONV and s.done_iters < r.itr_max and it > 0:
                 keep.append(s)
                 continue
             r.status = st

@@ -27,7 +27,7 @@ def test_mix_equals_alone(env):
                              eps_range=(3e-3, 2e-2), itr_max=1200)
         reqs.append(serve.Request(i, p.a, p.b, tuple(p.h), p.eps, p.tol, p.itr_max, p.arrival))
     srv = serve.Server(int(4e9), tick_iters=150)
-    summ = srv.run(reqs)
+    summ = srv.run(reqs, max_seconds=300.0)
     srv.close()
     assert summ["completed"] == len(reqs)
     assert srv.ticks >= 2 and srv.admitted_while_busy >= 1
