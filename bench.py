@@ -21,6 +21,9 @@ fs1_solve_batch; --workload picks one, 2 is the default and the headline):
      h = 1, eps = 1e-2, 1000 iterations
   9  32 3D grids of 64^3 cells, eps = 2e-3, 1-3 Gaussian blobs + 1e-7 floor,
      stabilised FP32, marginal error 1e-6 or 2000 iterations
+  10 the Remarks' tau-triggered stabilised form as written (FP64) on the
+     Section 5.2 Ricker pair at N = 2000, eps = 5e-4 (where the plain FP64
+     iteration overflows), 500 iterations, 100 repeats
 For 6-8 vs_baseline is the ratio to the FS-1 rate the paper's tables imply on
 its CPU (context: another machine).
 The serving workload is measured by `python -m paper_2202_10042_gb300.serve`.
@@ -94,10 +97,14 @@ WORKLOADS = {
             paper=160 * 160 * 1000 / 1.08),
     9: dict(name="fs1_3d_log_fp32_batch32_64^3_eps2e-3", pairs=32, variant="log", precision="fp32",
             dtype="f32", bytes_per_nit=28.0, kw={}, sample_pairs=4, sample_iters=20, solo=2),
+    10: dict(name="paper_form_fp64_ricker_n2000_eps5e-4_it500", pairs=100, variant="paper", precision="fp64",
+             dtype="f64", bytes_per_nit=56.0, kw=dict(n=2000, eps=5e-4, itr_max=500), sample_pairs=4,
+             sample_iters=500, solo=4),
 }
 
 GENERATORS = {1: inputs.workload1, 2: inputs.workload2, 3: inputs.workload3, 4: inputs.workload4,
-              6: inputs.paper_e1, 7: inputs.paper_e2, 8: inputs.paper_e3, 9: inputs.workload9}
+              6: inputs.paper_e1, 7: inputs.paper_e2, 8: inputs.paper_e3, 9: inputs.workload9,
+              10: inputs.paper_e2}
 
 
 def gen_problem(workload: int, index: int, **over):

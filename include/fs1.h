@@ -52,11 +52,18 @@ typedef enum fs1_status {
 
 enum fs1_variant {
   FS1_VARIANT_PLAIN = 0, /* Algorithm 1 / 2 as written: linear u, v, no stabilisation */
-  FS1_VARIANT_LOG = 1    /* log-domain stabilised (Remarks in Sections 2 and 3):
+  FS1_VARIANT_LOG = 1,   /* log-domain stabilised (Remarks in Sections 2 and 3):
                             the scalings are kept as FP32 mantissas times per-thread
                             power-of-two frames that absorb their magnitude every
                             half-step, and the chunk carries are combined with a
                             max-shifted (exponent-aligned) sum */
+  FS1_VARIANT_PAPER = 2  /* the stabilised form of the Remarks as written, FP64: scalings
+                            phi~, psi~ and absorbed potentials A = alpha/eps, B = beta/eps
+                            per point; when max|phi~| or max|psi~| exceeds tau they are
+                            absorbed (A += ln phi~, B += ln psi~, phi~ = psi~ = 1), and the
+                            sweeps use the per-point factors lam e^{+-(S_{k+1} - S_k)} of
+                            the replaced lines 5, 6, 10, 11.  1D, one CTA per pair,
+                            N <= 16384, a and b > 0 */
 };
 
 enum fs1_precision { FS1_FP64 = 0, FS1_FP32 = 1 };
@@ -65,7 +72,8 @@ enum fs1_location { FS1_MEM_DEVICE = 0, FS1_MEM_HOST = 1 };
 typedef struct fs1_config {
   int variant;          /* enum fs1_variant (default FS1_VARIANT_LOG) */
   int precision;        /* enum fs1_precision of the iteration arithmetic
-                           (default FS1_FP32; FS1_VARIANT_PLAIN also takes FS1_FP64) */
+                           (default FS1_FP32; FS1_VARIANT_PLAIN also takes FS1_FP64;
+                           FS1_VARIANT_PAPER takes FS1_FP64 only) */
   int check_every;      /* marginal-error test every k iterations; 1 = the paper's
                            rule (default 1; only 1 is implemented) */
   int team_size;        /* CTAs that share one pair; 0 = pick from the size */
@@ -82,6 +90,7 @@ typedef struct fs1_config {
                            signature on, the call's device work (header copy, slot reset,
                            input check, team kernel, result copy) is one replayed CUDA
                            graph; 0: direct launches */
+  double tau;           /* absorption threshold of FS1_VARIANT_PAPER (default 1e10) */
 } fs1_config;
 
 typedef struct fs1_problem {

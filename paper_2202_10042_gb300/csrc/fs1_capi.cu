@@ -179,6 +179,7 @@ __global__ void validate_kernel(const PairDesc* pairs, int in_f32, int* valid) {
 
 int kind_of(const fs1_config& c) {
   if (c.variant == FS1_VARIANT_PLAIN) return c.precision == FS1_FP64 ? KK_PLAIN_F64 : KK_PLAIN_F32;
+  if (c.variant == FS1_VARIANT_PAPER) return KK_PAPER_F64;
   return KK_LOG_F32;
 }
 
@@ -515,14 +516,19 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
   const int count = (int)ps.size();
   const bool two_d = ps[0]->ndim >= 2;   // 2D and 3D grids share the grid kernel
   fs1_status st = FS1_OK;
+  const bool paper = kind == KK_PAPER_F64;   // one CTA per pair, no teams
   if (two_d) {
     if (kind != KK_LOG_F32) return FS1_EUNSUPPORTED;   // 2D runs the stabilised FP32 variant
     geo.team_size = 0;
     geo.num_teams = 0;
+  } else if (paper) {
+    if (mode != 0) return FS1_EUNSUPPORTED;
+    geo.team_size = 1;
+    geo.num_teams = count;
   } else if ((st = choose_geometry(h, kind, ps, &geo)) != FS1_OK) {
     return st;
   }
-  const bool planned = !two_d && mode == 0;
+  const bool planned = !two_d && !paper && mode == 0;
   if (planned && h->cfg.autotune && h->cfg.team_size <= 0 && !h->tuning) {
     const int maxc = max_coresident_ctas(kind);
     const std::string key = tune_key(h, kind, ps, maxc);
@@ -532,7 +538,7 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
   if (planned && (st = plan_teams(h, kind, ps, &plan)) != FS1_OK) return st;
   const int T = two_d ? 1 : (planned ? plan.max_T : geo.team_size);
   const int teams = two_d ? 1 : (planned ? plan.num_teams : geo.num_teams);
-  const size_t nslots = two_d ? 0 : (planned ? (size_t)plan.slots : (size_t)teams * 2 * T);
+  const size_t nslots = (two_d || paper) ? 0 : (planned ? (size_t)plan.slots : (size_t)teams * 2 * T);
   const int in_f32 = ps[0]->dtype == FS1_FP32;
   const int nclass = planned ? (int)plan.class_T.size() : 0;
   const int pgrid = planned ? plan.grid : 0;
@@ -546,6 +552,7 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
   const size_t o_tick = off; off = align_up(off + sizeof(unsigned long long) * (planned ? teams : 0), 256);
   const size_t o_ctr = off;  off = align_up(off + sizeof(unsigned long long) * teams, 256);
   const size_t o_abt = off;  off = align_up(off + sizeof(int) * teams, 256);
+  const size_t o_poff = off; off = align_up(off + sizeof(int64_t) * (paper ? count : 0), 256);
   const size_t hdr = off;
   const size_t o_val = off;  off = align_up(off + sizeof(int) * count, 256);
   const size_t o_slot = off; off = align_up(off + sizeof(Slot) * nslots, 256);
@@ -575,6 +582,18 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
   }
   const size_t o_2d = off;
   if (two_d) off = align_up(off + solve2d_workspace(desc.data(), count), 256);
+  // paper form: kPaperArrays FP64 arrays of N per pair
+  std::vector<int64_t> poff(paper ? count : 0);
+  const size_t o_paper = off;
+  if (paper) {
+    int64_t acc = 0;
+    for (int i = 0; i < count; ++i) {
+      if (desc[i].n > kMaxPaperN) return FS1_EUNSUPPORTED;
+      poff[i] = acc;
+      acc += (int64_t)kPaperArrays * desc[i].n;
+    }
+    off = align_up(off + sizeof(double) * (size_t)acc, 256);
+  }
   if ((st = ensure_ws(h, off)) != FS1_OK) return st;
   if ((st = ensure_pinned(h, &h->hdr, &h->hdr_bytes, hdr)) != FS1_OK) return st;
   if ((st = ensure_pinned(h, &h->hres, &h->hres_bytes, sizeof(PairResult) * count + sizeof(int) * count)) !=
@@ -597,6 +616,7 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
     }
     // class_next stays zero
   }
+  if (paper) memcpy(hb + o_poff, poff.data(), sizeof(int64_t) * count);
   PairResult* hres = (PairResult*)h->hres;
   cudaError_t e;
 
@@ -677,7 +697,9 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
         cudaEventRecordWithFlags(h->ev0, s, cudaEventRecordExternal);
       else
         cudaEventRecord(h->ev0, s);
-      const int ls = launch_team_1d(kind | (mode << 8), L, s);
+      const int ls = paper ? launch_paper_1d(L.pairs, count, L.results, (double*)(ws + o_paper),
+                                             (const int64_t*)(ws + o_poff), in_f32, h->cfg.tau, L.valid, s)
+                           : launch_team_1d(kind | (mode << 8), L, s);
       if (ls != FS1_OK) return (fs1_status)ls;
       if (capturing)
         cudaEventRecordWithFlags(h->ev1, s, cudaEventRecordExternal);
@@ -775,6 +797,7 @@ fs1_status fs1_config_default(fs1_config* cfg) {
   cfg->autotune = 1;
   cfg->trial_iters = 48;
   cfg->use_graph = 1;
+  cfg->tau = 1e10;
   return FS1_OK;
 }
 
@@ -783,9 +806,12 @@ fs1_status fs1_create(const fs1_config* cfg, fs1_handle** out) {
   *out = nullptr;
   fs1_config c;
   if (cfg) c = *cfg; else fs1_config_default(&c);
-  if (c.variant != FS1_VARIANT_PLAIN && c.variant != FS1_VARIANT_LOG) return FS1_EINVAL;
+  if (c.variant != FS1_VARIANT_PLAIN && c.variant != FS1_VARIANT_LOG && c.variant != FS1_VARIANT_PAPER)
+    return FS1_EINVAL;
   if (c.precision != FS1_FP64 && c.precision != FS1_FP32) return FS1_EINVAL;
   if (c.variant == FS1_VARIANT_LOG && c.precision != FS1_FP32) return FS1_EUNSUPPORTED;
+  if (c.variant == FS1_VARIANT_PAPER && c.precision != FS1_FP64) return FS1_EUNSUPPORTED;
+  if (c.variant == FS1_VARIANT_PAPER && !(c.tau > 0.0)) return FS1_EINVAL;
   if (c.check_every != 1) return FS1_EUNSUPPORTED;
   if (c.spin_cap <= 0) c.spin_cap = 1ll << 22;
   if (c.trial_iters <= 0) c.trial_iters = 48;
@@ -860,6 +886,9 @@ fs1_status fs1_solve_batch(fs1_handle* h, const fs1_problem* probs, int64_t coun
   size_t need = 0;
   for (int64_t i = 0; i < count; ++i) {
     pst[i] = check_problem(probs[i]);
+    // the paper form solves 1D pairs of up to kMaxPaperN points (one CTA each)
+    if (pst[i] == FS1_OK && kind == KK_PAPER_F64 && (probs[i].ndim != 1 || npoints(probs[i]) > kMaxPaperN))
+      pst[i] = FS1_EUNSUPPORTED;
     if (pst[i] != FS1_OK || probs[i].location != FS1_MEM_HOST) continue;
     const int64_t n = npoints(probs[i]);
     const size_t in_b = align_up((probs[i].dtype == FS1_FP32 ? 4 : 8) * (size_t)n, 256);

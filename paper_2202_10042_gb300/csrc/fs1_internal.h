@@ -75,6 +75,7 @@ enum KernelKind {
   KK_PLAIN_F64 = 0,   // plain FS-1 (Algorithm 1 as written), FP64
   KK_PLAIN_F32 = 1,   // plain FS-1, FP32 (no stabilisation)
   KK_LOG_F32 = 2,     // stabilised FS-1: FP32 mantissas in extended range
+  KK_PAPER_F64 = 3,   // the Remarks' tau-triggered absorption as written, FP64
 };
 
 // 2D / 3D solver (fs1_solve2d.cu): up to kMaxImg2D grids per launch.
@@ -83,6 +84,15 @@ constexpr int kMaxLine2D = 1024;   // longest line along any axis (staged in sha
 size_t solve2d_workspace(const PairDesc* host_descs, int count);
 int launch_solve_2d(const PairDesc* host_descs, int count, int in_f32, PairResult* d_results, void* ws,
                     size_t ws_bytes, long long spin_cap, void* stream);
+
+// Paper-form solver (fs1_paper.cu): one CTA per pair, N <= kMaxPaperN.
+constexpr int kMaxPaperN = 16384;
+// FP64 doubles of per-pair workspace per grid point
+constexpr int kPaperArrays = 10;
+// d_off[i]: offset (in doubles) of pair i's kPaperArrays x N workspace in ws;
+// d_valid: input-check flags (may be null).
+int launch_paper_1d(const PairDesc* d_pairs, int count, PairResult* d_results, double* ws, const int64_t* d_off,
+                    int in_f32, double tau, const int* d_valid, void* stream);
 
 // Host-side launch helpers (fs1_solve1d.cu).
 int team_threads();

@@ -128,6 +128,7 @@ extern "C" fs1_status fs1_w1_noalloc(const fs1_config* cfg_in, const fs1_problem
   fs1_config cfg;
   if (cfg_in) cfg = *cfg_in; else fs1_config_default(&cfg);
   const fs1_problem& p = *prob;
+  if (cfg.variant == FS1_VARIANT_PAPER) return FS1_EUNSUPPORTED;   // the team kernel only
   if (cfg.variant != FS1_VARIANT_PLAIN && cfg.variant != FS1_VARIANT_LOG) return FS1_EINVAL;
   if (cfg.variant == FS1_VARIANT_LOG && cfg.precision != FS1_FP32) return FS1_EUNSUPPORTED;
   if (cfg.check_every != 1) return FS1_EUNSUPPORTED;

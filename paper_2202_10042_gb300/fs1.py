@@ -23,7 +23,7 @@ FS1_OK, FS1_EINVAL, FS1_ENOMEM, FS1_ENUMERIC, FS1_ETIMEOUT, FS1_ENOTCONV, FS1_EC
     FS1_EUNSUPPORTED = range(8)
 STATUS_NAMES = {0: "FS1_OK", 1: "FS1_EINVAL", 2: "FS1_ENOMEM", 3: "FS1_ENUMERIC",
                 4: "FS1_ETIMEOUT", 5: "FS1_ENOTCONV", 6: "FS1_ECUDA", 7: "FS1_EUNSUPPORTED"}
-FS1_VARIANT_PLAIN, FS1_VARIANT_LOG = 0, 1
+FS1_VARIANT_PLAIN, FS1_VARIANT_LOG, FS1_VARIANT_PAPER = 0, 1, 2
 FS1_FP64, FS1_FP32 = 0, 1
 FS1_MEM_DEVICE, FS1_MEM_HOST = 0, 1
 
@@ -32,7 +32,7 @@ class fs1_config(Structure):
     _fields_ = [("variant", c_int), ("precision", c_int), ("check_every", c_int),
                 ("team_size", c_int), ("spin_cap", c_longlong), ("hbm_budget", c_size_t),
                 ("stream", c_void_p), ("autotune", c_int), ("trial_iters", c_int),
-                ("use_graph", c_int)]
+                ("use_graph", c_int), ("tau", c_double)]
 
 
 class fs1_problem(Structure):
@@ -168,14 +168,15 @@ def _check(st: int) -> None:
 # ---- convenience wrapper for torch tensors ------------------------------------
 
 class Solver:
-    """One library handle.  `variant` is "log" (stabilised, FP32) or "plain";
-    `precision` "fp32" or "fp64" (plain only)."""
+    """One library handle.  `variant` is "log" (stabilised, FP32), "plain"
+    (FP32 or FP64) or "paper" (the Remarks' tau-triggered absorption as
+    written, FP64, 1D); `precision` "fp32" or "fp64"."""
 
     def __init__(self, variant: str = "log", precision: str = "fp32", team_size: int = 0,
                  stream=None, spin_cap: int = 0, hbm_budget: int = 0, autotune: bool = True,
-                 use_graph: bool = True, trial_iters: int = 0):
+                 use_graph: bool = True, trial_iters: int = 0, tau: float = 0.0):
         cfg = fs1_config_default()
-        cfg.variant = FS1_VARIANT_LOG if variant == "log" else FS1_VARIANT_PLAIN
+        cfg.variant = {"log": FS1_VARIANT_LOG, "plain": FS1_VARIANT_PLAIN, "paper": FS1_VARIANT_PAPER}[variant]
         cfg.precision = FS1_FP32 if precision == "fp32" else FS1_FP64
         cfg.team_size = int(team_size)
         if spin_cap:
@@ -183,6 +184,8 @@ class Solver:
         cfg.hbm_budget = int(hbm_budget)
         cfg.autotune = 1 if autotune else 0
         cfg.use_graph = 1 if use_graph else 0
+        if tau:
+            cfg.tau = float(tau)
         if trial_iters:
             cfg.trial_iters = int(trial_iters)
         if stream is not None:

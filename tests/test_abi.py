@@ -50,8 +50,8 @@ int main(void) {
   printf("%zu %zu %zu\n", sizeof(fs1_config), sizeof(fs1_problem), sizeof(fs1_info));
   printf("%zu %zu %zu %zu\n", offsetof(fs1_problem, n), offsetof(fs1_problem, a),
          offsetof(fs1_problem, g_init), offsetof(fs1_info, w1));
-  printf("%zu %zu %zu %zu\n", offsetof(fs1_config, spin_cap), offsetof(fs1_config, stream),
-         offsetof(fs1_config, autotune), offsetof(fs1_config, use_graph));
+  printf("%zu %zu %zu %zu %zu\n", offsetof(fs1_config, spin_cap), offsetof(fs1_config, stream),
+         offsetof(fs1_config, autotune), offsetof(fs1_config, use_graph), offsetof(fs1_config, tau));
   return 0;
 }
 '''
@@ -74,6 +74,7 @@ int main(void) {
     assert vals[8] == fs1.fs1_config.stream.offset
     assert vals[9] == fs1.fs1_config.autotune.offset
     assert vals[10] == fs1.fs1_config.use_graph.offset
+    assert vals[11] == fs1.fs1_config.tau.offset
 
 
 def test_status_strings_and_version(lib):
@@ -84,7 +85,7 @@ def test_status_strings_and_version(lib):
     cfg = fs1.fs1_config_default()
     assert cfg.variant == fs1.FS1_VARIANT_LOG and cfg.precision == fs1.FS1_FP32
     assert cfg.check_every == 1 and cfg.spin_cap > 0 and cfg.autotune == 1 and cfg.trial_iters > 0
-    assert cfg.use_graph == 1
+    assert cfg.use_graph == 1 and cfg.tau == 1e10
 
 
 def test_missing_library_fails_loudly(tmp_path):
