@@ -45,13 +45,14 @@ def _rand2d(seed, ns, nf, floor=0.02):
     return a / a.sum(), b / b.sum()
 
 
-# c P = (h / eps) ceil(L / 32) decides the line scan of an axis: <= 40 the
-# FP32-frame scan, above it the per-point extended-range scan.  The first six
-# cases take the frame scan on both axes, (40, 64, 2e-4) the extended-range
-# scan on both, (8, 512, 2e-3) the frame scan on rows and the extended-range
-# scan on columns.
+# c = h / eps and the points per lane P decide the line scan of an axis:
+# c P <= 40 one FP32 frame per lane, else the per-point extended-range scan.
+# The first six cases take the frame scan on both axes, the others the
+# extended-range scan on both axes or on one of them, over a range of c
+# (from about 3 to 300) and line lengths up to 1024.
 @pytest.mark.parametrize("ns,nf,eps", [(7, 9, 0.1), (33, 40, 0.02), (64, 64, 0.01), (70, 100, 5e-3),
-                                       (1, 50, 0.02), (45, 1, 0.02), (40, 64, 2e-4), (8, 512, 2e-3)])
+                                       (1, 50, 0.02), (45, 1, 0.02), (40, 64, 2e-4), (8, 512, 2e-3),
+                                       (48, 48, 6.9e-4), (200, 600, 5e-4), (16, 1024, 2e-4)])
 def test_2d_against_oracle(env, ns, nf, eps):
     a2, b2 = _rand2d(ns * 1000 + nf, ns, nf)
     h = (1.0 / nf, 1.0 / ns)

@@ -51,9 +51,11 @@ def _h(shape):
 
 # c P = (h / eps) ceil(L / 32) <= 40 takes the FP32-frame line scan on an axis;
 # the last two shapes take the extended-range scan on some or all axes.
+# (6, 200, 64), 5e-4: the extended-range scan on all three axes, with 64- and
+# 200-point lines
 @pytest.mark.parametrize("shape,eps", [((4, 5, 6), 0.05), ((3, 17, 33), 0.02), ((7, 9, 40), 0.01),
                                        ((1, 8, 9), 0.05), ((12, 1, 20), 0.05), ((5, 6, 7), 1e-3),
-                                       ((6, 40, 8), 2e-3)])
+                                       ((6, 40, 8), 2e-3), ((6, 200, 64), 5e-4)])
 def test_3d_against_oracle(env, shape, eps):
     _, fs1 = env
     a, b = _rand(sum(shape) * 31 + 7, shape)
