@@ -460,16 +460,19 @@ def run_gpu(args):
     return 0
 
 
-TEAM_KERNEL_SOURCES = ("fs1_solve1d.cu", "fs1_device.cuh", "fs1_internal.h")
+TEAM_KERNEL_SOURCES = ("fs1_team.cuh", "fs1_solve1d.cu", "fs1_team_exact_*.cu", "fs1_device.cuh",
+                       "fs1_internal.h")
 
 
 def kernel_revision() -> str:
     """Hash of the sources the 1D team kernel is built from: the recorded ncu
     traffic applies while it matches."""
+    import glob
     import hashlib
     h = hashlib.sha256()
-    for f in TEAM_KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, "paper_2202_10042_gb300", "csrc", f), "rb").read())
+    for pat in TEAM_KERNEL_SOURCES:
+        for f in sorted(glob.glob(os.path.join(ROOT, "paper_2202_10042_gb300", "csrc", pat))):
+            h.update(open(f, "rb").read())
     return h.hexdigest()[:16]
 
 

@@ -205,6 +205,17 @@ const char* fs1_status_string(fs1_status s);
  * captured, size classes in the autotuner's table, autotune trial launches. */
 fs1_status fs1_handle_stats(const fs1_handle* h, int64_t* out);
 
+/* Which 1D solver kernel the handle's team launches took, written to
+ * out[0..1]: the number of launches (autotune trials included) that used an
+ * exact instantiation, and the points per thread of the most recent team
+ * launch when it used one (0 when it used the generic kernel).  A team of T
+ * CTAs gives each of its 512-thread CTAs' threads ceil(N / (512 T)) points of
+ * an N-point pair; when every pair of a launch has the same count E and an
+ * exact kernel is built for it (stabilised FP32: E = 1 .. 32; plain FP64:
+ * E = 1 .. 8), that kernel runs its per-thread loops without per-point
+ * guards.  out: host, 2 elements.  FS1_EINVAL for a NULL argument. */
+fs1_status fs1_handle_launch_stats(const fs1_handle* h, int64_t* out);
+
 /* Library version string. */
 const char* fs1_version(void);
 

@@ -56,6 +56,7 @@ struct fs1_handle {
   std::string pending;         // last signature seen but not captured yet
   bool graphs_off = false;     // capture failed once: stay eager
   int64_t replays = 0, captures = 0, trial_launches = 0;
+  int64_t exact_launches = 0, last_E = 0;   // team launches of an exact instantiation
 };
 
 namespace {
@@ -492,11 +493,27 @@ fs1_status autotune(fs1_handle* h, int kind, const std::vector<const fs1_problem
 // arguments a captured graph bakes in.  The header's contents (descriptors,
 // plan) are data copied from pinned memory on every replay.
 std::string graph_key(int kind, int mode, int in_f32, int count, int grid, int T, int teams, int nclass,
-                      size_t nslots, size_t hdr, bool validate, long long spin_cap) {
+                      size_t nslots, size_t hdr, bool validate, long long spin_cap, int exact_E) {
   char buf[192];
-  snprintf(buf, sizeof buf, "%d.%d.%d.%d.%d.%d.%d.%d.%zu.%zu.%d.%lld", kind, mode, in_f32, count, grid, T, teams,
-           nclass, nslots, hdr, (int)validate, spin_cap);
+  snprintf(buf, sizeof buf, "%d.%d.%d.%d.%d.%d.%d.%d.%zu.%zu.%d.%lld.%d", kind, mode, in_f32, count, grid, T, teams,
+           nclass, nslots, hdr, (int)validate, spin_cap, exact_E);
   return buf;
+}
+
+// The point count per thread shared by every pair of a team launch (each pair
+// of N points on a team of T CTAs gives every thread ceil(N / (512 T))
+// points), or 0 when the pairs differ; the launch then takes the exact
+// instantiation of that count when one is built.
+int common_points_per_thread(const std::vector<const fs1_problem*>& ps, const std::vector<int>& team_of) {
+  const int64_t thr = team_threads();
+  int64_t e0 = -1;
+  for (size_t i = 0; i < ps.size(); ++i) {
+    const int64_t t = team_of[i];
+    const int64_t e = (npoints(*ps[i]) + thr * t - 1) / (thr * t);
+    if (e0 >= 0 && e != e0) return 0;
+    e0 = e;
+  }
+  return e0 > 0 && e0 <= 32 ? (int)e0 : 0;
 }
 
 // Run one group (same kind and input dtype; all 1D or all 2D; device-located).
@@ -684,6 +701,8 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
       L.tickets = (unsigned long long*)(ws + o_tick);
     }
     L.spin_cap = h->cfg.spin_cap;
+    const int exact_E =
+        paper ? 0 : common_points_per_thread(ps, planned ? plan.prob_T : std::vector<int>(count, T));
     // the call's stream work, issued on s (captured when s is the capture stream)
     auto issue = [&](cudaStream_t s, bool capturing) -> fs1_status {
       cudaError_t ee;
@@ -699,7 +718,7 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
         cudaEventRecord(h->ev0, s);
       const int ls = paper ? launch_paper_1d(L.pairs, count, L.results, (double*)(ws + o_paper),
                                              (const int64_t*)(ws + o_poff), in_f32, h->cfg.tau, L.valid, s)
-                           : launch_team_1d(kind | (mode << 8), L, s);
+                           : launch_team_1d(kind | (mode << 8), L, s, exact_E);
       if (ls != FS1_OK) return (fs1_status)ls;
       if (capturing)
         cudaEventRecordWithFlags(h->ev1, s, cudaEventRecordExternal);
@@ -713,7 +732,7 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
     const bool graphs = h->cfg.use_graph && !h->graphs_off && !h->tuning;
     const std::string gkey =
         graphs ? graph_key(kind, mode, in_f32, count, planned ? pgrid : teams * T, T, teams, nclass, nslots, hdr,
-                           validate, h->cfg.spin_cap)
+                           validate, h->cfg.spin_cap, exact_E)
                : std::string();
     cudaGraphExec_t exec = nullptr;
     for (size_t k = 0; graphs && k < h->graphs.size(); ++k)
@@ -758,6 +777,10 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
     }
     g_launches.fetch_add(validate ? 2 : 1);
     if (h->tuning) h->trial_launches += 1;
+    if (!paper) {
+      h->last_E = team_exact_built(kind, exact_E) ? exact_E : 0;
+      if (h->last_E) ++h->exact_launches;
+    }
   }
   if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(e, "solve");
   if (cudaEventElapsedTime(ms, h->ev0, h->ev1) != cudaSuccess) {
@@ -867,6 +890,13 @@ fs1_status fs1_handle_stats(const fs1_handle* h, int64_t* out) {
   out[1] = h->captures;
   out[2] = (int64_t)h->tuned.size();
   out[3] = h->trial_launches;
+  return FS1_OK;
+}
+
+fs1_status fs1_handle_launch_stats(const fs1_handle* h, int64_t* out) {
+  if (!h || !out) return FS1_EINVAL;
+  out[0] = h->exact_launches;
+  out[1] = h->last_E;
   return FS1_OK;
 }
 

@@ -101,7 +101,11 @@ size_t team_smem_bytes(int kind);
 // Largest elements-per-thread the stabilised variant allows for c = h/eps.
 int elems_cap_for(int kind, double c);
 // Launch the 1D team kernel; cooperative when team_size > 1.
-int launch_team_1d(int kind, const TeamLaunch& L, void* stream);
+// exact_E > 0: every pair of the launch has that many points per thread, and
+// the exact instantiation is used when one is built for it
+int launch_team_1d(int kind, const TeamLaunch& L, void* stream, int exact_E = 0);
+// whether an exact instantiation of E points per thread is built for kind
+bool team_exact_built(int kind, int E);
 int max_coresident_ctas(int kind);
 
 }  // namespace fs1

@@ -229,7 +229,7 @@ extern "C" fs1_status fs1_w1_noalloc(const fs1_config* cfg_in, const fs1_problem
   L.counters = (unsigned long long*)(sc + kOffCtr);
   L.abort_flags = (int*)(sc + kOffAbort);
   L.spin_cap = spin_cap;
-  const int ls = launch_team_1d(kind, L, stream);
+  const int ls = launch_team_1d(kind, L, stream, (int)((n + thr * T - 1) / (thr * T)));
   if (ls != FS1_OK) return (fs1_status)ls;
   PairResult r;
   if ((e = cudaMemcpyAsync(&r, sc + kOffRes, sizeof r, cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||

@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(kT) fs1_paper_kernel(const PairDesc* pairs, Pa
     return;
   }
 
-  // Algorithm 1, line 1 (phi = psi = 1/N), or a warm start: the given log
+  // the initialisation of Algorithm 1 (phi = psi = 1/N), or a warm start: the given log
   // potentials become the absorbed A, B with phi~ = psi~ = 1
   const bool warm = P.f_init != nullptr;
   for (int64_t k = k0; k < k1; ++k) {

@@ -501,7 +501,7 @@ __global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
     L.tab[t] = c_decay(k, c, XF{});
   }
   auto tab = [&](int i, int ax) -> const XF* { return L.tab + (i * 3 + ax) * kTab; };
-  // u = v = 1 / N  (Algorithm 2, line 1), or a warm start
+  // u = v = 1 / N  (the initialisation of Algorithm 2), or a warm start
   for (int i = 0; i < nimg; ++i) {
     const Img2D& I = L.imgs[i];
     const int64_t N = (int64_t)I.nf * I.nm * I.ns;

@@ -1,0 +1,11 @@
+// Exact instantiations of the team kernel (fs1_team.cuh): stabilised FP32,
+// E = G = 5, 6, 7, 8 points per thread.
+#include "fs1_team.cuh"
+
+namespace fs1 {
+
+bool launch_team_exact_e05_08(int kind, int Eeff, const TeamLaunch& L, int mode, cudaStream_t st, cudaError_t& e) {
+  return kind == KK_LOG_F32 && launch_exact_in<float, XF, 5, 6, 7, 8>(Eeff, L, mode, st, e);
+}
+
+}  // namespace fs1

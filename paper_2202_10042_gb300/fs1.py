@@ -50,7 +50,8 @@ class fs1_info(Structure):
 
 EXPORTED = ["fs1_config_default", "fs1_create", "fs1_w1", "fs1_solve_batch",
             "fs1_kernel_apply_log", "fs1_destroy", "fs1_status_string", "fs1_version",
-            "fs1_launch_count", "fs1_w1_noalloc", "fs1_handle_stats"]
+            "fs1_launch_count", "fs1_w1_noalloc", "fs1_handle_stats",
+            "fs1_handle_launch_stats"]
 
 _lib = None
 
@@ -88,6 +89,8 @@ def load(path: str = LIB_PATH):
     L.fs1_w1_noalloc.restype = c_int
     L.fs1_handle_stats.argtypes = [c_void_p, POINTER(c_int64)]
     L.fs1_handle_stats.restype = c_int
+    L.fs1_handle_launch_stats.argtypes = [c_void_p, POINTER(c_int64)]
+    L.fs1_handle_launch_stats.restype = c_int
     _lib = L
     return L
 
@@ -147,8 +150,10 @@ def fs1_launch_count() -> int:
 def fs1_handle_stats(h) -> dict:
     out = (c_int64 * 4)()
     _check(load().fs1_handle_stats(h, out))
+    out2 = (c_int64 * 2)()
+    _check(load().fs1_handle_launch_stats(h, out2))
     return {"graph_replays": out[0], "graphs_captured": out[1], "tuned_classes": out[2],
-            "trial_launches": out[3]}
+            "trial_launches": out[3], "exact_launches": out2[0], "last_exact_E": out2[1]}
 
 
 def fs1_w1_noalloc(cfg: Optional[fs1_config], prob: fs1_problem):
