@@ -371,7 +371,11 @@ def run_gpu(args):
     teams = sorted({int(i.team_size) for i in infos})
     kernel_ms = statistics.mean(kern_ms)
     nit_step = nit / args.steps
-    graph = solver.stats()["graph_replays"] > 0
+    st_h = solver.stats()
+    graph = st_h["graph_replays"] > 0
+    # the team kernel's instantiation of the timed launches (1D): exact E, or generic
+    kernel_inst = (f"exact, {st_h['last_exact_E']} points per thread" if st_h["last_exact_E"] > 0 else "generic") \
+        if host[0].ndim == 1 and W["variant"] != "paper" else None
 
     # ---- end to end: pinned host buffers, H2D + solve + D2H each step
     barrier(world)
@@ -434,6 +438,7 @@ def run_gpu(args):
                else "L2 flushed between steps (%.0f MB write)" % (flush.numel() * 4 / 1e6),
                "team_size": teams[0] if len(teams) == 1 else teams,
                "launch": "graph replay" if graph else "direct",
+               **({"team_kernel": kernel_inst} if kernel_inst else {}),
                "iters_min": min(iters), "iters_max": max(iters), "err_median": statistics.median(errs)}
         if args.workload == 2:
             cfg.update({"n": p0.a.size, "eps": p0.eps, "tol": p0.tol, "itr_max": p0.itr_max})

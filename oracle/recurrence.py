@@ -79,6 +79,43 @@ def distance_matvec(x, lam: float):
     return np.array(A) + np.array(B)
 
 
+def _lse3(x: float, y: float, z: float) -> float:
+    """log(e^x + e^y + e^z), shifted by the largest argument."""
+    m = max(x, y, z)
+    if m == -math.inf:
+        return -math.inf
+    return m + math.log(math.exp(x - m) + math.exp(y - m) + math.exp(z - m))
+
+
+def lse_distance_matvec(g, c: float):
+    """Log-domain form of distance_matvec: with x = e^g and lam = e^{-c},
+    log(sum_j lam^{|k-j|} |k-j| x_j) for every k (-inf where the sum is 0).
+    The four recurrences of horner_matvec / distance_matvec, every quantity
+    kept as its logarithm (all of them are sums of non-negative terms):
+        P_1 = g_1,       P_{k+1} = LSE(P_k - c, g_{k+1})           (log p)
+        A_1 = -inf,      A_{k+1} = LSE(A_k, P_k) - c               (log A)
+        Q_N = -inf,      Q_k = LSE(Q_{k+1}, g_{k+1}) - c           (log q)
+        B_N = -inf,      B_k = LSE(B_{k+1}, Q_{k+1}, g_{k+1}) - c  (log B)
+    and the result is LSE(A_k, B_k).  Unlike distance_matvec it stays finite
+    for potentials g of any magnitude."""
+    n = len(g)
+    P = [0.0] * n
+    A = [0.0] * n
+    Q = [0.0] * n
+    B = [0.0] * n
+    P[0] = float(g[0])
+    A[0] = -math.inf
+    for k in range(n - 1):
+        P[k + 1] = _lse2(P[k] - c, float(g[k + 1]))
+        A[k + 1] = _lse2(A[k], P[k]) - c
+    Q[n - 1] = -math.inf
+    B[n - 1] = -math.inf
+    for k in range(n - 2, -1, -1):
+        Q[k] = _lse2(Q[k + 1], float(g[k + 1])) - c
+        B[k] = _lse3(B[k + 1], Q[k + 1], float(g[k + 1])) - c
+    return np.logaddexp(np.array(A), np.array(B))
+
+
 def transport_cost_recurrence(u, v, lam: float, h: float) -> float:
     """sum_ij u_i lam^{|i-j|} |i-j| h v_j via distance_matvec (O(N))."""
     d = distance_matvec(v, lam)

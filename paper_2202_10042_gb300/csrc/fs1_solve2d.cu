@@ -610,7 +610,19 @@ __global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
       const Img2D& I = L.imgs[i];
       float h = 0.f, l = 0.f;
       const int nt = (I.nf * I.nm + I.tw_s - 1) / I.tw_s;
-      for (int c = lane; c < nt; c += 32) df_add(h, l, __ldcg(I.errp + 2 * c), __ldcg(I.errp + 2 * c + 1));
+      // lane sums tiles lane, lane + 32, ... in that order; four loads in
+      // flight per lane (a zero pair past the end adds nothing)
+      for (int c0 = lane; c0 < nt; c0 += 128) {
+        float eh[4], el[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int c = c0 + 32 * u;
+          eh[u] = c < nt ? __ldcg(I.errp + 2 * c) : 0.f;
+          el[u] = c < nt ? __ldcg(I.errp + 2 * c + 1) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) df_add(h, l, eh[u], el[u]);
+      }
       warp_sum_df(h, l);
       if (lane == 0) {
         const double err = (double)h + (double)l;

@@ -223,6 +223,50 @@ def test_warm_start_resume_bit_identical(fs1mod, torch_cuda, team):
     assert i_res[0].marginal_err == i_full[0].marginal_err
 
 
+def test_workload2_full_length_returned_iterate(fs1mod, torch_cuda):
+    """Workload 2 pairs 0, 17 and 255 at full size (N = 2^20, eps = 1e-4), each
+    solved to its own stop (tol 1e-6, cap 5000) in the launch the benchmark
+    times (teams of 76 CTAs, the exact 27-points-per-thread kernel).  From the
+    returned log-potentials the FP64 oracle recomputes the marginal error of
+    the returned iterate (log-domain K^T u) and its transport cost (log-domain
+    distance-weighted recurrences); re-running up to 5000 iterations of the
+    oracle per pair would take minutes.  W agrees to the FP32 tolerance; the
+    error to the FP32 rounding of the terms |v (K^T u) - b| (about 6e-8 of
+    each b_j) times the recurrence gain 1 / (1 - lam) ~ 105."""
+    torch = torch_cuda
+    ps = [inputs.workload2(i) for i in (0, 17, 255)]
+    keep, probs, outs = [], [], []
+    for p in ps:
+        ta, tb = _dev(torch, p.a, torch.float32), _dev(torch, p.b, torch.float32)
+        f = torch.empty(p.a.size, dtype=torch.float64, device="cuda")
+        g = torch.empty_like(f)
+        keep += [ta, tb]
+        outs.append((f, g))
+        probs.append(fs1mod.Solver.problem(ta, tb, p.h[0], p.eps, p.tol, p.itr_max, f_out=f, g_out=g))
+    s = fs1mod.Solver("log", "fp32", autotune=False)
+    st, w, infos = s.solve(probs)
+    stats = s.stats()
+    s.close()
+    assert stats["last_exact_E"] == 27
+    for k, p in enumerate(ps):
+        i = infos[k]
+        assert i.team_size == 76
+        assert i.status in (fs1mod.FS1_OK, fs1mod.FS1_ENOTCONV)
+        f = outs[k][0].cpu().numpy()
+        g = outs[k][1].cpu().numpy()
+        assert np.all(np.isfinite(f)) and np.all(np.isfinite(g))
+        c = p.h[0] / p.eps
+        R, S = recurrence.lse_matvec(f, c)
+        err = float(np.sum(np.abs(np.exp(g + np.logaddexp(R, S)) - p.b)))
+        wc = p.h[0] * float(np.sum(np.exp(f + recurrence.lse_distance_matvec(g, c))))
+        assert _rel(w[k], wc) <= TOL32, (k, w[k], wc)
+        assert abs(i.marginal_err - err) <= 1e-5 + 0.05 * err, (k, i.marginal_err, err)
+        if i.status == fs1mod.FS1_OK:
+            assert i.iters < p.itr_max and i.marginal_err <= p.tol
+        else:
+            assert i.iters == p.itr_max and i.marginal_err > p.tol
+
+
 def test_workload2_full_size_sampled(fs1mod, torch_cuda):
     """Workload 2 at its full size (N = 2^20, eps = 1e-4) in the launch
     configuration the benchmark times, with the iteration cap cut to 100 so that

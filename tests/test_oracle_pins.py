@@ -228,6 +228,40 @@ def test_lse_recurrence():
     assert np.allclose(np.logaddexp(R, S), np.log(K @ np.exp(f)), rtol=0, atol=1e-12)
 
 
+@pytest.mark.parametrize("n", [1, 2, 45])
+def test_lse_distance_matvec_against_linear_and_brute_force(n):
+    """The log-domain distance-weighted product equals log of distance_matvec
+    and of the O(N^2) definition where e^g is representable."""
+    rng = np.random.default_rng(5 + n)
+    g = rng.normal(0, 3, n)
+    c = 0.35
+    D = np.abs(np.arange(n)[:, None] - np.arange(n)[None, :]).astype(float)
+    brute = (np.exp(-c * D) * D) @ np.exp(g)
+    got = recurrence.lse_distance_matvec(g, c)
+    lin = recurrence.distance_matvec(np.exp(g), math.exp(-c))
+    if n == 1:
+        assert got[0] == -np.inf and brute[0] == 0.0
+        return
+    assert np.allclose(got, np.log(brute), rtol=0, atol=1e-12)
+    assert np.allclose(got, np.log(lin), rtol=0, atol=1e-12)
+
+
+def test_lse_distance_matvec_large_potentials_and_zeros():
+    """Potentials of magnitude 1e4 (e^g far outside FP64) and zero entries:
+    against the O(N^2) definition taken in log space term by term,
+    log sum_j exp(g_j - c |k-j| + log |k-j|)."""
+    rng = np.random.default_rng(6)
+    n, c = 60, 2.5
+    g = np.cumsum(rng.uniform(-2 * c, 2 * c, n)) + 1e4
+    g[[4, 33]] = -np.inf
+    got = recurrence.lse_distance_matvec(g, c)
+    for k in range(n):
+        terms = [g[j] - c * abs(k - j) + math.log(abs(k - j)) for j in range(n) if j != k and g[j] > -np.inf]
+        m = max(terms)
+        ref = m + math.log(sum(math.exp(t - m) for t in terms))
+        assert abs(got[k] - ref) <= 1e-12 * abs(ref)
+
+
 def test_fs1_equals_dense_sinkhorn():
     p = inputs.workload1(3, n=128)
     h = p.h[0]
