@@ -3,7 +3,9 @@
 Tolerances (relative W1, at the GPU's reported iteration count):
   FP64 plain variant: 1e-6;  FP32 stabilised variant: 1e-4.
 """
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -230,9 +232,11 @@ def test_workload2_full_length_returned_iterate(fs1mod, torch_cuda):
     returned log-potentials the FP64 oracle recomputes the marginal error of
     the returned iterate (log-domain K^T u) and its transport cost (log-domain
     distance-weighted recurrences); re-running up to 5000 iterations of the
-    oracle per pair would take minutes.  W agrees to the FP32 tolerance; the
-    error to the FP32 rounding of the terms |v (K^T u) - b| (about 6e-8 of
-    each b_j) times the recurrence gain 1 / (1 - lam) ~ 105."""
+    oracle per pair takes about five minutes, so pairs 0 and 17, which reach
+    the cap on both sides, are compared with the oracle's W and final error
+    stored under tests/golden.  W agrees to the FP32 tolerance; the error to
+    the FP32 rounding of the terms |v (K^T u) - b| (about 6e-8 of each b_j)
+    times the recurrence gain 1 / (1 - lam) ~ 105."""
     torch = torch_cuda
     ps = [inputs.workload2(i) for i in (0, 17, 255)]
     keep, probs, outs = [], [], []
@@ -265,6 +269,15 @@ def test_workload2_full_length_returned_iterate(fs1mod, torch_cuda):
             assert i.iters < p.itr_max and i.marginal_err <= p.tol
         else:
             assert i.iters == p.itr_max and i.marginal_err > p.tol
+    # pairs 0 and 17 run to the cap on both sides: W and the final error against
+    # the FP64 oracle's, stored by tests/golden/make_workload2_oracle.py
+    with open(os.path.join(os.path.dirname(__file__), "golden", "workload2_oracle.json")) as fh:
+        gold = json.load(fh)["pairs"]
+    for k, idx in enumerate((0, 17)):
+        G = gold[str(idx)]
+        assert infos[k].iters == G["iters"] == ps[k].itr_max
+        assert _rel(w[k], G["w"]) <= TOL32, (idx, w[k], G["w"])
+        assert abs(infos[k].marginal_err - G["err"]) <= 2e-5 + 1e-2 * G["err"], (idx, infos[k].marginal_err, G["err"])
 
 
 def test_workload2_full_size_sampled(fs1mod, torch_cuda):
