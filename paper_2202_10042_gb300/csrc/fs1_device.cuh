@@ -22,7 +22,8 @@ namespace fs1 {
 
 constexpr int kZeroExp = -(1 << 28);   // exponent of the extended-range zero
 
-struct XF {
+// 8-byte aligned: one 64-bit load or store per value in shared and global memory
+struct __align__(8) XF {
   float m;  // 0 or in [0.5, 1)
   int e;
 };

@@ -123,3 +123,38 @@ def test_exact_and_generic_agree(env):
         assert i_x[k].iters == i_g[k].iters == itr
         assert abs(w_x[k] - w_g[k]) <= 1e-5 * abs(w_g[k]), (k, w_x[k], w_g[k])
     _check(pairs, np.asarray(w_x), i_x, itr, 1e10, TOL32)
+
+
+def test_graph_key_separates_point_counts(env):
+    """Two batches with the same count, team size and header size but pairs of
+    10 and of 12 points per thread: the second must not replay the graph
+    captured for the first (the exact instantiation is part of the key)."""
+    torch, fs1 = env
+    itr = 30
+    p10 = _pairs([_n_for(10, k) for k in range(3)], (0.2, 0.05, 0.01), 9500, 1e-3)
+    p12 = _pairs([_n_for(12, k) for k in range(3)], (0.2, 0.05, 0.01), 9600, 1e-3)
+
+    def probs_of(pairs):
+        keep, probs = [], []
+        for a, b, h, eps in pairs:
+            ta = torch.tensor(a, dtype=torch.float32, device="cuda")
+            tb = torch.tensor(b, dtype=torch.float32, device="cuda")
+            keep += [ta, tb]
+            probs.append(fs1.Solver.problem(ta, tb, h, eps, 0.0, itr))
+        return keep, probs
+
+    k10, q10 = probs_of(p10)
+    k12, q12 = probs_of(p12)
+    s = fs1.Solver("log", "fp32", team_size=1, autotune=False)
+    s.solve(q10)
+    s.solve(q10)                      # captured
+    _, w10, i10 = s.solve(q10)        # replayed
+    st = s.stats()
+    assert st["graphs_captured"] == 1 and st["graph_replays"] == 2 and st["last_exact_E"] == 10
+    _, w12, i12 = s.solve(q12)        # another signature: direct launch of E = 12
+    st2 = s.stats()
+    s.close()
+    assert st2["graph_replays"] == 2 and st2["last_exact_E"] == 12
+    assert all(i.status == fs1.FS1_ENOTCONV for i in i12)
+    _check(p10, w10, i10, itr, 1e10, TOL32)
+    _check(p12, w12, i12, itr, 1e10, TOL32)
