@@ -106,7 +106,12 @@ typedef struct fs1_problem {
                            index (spacing h[0]) running fastest.  3D: n[1] along the
                            middle axis, n[2] along the slow one; arrays are n[2] slabs
                            of n[1] rows of n[0].  Unused entries are ignored.  2D / 3D
-                           axes longer than 1024 give FS1_EUNSUPPORTED */
+                           axes longer than 1024 give FS1_EUNSUPPORTED.  A 1D pair is
+                           solved with its state on chip: at most (co-resident CTAs,
+                           152 on a GB300) x 512 threads x 32 points (8 for plain
+                           FP64), and in the stabilised variant at most
+                           max(1, floor(24 eps / h[0])) points per thread; a larger
+                           pair gives FS1_EUNSUPPORTED */
   double h[3];          /* grid spacings of the axes in the order of n */
   double eps;           /* entropic regularisation, > 0 */
   double tol;           /* stop when the column-marginal L1 error <= tol (>= 0) */

@@ -16,16 +16,18 @@
 //   warp   : Kogge-Stone over the 32 thread aggregates (shuffles), in plain
 //            FP32 inside one per-warp frame when the warp's values span a
 //            narrow exponent range, in extended range otherwise;
-//   CTA    : warp 0 scans the 16 warp aggregates;
-//   team   : warp 0 publishes the CTA aggregates and the error partial as
-//            epoch-tagged 64-bit words, polls the T published slots (every
-//            word validates itself, so one L2 round trip suffices) and scans
-//            them.  This is the only global synchronisation of a half-step.
+//   CTA    : every warp forms its CTA-local carry as one decay-weighted sum
+//            of the other warps' totals (no serial scan over warps);
+//   team   : warp 0 publishes the CTA totals and the error partial as
+//            epoch-tagged 64-bit words; thread j < T polls slot j (every
+//            word validates itself, so one L2 round trip suffices) and the
+//            CTA's warps reduce the slots into its team carries.  This is the
+//            only global synchronisation of a half-step.
 // The aggregates of a half-step's output are formed while the output is
 // produced.  The marginal error of the while condition of Algorithm 1 (FP32
-// terms, compensated FP32 sums inside a warp, FP64 across warps and CTAs)
-// rides on the same exchange, and every CTA takes the stop decision from the
-// same FP64 sum.
+// terms, summed as compensated FP32 pairs within warps, across warps and
+// across CTAs in a fixed order) rides on the same exchange, and every warp of
+// every CTA takes the stop decision from the same compensated sum.
 //
 // Variants (template parameters):
 //   V = double, C = double : plain FS-1 (Algorithm 1 as written), FP64.
