@@ -100,11 +100,15 @@ WORKLOADS = {
     10: dict(name="paper_form_fp64_ricker_n2000_eps5e-4_it500", pairs=100, variant="paper", precision="fp64",
              dtype="f64", bytes_per_nit=56.0, kw=dict(n=2000, eps=5e-4, itr_max=500), sample_pairs=4,
              sample_iters=500, solo=4),
+    # pairs beyond the on-chip capacity: the state in device memory
+    11: dict(name="fs1_1d_log_fp32_stream4_n2^23_eps1e-5_it500", pairs=4, variant="log", precision="fp32",
+             dtype="f32", bytes_per_nit=28.0, kw=dict(n=1 << 23, eps=1e-5, tol=1e-6, itr_max=500),
+             sample_pairs=2, sample_iters=20, solo=0),
 }
 
 GENERATORS = {1: inputs.workload1, 2: inputs.workload2, 3: inputs.workload3, 4: inputs.workload4,
               6: inputs.paper_e1, 7: inputs.paper_e2, 8: inputs.paper_e3, 9: inputs.workload9,
-              10: inputs.paper_e2}
+              10: inputs.paper_e2, 11: inputs.workload2}
 
 
 def gen_problem(workload: int, index: int, **over):
@@ -374,8 +378,14 @@ def run_gpu(args):
     st_h = solver.stats()
     graph = st_h["graph_replays"] > 0
     # the team kernel's instantiation of the timed launches (1D): exact E, or generic
-    kernel_inst = (f"exact, {st_h['last_exact_E']} points per thread" if st_h["last_exact_E"] > 0 else "generic") \
-        if host[0].ndim == 1 and W["variant"] != "paper" else None
+    kernel_inst = None
+    if host[0].ndim == 1 and W["variant"] != "paper":
+        if all(int(i.team_size) == 0 for i in infos):
+            kernel_inst = "streaming (state in device memory)"
+        elif st_h["last_exact_E"] > 0:
+            kernel_inst = f"exact, {st_h['last_exact_E']} points per thread"
+        else:
+            kernel_inst = "generic"
 
     # ---- end to end: pinned host buffers, H2D + solve + D2H each step
     barrier(world)
@@ -440,7 +450,7 @@ def run_gpu(args):
                "launch": "graph replay" if graph else "direct",
                **({"team_kernel": kernel_inst} if kernel_inst else {}),
                "iters_min": min(iters), "iters_max": max(iters), "err_median": statistics.median(errs)}
-        if args.workload == 2:
+        if args.workload in (2, 11):
             cfg.update({"n": p0.a.size, "eps": p0.eps, "tol": p0.tol, "itr_max": p0.itr_max})
         line = {"metric": METRIC, "value": value, "unit": "N*iters/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,

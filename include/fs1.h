@@ -107,11 +107,14 @@ typedef struct fs1_problem {
                            middle axis, n[2] along the slow one; arrays are n[2] slabs
                            of n[1] rows of n[0].  Unused entries are ignored.  2D / 3D
                            axes longer than 1024 give FS1_EUNSUPPORTED.  A 1D pair is
-                           solved with its state on chip: at most (co-resident CTAs,
-                           152 on a GB300) x 512 threads x 32 points (8 for plain
-                           FP64), and in the stabilised variant at most
-                           max(1, floor(24 eps / h[0])) points per thread; a larger
-                           pair gives FS1_EUNSUPPORTED */
+                           solved with its state on chip when it fits: at most
+                           (co-resident CTAs, 152 on a GB300) x 512 threads x 32
+                           points (8 for plain FP64), and in the stabilised variant
+                           at most max(1, floor(24 eps / h[0])) points per thread.
+                           A larger stabilised pair is solved with its state in
+                           device memory (fs1_info.team_size 0), after the call's
+                           other problems; a larger plain pair gives
+                           FS1_EUNSUPPORTED */
   double h[3];          /* grid spacings of the axes in the order of n */
   double eps;           /* entropic regularisation, > 0 */
   double tol;           /* stop when the column-marginal L1 error <= tol (>= 0) */

@@ -792,6 +792,69 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
   return FS1_OK;
 }
 
+// One stabilised 1D pair beyond the on-chip capacity: input check, then the
+// solve with the state in device memory (fs1_stream.cu), in the handle's
+// workspace after a 1 KB head (result | check flag | descriptor).
+fs1_status run_stream(fs1_handle* h, const fs1_problem& p, PairResult& r, float* ms) {
+  const size_t head = 1024;
+  const int64_t n = npoints(p);
+  fs1_status s;
+  if ((s = ensure_ws(h, head + stream_workspace(n))) != FS1_OK) return s;
+  if ((s = ensure_pinned(h, &h->hdr, &h->hdr_bytes, sizeof(PairDesc))) != FS1_OK) return s;
+  if ((s = ensure_pinned(h, &h->hres, &h->hres_bytes, sizeof(PairResult) + sizeof(int))) != FS1_OK) return s;
+  char* ws = (char*)h->ws;
+  PairResult* d_res = (PairResult*)ws;
+  int* d_valid = (int*)(ws + 256);
+  PairDesc* d_desc = (PairDesc*)(ws + 512);
+  PairDesc d{};
+  d.a = p.a;
+  d.b = p.b;
+  d.n = n;
+  d.n_fast = n;
+  d.n_mid = 1;
+  d.n_slow = 1;
+  d.h_fast = p.h[0];
+  d.eps = p.eps;
+  d.tol = p.tol;
+  d.itr_max = p.itr_max;
+  d.f_out = p.f_out;
+  d.g_out = p.g_out;
+  d.f_init = p.f_init;
+  d.g_init = p.g_init;
+  const int in_f32 = p.dtype == FS1_FP32;
+  memcpy(h->hdr, &d, sizeof d);
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(d_desc, h->hdr, sizeof d, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
+    return cuda_fail(e, "descriptor copy");
+  validate_kernel<<<1, 256, 0, h->stream>>>(d_desc, in_f32, d_valid);
+  g_launches.fetch_add(1);
+  int* hval = (int*)((char*)h->hres + sizeof(PairResult));
+  if ((e = cudaMemcpyAsync(hval, d_valid, sizeof(int), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
+    return cuda_fail(e, "input check");
+  if (!*hval) {
+    r = PairResult{NAN, NAN, 0, FS1_EINVAL, 0};
+    *ms = 0.f;
+    return FS1_OK;
+  }
+  cudaEventRecord(h->ev0, h->stream);
+  long long nl = 0;
+  const int ls = solve_stream_1d(d, in_f32, d_res, ws + head, h->ws_bytes - head, h->stream, &nl);
+  g_launches.fetch_add(nl);
+  if (ls != FS1_OK) return (fs1_status)ls;
+  cudaEventRecord(h->ev1, h->stream);
+  PairResult* hr = (PairResult*)h->hres;
+  if ((e = cudaMemcpyAsync(hr, d_res, sizeof(PairResult), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
+    return cuda_fail(e, "streaming solve");
+  r = *hr;
+  if (cudaEventElapsedTime(ms, h->ev0, h->ev1) != cudaSuccess) {
+    cudaGetLastError();
+    *ms = NAN;
+  }
+  return FS1_OK;
+}
+
 fs1_status worst(fs1_status a, fs1_status b) {
   auto rank = [](fs1_status s) {
     switch (s) {
@@ -967,6 +1030,24 @@ fs1_status fs1_solve_batch(fs1_handle* h, const fs1_problem* probs, int64_t coun
       s.location = FS1_MEM_DEVICE;
     }
   }
+  // 1D pairs beyond the team kernel's on-chip capacity: the stabilised
+  // variant solves them with the state in device memory, one at a time after
+  // the launches below; the plain variants report FS1_EUNSUPPORTED for them
+  std::vector<char> streamed(count, 0);
+  if (kind != KK_PAPER_F64) {
+    int maxc = -1;
+    for (int64_t i = 0; i < count; ++i) {
+      if (pst[i] != FS1_OK || staged[i].ndim != 1) continue;
+      if (maxc < 0) maxc = max_coresident_ctas(kind);
+      if (maxc <= 0) break;
+      if (min_ctas(kind, staged[i]) > std::min(maxc, kMaxTeamCtas)) {
+        if (kind == KK_LOG_F32)
+          streamed[i] = 1;
+        else
+          pst[i] = FS1_EUNSUPPORTED;
+      }
+    }
+  }
   // group by kernel (1D or grid) and input dtype (a launch reads one dtype);
   // grid groups are cut into launches of at most kMaxImg2D grids
   std::vector<std::pair<std::vector<const fs1_problem*>, std::vector<int64_t>>> groups;
@@ -975,7 +1056,7 @@ fs1_status fs1_solve_batch(fs1_handle* h, const fs1_problem* probs, int64_t coun
       std::vector<const fs1_problem*> grp;
       std::vector<int64_t> idx;
       for (int64_t i = 0; i < count; ++i)
-        if (pst[i] == FS1_OK && staged[i].dtype == dt && (staged[i].ndim >= 2 ? 2 : 1) == nd) {
+        if (pst[i] == FS1_OK && !streamed[i] && staged[i].dtype == dt && (staged[i].ndim >= 2 ? 2 : 1) == nd) {
           grp.push_back(&staged[i]);
           idx.push_back(i);
           if (nd == 2 && (int)grp.size() == kMaxImg2D) {
@@ -1003,6 +1084,20 @@ fs1_status fs1_solve_batch(fs1_handle* h, const fs1_problem* probs, int64_t coun
       team[idx[j]] = geo.team_size;
       ms[idx[j]] = gms;
     }
+  }
+  for (int64_t i = 0; i < count; ++i) {
+    if (!streamed[i]) continue;
+    PairResult r;
+    float sms = 0.f;
+    const fs1_status s = run_stream(h, staged[i], r, &sms);
+    if (s != FS1_OK) {
+      pst[i] = s;
+      continue;
+    }
+    res[i] = r;
+    pst[i] = (fs1_status)r.status;
+    team[i] = 0;
+    ms[i] = sms;
   }
   // copy host-located outputs back
   for (int64_t i = 0; i < count; ++i) {

@@ -85,6 +85,13 @@ size_t solve2d_workspace(const PairDesc* host_descs, int count);
 int launch_solve_2d(const PairDesc* host_descs, int count, int in_f32, PairResult* d_results, void* ws,
                     size_t ws_bytes, long long spin_cap, void* stream);
 
+// Stabilised 1D solver with the state in device memory (fs1_stream.cu), for
+// a pair beyond the team kernel's on-chip capacity: workspace bytes for N
+// points, and the solve (d_result: device; *launches: kernels issued).
+size_t stream_workspace(int64_t n);
+int solve_stream_1d(const PairDesc& host_desc, int in_f32, PairResult* d_result, void* ws, size_t ws_bytes,
+                    void* stream, long long* launches);
+
 // Paper-form solver (fs1_paper.cu): one CTA per pair, N <= kMaxPaperN.
 constexpr int kMaxPaperN = 16384;
 // FP64 doubles of per-pair workspace per grid point

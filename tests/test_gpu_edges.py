@@ -73,7 +73,8 @@ def test_no_iterations_and_met_tolerance(env):
 
 def test_largest_pair_on_chip_and_beyond(env):
     """152 CTAs x 512 threads x 32 points = 2490368 points is the largest pair
-    the team kernel holds on chip (small c); one team of every SM runs it."""
+    the team kernel holds on chip (small c); one team of every SM runs it.  A
+    larger pair streams through device memory."""
     torch, fs1 = env
     n = 152 * 512 * 32
     a, b = inputs.random_pair_1d(5, n, floor=0.05)
@@ -85,10 +86,19 @@ def test_largest_pair_on_chip_and_beyond(env):
     ref = cref.solve(a.astype(np.float32).astype(np.float64), b.astype(np.float32).astype(np.float64),
                      1.0 / n, eps, 0.0, 6, tau=1e10)
     assert abs(w[0] - ref.w) <= TOL32 * abs(ref.w)
+    # one CTA more than fits: the stabilised variant streams it through device
+    # memory (team size 0); the plain FP32 variant reports FS1_EUNSUPPORTED
     a2, b2 = inputs.random_pair_1d(6, n + 512 * 32, floor=0.05)
     keep2, probs2 = _problems(torch, fs1, [(a2, b2, 1.0 / a2.size, 50.0 / a2.size, 0.0, 6)], dtype=torch.float32)
     st, w, infos = s.solve(probs2)
     s.close()
+    assert infos[0].status == fs1.FS1_ENOTCONV and infos[0].team_size == 0
+    ref2 = cref.solve(a2.astype(np.float32).astype(np.float64), b2.astype(np.float32).astype(np.float64),
+                      1.0 / a2.size, 50.0 / a2.size, 0.0, 6, tau=1e10)
+    assert abs(w[0] - ref2.w) <= TOL32 * abs(ref2.w)
+    sp = fs1.Solver("plain", "fp32", autotune=False)
+    st, w, infos = sp.solve(probs2)
+    sp.close()
     assert infos[0].status == fs1.FS1_EUNSUPPORTED
 
 
