@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(kThreads, 1) stream_carry_kernel(StreamArgs A,
 
 // One half-step over the chunks (vhalf 1: y = K^T u, v_new = b / y and the
 // error of the accepted v; vhalf 0: y = K v, u = a / y).
-__global__ void __launch_bounds__(kThreads, 1) stream_half_kernel(StreamArgs A, int vhalf) {
+__global__ void __launch_bounds__(kThreads, 2) stream_half_kernel(StreamArgs A, int vhalf) {
   __shared__ DecayTables<XF> tb;
   __shared__ XchgSmem<XF> X;
   __shared__ XF sw[2 * kWarps];
