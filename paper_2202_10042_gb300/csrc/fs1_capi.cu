@@ -178,6 +178,76 @@ __global__ void validate_kernel(const PairDesc* pairs, int in_f32, int* valid) {
   }
 }
 
+// The same check for one large pair, in blocks of kCheckBlock points: each
+// block writes its compensated sums (as FP64) and a flag; one warp then sums
+// the blocks in a fixed order and applies the test of validate_kernel.
+constexpr int64_t kCheckBlock = 1 << 16;
+
+__global__ void check_range_kernel(const PairDesc* pd, int in_f32, double* part) {
+  const PairDesc P = *pd;
+  const int64_t lo = (int64_t)blockIdx.x * kCheckBlock;
+  const int64_t hi = lo + kCheckBlock < P.n ? lo + kCheckBlock : P.n;
+  float ah = 0.f, al = 0.f, bh = 0.f, bl = 0.f;
+  int bad = 0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    float a0, a1 = 0.f, b0, b1 = 0.f;
+    if (in_f32) {
+      a0 = ((const float*)P.a)[i];
+      b0 = ((const float*)P.b)[i];
+    } else {
+      const double va = ((const double*)P.a)[i], vb = ((const double*)P.b)[i];
+      if (!(va >= 0.0) || !(vb >= 0.0) || !isfinite(va) || !isfinite(vb)) bad = 1;
+      a0 = (float)va;
+      a1 = (float)(va - (double)a0);
+      b0 = (float)vb;
+      b1 = (float)(vb - (double)b0);
+    }
+    if (!(a0 >= 0.f) || !(b0 >= 0.f) || !isfinite(a0) || !isfinite(b0)) bad = 1;
+    two_sum_acc(ah, al, a0);
+    two_sum_acc(bh, bl, b0);
+    al += a1;
+    bl += b1;
+  }
+  bad = __syncthreads_or(bad);
+  __shared__ double ss[2][32];
+  double sa = (double)ah + (double)al, sb = (double)bh + (double)bl;
+  for (int o = 16; o > 0; o >>= 1) {
+    sa += __shfl_xor_sync(0xffffffffu, sa, o);
+    sb += __shfl_xor_sync(0xffffffffu, sb, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    ss[0][threadIdx.x >> 5] = sa;
+    ss[1][threadIdx.x >> 5] = sb;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ta = 0, tb = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      ta += ss[0][w];
+      tb += ss[1][w];
+    }
+    part[3 * blockIdx.x] = ta;
+    part[3 * blockIdx.x + 1] = tb;
+    part[3 * blockIdx.x + 2] = bad ? 1.0 : 0.0;
+  }
+}
+
+__global__ void check_final_kernel(const double* part, int nblk, int* valid) {
+  const int lane = threadIdx.x & 31;
+  double ta = 0, tb = 0, bad = 0;
+  for (int k = lane; k < nblk; k += 32) {
+    ta += part[3 * k];
+    tb += part[3 * k + 1];
+    bad += part[3 * k + 2];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ta += __shfl_xor_sync(0xffffffffu, ta, o);
+    tb += __shfl_xor_sync(0xffffffffu, tb, o);
+    bad += __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if (lane == 0) valid[0] = (bad == 0.0 && ta > 0.0 && tb > 0.0 && fabs(ta - tb) <= 1e-6 * fmax(ta, tb)) ? 1 : 0;
+}
+
 int kind_of(const fs1_config& c) {
   if (c.variant == FS1_VARIANT_PLAIN) return c.precision == FS1_FP64 ? KK_PLAIN_F64 : KK_PLAIN_F32;
   if (c.variant == FS1_VARIANT_PAPER) return KK_PAPER_F64;
@@ -794,10 +864,11 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
 
 // One stabilised 1D pair beyond the on-chip capacity: input check, then the
 // solve with the state in device memory (fs1_stream.cu), in the handle's
-// workspace after a 1 KB head (result | check flag | descriptor).
+// workspace after a head (result | check flag | descriptor | check partials).
 fs1_status run_stream(fs1_handle* h, const fs1_problem& p, PairResult& r, float* ms) {
-  const size_t head = 1024;
   const int64_t n = npoints(p);
+  const int nblk = (int)((n + kCheckBlock - 1) / kCheckBlock);
+  const size_t head = 1024 + align_up(sizeof(double) * 3 * (size_t)nblk, 256);
   fs1_status s;
   if ((s = ensure_ws(h, head + stream_workspace(n))) != FS1_OK) return s;
   if ((s = ensure_pinned(h, &h->hdr, &h->hdr_bytes, sizeof(PairDesc))) != FS1_OK) return s;
@@ -826,8 +897,9 @@ fs1_status run_stream(fs1_handle* h, const fs1_problem& p, PairResult& r, float*
   cudaError_t e;
   if ((e = cudaMemcpyAsync(d_desc, h->hdr, sizeof d, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
     return cuda_fail(e, "descriptor copy");
-  validate_kernel<<<1, 256, 0, h->stream>>>(d_desc, in_f32, d_valid);
-  g_launches.fetch_add(1);
+  check_range_kernel<<<nblk, 256, 0, h->stream>>>(d_desc, in_f32, (double*)(ws + 1024));
+  check_final_kernel<<<1, 32, 0, h->stream>>>((const double*)(ws + 1024), nblk, d_valid);
+  g_launches.fetch_add(2);
   int* hval = (int*)((char*)h->hres + sizeof(PairResult));
   if ((e = cudaMemcpyAsync(hval, d_valid, sizeof(int), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
       (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)

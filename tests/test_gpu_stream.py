@@ -116,3 +116,20 @@ def test_stream_warm_start_resume_bit_identical(env):
     assert i_res[0].iters == 8
     assert w_res[0] == w_full[0]
     assert i_res[0].marginal_err == i_full[0].marginal_err
+
+
+def test_stream_input_check(env):
+    """A negative mass or unequal totals in a pair that would stream is refused
+    with FS1_EINVAL by the chunked device check; a valid pair in the same call
+    is solved."""
+    torch, fs1 = env
+    a, b, h, eps = _pair(38, N_BEYOND, 0.05)
+    a_neg = a.copy()
+    a_neg[N_BEYOND - 7] = -1e-9
+    b_big = b * 1.01
+    small = _pair(39, 3000, 0.1)
+    st, w, infos = _solve(env, [(a_neg, b, h, eps), (a, b_big, h, eps), small], 5)
+    assert infos[0].status == fs1.FS1_EINVAL and infos[1].status == fs1.FS1_EINVAL
+    assert infos[2].status == fs1.FS1_ENOTCONV
+    ref = cref.solve(*small[:2], small[2], small[3], 0.0, 5, tau=1e10)
+    assert abs(w[2] - ref.w) <= TOL32 * abs(ref.w)
