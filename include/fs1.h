@@ -177,7 +177,8 @@ fs1_status fs1_solve_batch(fs1_handle* h, const fs1_problem* probs, int64_t coun
  * out_k = log sum_j exp(-|k-j| h / eps + in_j) over a 1D grid of n points
  * (the sweeps of eq. "recursion" with the stabilised arithmetic of the handle's
  * variant).  in/out: device FP64 arrays of n values (-inf allowed in `in`).
- * Exposed for testing the scan primitive on its own. */
+ * n must fit on chip as a 1D pair (see fs1_problem.n); larger n gives
+ * FS1_EUNSUPPORTED.  Exposed for testing the scan primitive on its own. */
 fs1_status fs1_kernel_apply_log(fs1_handle* h, const double* in, double* out, int64_t n,
                                 double hx, double eps);
 
