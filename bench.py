@@ -237,6 +237,15 @@ def host_cores() -> int:
 # the oracle arm (CPU)
 # ---------------------------------------------------------------------------
 
+def solve_ms(problems, infos) -> float:
+    """Solve-kernel time of one call (ms) from its per-problem infos: problems of
+    one team or grid launch share that launch's time; a 1D pair streamed through
+    device memory (team size 0) reports the time of its own solve."""
+    streamed = [float(i.ms) for p, i in zip(problems, infos) if p.ndim == 1 and int(i.team_size) == 0]
+    shared = [float(i.ms) for p, i in zip(problems, infos) if not (p.ndim == 1 and int(i.team_size) == 0)]
+    return (max(shared) if shared else 0.0) + sum(streamed)
+
+
 def oracle_sample(workload, pairs_idx, iters, workers):
     """Time the CPU FP64 oracle (sequential FS-1 in C: the plain form for the
     plain workload, the stabilised one otherwise) on a sample: the given pairs
@@ -343,12 +352,6 @@ def run_gpu(args):
     def nit_of(infos):
         return sum(int(p.a.size) * int(i.iters) for p, i in zip(host, infos))
 
-    def solve_ms(infos):
-        # problems of one team or grid launch share that launch's time; a 1D pair
-        # streamed through device memory (team size 0) reports its own solve
-        streamed = [float(i.ms) for p, i in zip(host, infos) if p.ndim == 1 and int(i.team_size) == 0]
-        shared = [float(i.ms) for p, i in zip(host, infos) if not (p.ndim == 1 and int(i.team_size) == 0)]
-        return (max(shared) if shared else 0.0) + sum(streamed)
 
     for _ in range(args.warmup):
         step(probs)
@@ -369,7 +372,7 @@ def run_gpu(args):
             w, infos = step(probs)
             e1.record(stream)
             nit += nit_of(infos)
-            kern_ms.append(solve_ms(infos))
+            kern_ms.append(solve_ms(host, infos))
         torch.cuda.synchronize()
     launches = fs1.fs1_launch_count() - l0
     barrier(world)

@@ -1,0 +1,38 @@
+"""Host-side bookkeeping of bench.py that needs no GPU."""
+import os
+import sys
+import types
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _p(ndim):
+    return types.SimpleNamespace(ndim=ndim)
+
+
+def _i(ms, team):
+    return types.SimpleNamespace(ms=ms, team_size=team)
+
+
+def test_solve_ms_shared_launch():
+    # a team launch: every pair reports the launch's time once
+    assert bench.solve_ms([_p(1)] * 3, [_i(5.0, 76), _i(5.0, 76), _i(5.0, 76)]) == 5.0
+    # a grid launch (2D and 3D report team size 0 but share one launch)
+    assert bench.solve_ms([_p(2), _p(3)], [_i(7.5, 0), _i(7.5, 0)]) == 7.5
+
+
+def test_solve_ms_streamed_pairs_add_up():
+    # 1D pairs streamed through device memory (team size 0) run one after another
+    assert bench.solve_ms([_p(1)] * 4, [_i(2.0, 0), _i(3.0, 0), _i(2.5, 0), _i(1.5, 0)]) == 9.0
+    # a mixed call: the team launch plus the streamed pair
+    assert bench.solve_ms([_p(1), _p(1), _p(1)], [_i(4.0, 8), _i(4.0, 8), _i(6.0, 0)]) == 10.0
+
+
+def test_workload_table_is_consistent():
+    for k, W in bench.WORKLOADS.items():
+        assert k in bench.GENERATORS
+        assert W["variant"] in ("log", "plain", "paper") and W["precision"] in ("fp32", "fp64")
+        assert W["bytes_per_nit"] in (28.0, 56.0)
