@@ -352,7 +352,6 @@ def run_gpu(args):
     def nit_of(infos):
         return sum(int(p.a.size) * int(i.iters) for p, i in zip(host, infos))
 
-
     for _ in range(args.warmup):
         step(probs)
 
