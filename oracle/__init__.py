@@ -20,6 +20,9 @@ Contents
               recurrences of Section 3 (eq. "recursion") and Section 4
               (eq. "2d recursion") in pure Python loops, the log-domain
               recurrences, and the O(N) transport-cost recurrence.
+  marginals   log-domain application of the (separable) Gibbs kernel and the
+              row / column marginals of a returned iterate, vectorised for
+              entry-by-entry checks of full-size workloads.
   cref        ctypes wrapper of fs1_ref.c: the same sequential recurrences in
               plain C99 FP64 (plain form and the stabilised form of the Remark
               in Section 3), in 1D, 2D and 3D, fast enough for N = 2^20 and
