@@ -76,34 +76,34 @@ L2_BYTES = 129 << 20
 # realisation also writes and reads the fast-axis partial sums, 44 B).
 WORKLOADS = {
     1: dict(name="fs1_1d_plain_fp64_n1000_eps1e-2_it1000", pairs=1, variant="plain", precision="fp64",
-            dtype="f64", bytes_per_nit=56.0, kw={}, sample_pairs=1, sample_iters=1000, solo=0),
+            dtype="f64", bytes_per_nit=56.0, kw={}, sample_iters=1000, solo=0),
     2: dict(name="fs1_1d_log_fp32_batch256_n2^20_eps1e-4", pairs=256, variant="log", precision="fp32",
             dtype="f32", bytes_per_nit=28.0, kw=dict(n=1 << 20, eps=1e-4, tol=1e-6, itr_max=5000),
-            sample_pairs=8, sample_iters=300, solo=8),
+            sample_iters=300, solo=8),
     3: dict(name="fs1_1d_log_fp32_uneven4096_n256-65536", pairs=4096, variant="log", precision="fp32",
-            dtype="f32", bytes_per_nit=28.0, kw={}, sample_pairs=64, sample_iters=200, solo=64),
+            dtype="f32", bytes_per_nit=28.0, kw={}, sample_iters=200, solo=64),
     4: dict(name="fs1_2d_log_fp32_batch64_512x512_eps1e-3", pairs=64, variant="log", precision="fp32",
-            dtype="f32", bytes_per_nit=28.0, kw={}, sample_pairs=4, sample_iters=40, solo=4),
+            dtype="f32", bytes_per_nit=28.0, kw={}, sample_iters=40, solo=4),
     # replays of the paper's Section 5 experiments; `paper` is the FS-1 rate its
     # tables imply on its CPU (grid points x iterations / printed time)
     6: dict(name="paper_e1_1d_random_n8000_eps1e-3_it1000", pairs=100, variant="log", precision="fp32",
-            dtype="f32", bytes_per_nit=28.0, kw={}, sample_pairs=4, sample_iters=1000, solo=8,
+            dtype="f32", bytes_per_nit=28.0, kw={}, sample_iters=1000, solo=8,
             paper=8000 * 1000 / 1.53e-1),
     7: dict(name="paper_e2_ricker_n8000_eps1e-2_it500", pairs=100, variant="log", precision="fp32",
-            dtype="f32", bytes_per_nit=28.0, kw={}, sample_pairs=4, sample_iters=500, solo=8,
+            dtype="f32", bytes_per_nit=28.0, kw={}, sample_iters=500, solo=8,
             paper=8000 * 500 / 5.96e-2),
     8: dict(name="paper_e3_2d_random_160x160_h1_eps1e-2_it1000", pairs=64, variant="log", precision="fp32",
-            dtype="f32", bytes_per_nit=28.0, kw={}, sample_pairs=4, sample_iters=200, solo=4,
+            dtype="f32", bytes_per_nit=28.0, kw={}, sample_iters=200, solo=4,
             paper=160 * 160 * 1000 / 1.08),
     9: dict(name="fs1_3d_log_fp32_batch32_64^3_eps2e-3", pairs=32, variant="log", precision="fp32",
-            dtype="f32", bytes_per_nit=28.0, kw={}, sample_pairs=4, sample_iters=20, solo=2),
+            dtype="f32", bytes_per_nit=28.0, kw={}, sample_iters=20, solo=2),
     10: dict(name="paper_form_fp64_ricker_n2000_eps5e-4_it500", pairs=100, variant="paper", precision="fp64",
-             dtype="f64", bytes_per_nit=56.0, kw=dict(n=2000, eps=5e-4, itr_max=500), sample_pairs=4,
+             dtype="f64", bytes_per_nit=56.0, kw=dict(n=2000, eps=5e-4, itr_max=500),
              sample_iters=500, solo=4),
     # pairs beyond the on-chip capacity: the state in device memory
     11: dict(name="fs1_1d_log_fp32_stream4_n2^23_eps1e-5_it500", pairs=4, variant="log", precision="fp32",
              dtype="f32", bytes_per_nit=28.0, kw=dict(n=1 << 23, eps=1e-5, tol=1e-6, itr_max=500),
-             sample_pairs=2, sample_iters=20, solo=0),
+             sample_iters=20, solo=0),
 }
 
 GENERATORS = {1: inputs.workload1, 2: inputs.workload2, 3: inputs.workload3, 4: inputs.workload4,
@@ -263,6 +263,13 @@ def oracle_sample(workload, pairs_idx, iters, workers):
     return nit / dt, dt, nit
 
 
+def cpu_sample_threads(W, cores: int) -> int:
+    """Host threads of the oracle sample: one pair per thread on every core the
+    process may run on (os.sched_getaffinity), at most one per pair of the
+    workload."""
+    return max(1, min(W["pairs"], cores))
+
+
 def cpu_sample_desc(W, npairs, iters, dt=None):
     what = f"{npairs} pair(s) of the workload x {iters} iterations (FP64 " + \
         ("plain" if W["variant"] == "plain" else "stabilised") + " sequential FS-1, one pair per thread, tol=0)"
@@ -275,7 +282,7 @@ def run_reference(args):
         return 0
     W = WORKLOADS[args.workload]
     cores = host_cores()
-    npairs = max(1, min(W["sample_pairs"], cores))
+    npairs = cpu_sample_threads(W, cores)
     iters = max(1, W["sample_iters"] // 4)
     for _ in range(args.warmup):
         oracle_sample(args.workload, list(range(npairs)), max(1, iters // 8), npairs)
@@ -290,7 +297,8 @@ def run_reference(args):
             "ms_per_step": 1000.0 * t_tot / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": W["name"], "pairs": W["pairs"], "parallelism": "host threads"},
-            "cpu_baseline": {"value": value, "unit": "N*iters/s", "cores": npairs, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": "N*iters/s", "cores": npairs, "host_cores": cores,
+                             "kind": "oracle",
                              "sample": cpu_sample_desc(W, npairs, iters) + " per step"},
             "e2e": {"value": value, "unit": "N*iters/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -396,10 +404,13 @@ def run_gpu(args):
         else:
             kernel_inst = "generic"
 
-    # ---- end to end: pinned host buffers, H2D + solve + D2H each step
+    # ---- end to end: pinned host buffers, H2D + solve + D2H each step, over
+    # as many steps as the device-timed region, after one untimed pass that
+    # sizes the staging buffers
+    step(probs_h)
     barrier(world)
     torch.cuda.synchronize()
-    e_steps = max(1, min(args.steps, args.e2e_steps))
+    e_steps = args.e2e_steps if args.e2e_steps > 0 else args.steps
     t0 = time.perf_counter()
     e_nit = 0
     for _ in range(e_steps):
@@ -444,9 +455,9 @@ def run_gpu(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cores = host_cores()
-        n_s = max(1, min(W["sample_pairs"], cores))
+        n_s = cpu_sample_threads(W, cores)
         v, dt, onit = oracle_sample(args.workload, list(range(n_s)), W["sample_iters"], n_s)
-        cpu = {"value": v, "unit": METRIC, "cores": n_s, "kind": "oracle",
+        cpu = {"value": v, "unit": METRIC, "cores": n_s, "host_cores": cores, "kind": "oracle",
                "sample": cpu_sample_desc(W, n_s, W["sample_iters"], dt)}
 
     if rank == 0:
@@ -471,7 +482,7 @@ def run_gpu(args):
                              "note": "achieved = %.0f B per N*iteration (streaming-equivalent bytes) "
                                      "/ solve-kernel time; the kernel keeps state on chip" % W["bytes_per_nit"]},
                 "e2e": {"value": e_val, "unit": "N*iters/s", "h2d_bytes_per_step": h2d,
-                        "d2h_bytes_per_step": d2h},
+                        "d2h_bytes_per_step": d2h, "steps": e_steps},
                 "one_pair_per_launch": solo,
                 "gpu_launches": launches,
                 "clocks": clk.summary(),
@@ -510,7 +521,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="fs1", choices=["fs1", "reference"])
     ap.add_argument("--pairs", type=int, default=0, help="override pairs per rank (testing)")
     ap.add_argument("--itr-max", type=int, default=None, help="override the cap (testing)")
-    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=0, help="end-to-end steps (0: as many as --steps)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--team-size", type=int, default=0, help="CTAs per pair (0: autotuned)")
     ap.add_argument("--no-autotune", action="store_true", help="fixed team-size heuristic")

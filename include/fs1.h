@@ -193,17 +193,21 @@ void fs1_destroy(fs1_handle* h);
  * synchronise the device).  This entry point solves ONE 1D, device-located
  * problem with the same kernel as fs1_w1 and allocates nothing, on the device
  * or the host: its device scratch (descriptor, result, exchange slots, barrier
- * counter) is a fixed file-scope __device__ array of about 81 KiB that every GPU
- * loading the library holds until exit.  No handle is needed: cfg (may be NULL
- * for the defaults) supplies the variant, precision, team size, spin cap and
- * stream.  The first call on each device, with that device current, looks up
- * the array's device address (cudaGetSymbolAddress) and caches it; make that
- * first call before any stream capture begins.  Every call reuses the array
- * (it is cleared where it must start from zero); calls that overlap on the GPU
- * race on it, so serialise them.  Problems that would need a team of more than
- * 160 CTAs are rejected with FS1_EINVAL (and a message on stderr); host-located
- * problems are rejected with FS1_EINVAL.  w1_out, info_out: host, may be NULL;
- * info_out->ms is not measured (0). */
+ * counter, input-check partials) is a fixed file-scope __device__ array of
+ * about 84 KiB that every GPU loading the library holds until exit.  No
+ * handle is needed: cfg (may be NULL for the defaults) supplies the variant,
+ * precision, team size, spin cap and stream.  Every call, with the problem's
+ * device current, looks up the array's device address (cudaGetSymbolAddress,
+ * which allocates nothing).  The call is synchronous (it synchronises
+ * cfg->stream before returning) and may not be issued on a stream that is
+ * being captured.  Every call reuses the array (it is cleared where it must
+ * start from zero); calls that overlap on the GPU race on it, so serialise
+ * them.  With the same configuration and team size the result is
+ * bit-identical to fs1_w1's.  Errors: problems that would need a team of more
+ * than 160 CTAs give FS1_EINVAL (and a message on stderr); a pair beyond the
+ * on-chip capacity (see fs1_problem.n) gives FS1_EUNSUPPORTED; host-located
+ * problems, negative or non-finite entries and unequal masses give FS1_EINVAL.
+ * w1_out, info_out: host, may be NULL; info_out->ms is not measured (0). */
 fs1_status fs1_w1_noalloc(const fs1_config* cfg, const fs1_problem* prob, double* w1_out,
                           fs1_info* info_out);
 

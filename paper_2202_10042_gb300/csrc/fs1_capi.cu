@@ -1253,3 +1253,5 @@ const char* fs1_version(void) { return kVersion; }
 int64_t fs1_launch_count(void) { return (int64_t)g_launches.load(); }
 
 }  // extern "C"
+
+void fs1::note_launches(long long k) { g_launches.fetch_add(k); }

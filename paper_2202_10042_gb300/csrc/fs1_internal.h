@@ -114,5 +114,7 @@ int launch_team_1d(int kind, const TeamLaunch& L, void* stream, int exact_E = 0)
 // whether an exact instantiation of E points per thread is built for kind
 bool team_exact_built(int kind, int E);
 int max_coresident_ctas(int kind);
+// Add k to the process-wide count of kernels this library launched.
+void note_launches(long long k);
 
 }  // namespace fs1

@@ -6,31 +6,35 @@
 // not pay for an allocation (which may synchronise the device).  For them this
 // entry point runs the same 1D team kernel as fs1_w1, but every byte of device
 // scratch it needs (the pair descriptor, the result record, the mass-check
-// record, the two sets of team exchange slots, the counter and the abort flag)
+// partials, the two sets of team exchange slots, the counter and the abort flag)
 // lives in one file-scope __device__ array of fixed size.  The caller passes
 // device-resident inputs and host outputs; nothing is allocated on the device
 // or the host.
 //
 // Notes for users
-//   - The array (kScratchBytes, about 81 KiB) is part of the library image:
+//   - The array (kScratchBytes, about 84 KiB) is part of the library image:
 //     every GPU that loads the library holds it until the process exits.
 //   - Host code may not use the array's name as a device address (on the host
-//     it names a host-side stand-in).  The first call on each device, with that
-//     device current, looks the device address up with cudaGetSymbolAddress
-//     and caches it; make that first call before any stream capture begins.
+//     it names a host-side stand-in).  Every call, with the problem's device
+//     current, looks the device address up with cudaGetSymbolAddress (which
+//     allocates nothing), so the address stays right across a device reset
+//     that reloads the library's module at another address.
+//   - The call is synchronous: it synchronises its stream twice (after the
+//     mass check and after the solve), so it may not be called on a stream
+//     that is being captured.
 //   - Every call shares the one array and finds the previous call's contents:
 //     the counter, the abort flag and the exchange slots are cleared at the
 //     start of each call.  Calls that overlap on the GPU (two host threads, or
 //     two streams) race on the array; serialise them.
 //   - Problems whose team would exceed kMaxTeam CTAs are rejected with
-//     FS1_EINVAL and a message on stderr.
+//     FS1_EINVAL and a message on stderr; pairs beyond the on-chip capacity
+//     (no co-resident team holds them) with FS1_EUNSUPPORTED.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 
 #include "fs1.h"
 #include "fs1_internal.h"
@@ -39,7 +43,6 @@ namespace fs1 {
 namespace {
 
 constexpr int kMaxTeam = 160;          // CTAs per team the static scratch can serve
-constexpr int kMaxDevices = 64;
 
 struct NaValOut {
   double sa, sb;
@@ -50,43 +53,39 @@ struct NaValOut {
 constexpr size_t al(size_t x) { return (x + 255) / 256 * 256; }
 constexpr size_t kOffDesc = 0;
 constexpr size_t kOffRes = kOffDesc + al(sizeof(PairDesc));
-constexpr size_t kOffVal = kOffRes + al(sizeof(PairResult));
-constexpr size_t kOffCtr = kOffVal + al(sizeof(NaValOut));
+constexpr size_t kOffCtr = kOffRes + al(sizeof(PairResult));
 constexpr size_t kOffAbort = kOffCtr + al(sizeof(unsigned long long));
 constexpr size_t kOffSlots = kOffAbort + al(sizeof(int));
 constexpr size_t kOffCSlots = kOffSlots + al(sizeof(Slot) * 2 * (size_t)kMaxTeam);
-constexpr size_t kScratchBytes = kOffCSlots + al(128 * 2 * (size_t)kMaxTeam);
+constexpr int kCheckBlocks = 128;      // CTAs of the mass check, one partial each
+constexpr size_t kOffVal = kOffCSlots + al(128 * 2 * (size_t)kMaxTeam);
+constexpr size_t kScratchBytes = kOffVal + al(sizeof(NaValOut) * (size_t)kCheckBlocks);
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-std::mutex g_mu;
-void* g_scratch_dev[kMaxDevices] = {nullptr};
-
-// device address of g_scratch for the current device (set up once per device)
+// device address of g_scratch on the current device.  Looked up on every call:
+// cudaGetSymbolAddress allocates nothing, and a cached address would go stale
+// if a device reset reloaded the module elsewhere.
 fs1_status scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return FS1_ECUDA;
-  if (dev < 0 || dev >= kMaxDevices) return FS1_EUNSUPPORTED;
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (g_scratch_dev[dev] == nullptr) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess || p == nullptr) {
-      fprintf(stderr, "fs1_w1_noalloc: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(e));
-      return FS1_ECUDA;
-    }
-    g_scratch_dev[dev] = p;
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+  if (e != cudaSuccess || p == nullptr) {
+    fprintf(stderr, "fs1_w1_noalloc: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(e));
+    return FS1_ECUDA;
   }
-  *out = g_scratch_dev[dev];
+  *out = p;
   return FS1_OK;
 }
 
+// Input check of the pair: CTA k sums a and b over a grid-stride share of the
+// points and flags negative or non-finite entries; its partial goes to out[k]
+// and the host adds the partials in CTA order.
 __global__ void noalloc_mass_check(const PairDesc* pd, int in_f32, NaValOut* out) {
   const PairDesc P = *pd;
   double sa = 0.0, sb = 0.0;
   int bad = 0;
-  for (int64_t i = threadIdx.x; i < P.n; i += blockDim.x) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += stride) {
     const double va = in_f32 ? (double)((const float*)P.a)[i] : ((const double*)P.a)[i];
     const double vb = in_f32 ? (double)((const float*)P.b)[i] : ((const double*)P.b)[i];
     if (!(va >= 0.0) || !(vb >= 0.0) || !isfinite(va) || !isfinite(vb)) bad = 1;
@@ -113,7 +112,7 @@ __global__ void noalloc_mass_check(const PairDesc* pd, int in_f32, NaValOut* out
       ta += ssa[w];
       tb += ssb[w];
     }
-    *out = NaValOut{ta, tb, sbad, 0};
+    out[blockIdx.x] = NaValOut{ta, tb, sbad, 0};
   }
 }
 
@@ -150,9 +149,9 @@ extern "C" fs1_status fs1_w1_noalloc(const fs1_config* cfg_in, const fs1_problem
   const int64_t n = p.n[0];
   const int64_t cap = elems_cap_for(kind, p.h[0] / p.eps);
   const int64_t tmin = (n + thr * cap - 1) / (thr * cap);
-  const int64_t tuse = std::min<int64_t>((n + thr - 1) / thr, maxc);
+  const int64_t tuse = std::min<int64_t>({(n + thr - 1) / thr, (int64_t)maxc, (int64_t)kMaxTeam});
   if (tmin > maxc) return FS1_EUNSUPPORTED;
-  int64_t T = cfg.team_size > 0 ? std::max<int64_t>(tmin, cfg.team_size) : std::max<int64_t>(tmin, tuse);
+  const int64_t T = cfg.team_size > 0 ? std::max<int64_t>(tmin, cfg.team_size) : std::max<int64_t>(tmin, tuse);
   if (T > maxc) return FS1_EINVAL;
   if (T > kMaxTeam) {
     fprintf(stderr, "fs1_w1_noalloc: the problem needs a team of %lld CTAs; the static scratch serves "
@@ -194,13 +193,23 @@ extern "C" fs1_status fs1_w1_noalloc(const fs1_config* cfg_in, const fs1_problem
     return FS1_ECUDA;
   }
   const int in_f32 = p.dtype == FS1_FP32;
-  noalloc_mass_check<<<1, 256, 0, stream>>>((const PairDesc*)(sc + kOffDesc), in_f32,
-                                            (NaValOut*)(sc + kOffVal));
-  NaValOut vo;
-  if ((e = cudaMemcpyAsync(&vo, sc + kOffVal, sizeof vo, cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
+  const int nblk = (int)std::min<int64_t>(kCheckBlocks, (n + 255) / 256);
+  noalloc_mass_check<<<nblk, 256, 0, stream>>>((const PairDesc*)(sc + kOffDesc), in_f32,
+                                               (NaValOut*)(sc + kOffVal));
+  note_launches(1);
+  NaValOut part[kCheckBlocks];
+  if ((e = cudaGetLastError()) != cudaSuccess ||
+      (e = cudaMemcpyAsync(part, sc + kOffVal, sizeof(NaValOut) * nblk, cudaMemcpyDeviceToHost, stream)) !=
+          cudaSuccess ||
       (e = cudaStreamSynchronize(stream)) != cudaSuccess) {
     fprintf(stderr, "fs1_w1_noalloc: %s\n", cudaGetErrorString(e));
     return FS1_ECUDA;
+  }
+  NaValOut vo{0.0, 0.0, 0, 0};
+  for (int k = 0; k < nblk; ++k) {
+    vo.sa += part[k].sa;
+    vo.sb += part[k].sb;
+    vo.bad |= part[k].bad;
   }
   fs1_info info;
   memset(&info, 0, sizeof info);
@@ -231,6 +240,7 @@ extern "C" fs1_status fs1_w1_noalloc(const fs1_config* cfg_in, const fs1_problem
   L.spin_cap = spin_cap;
   const int ls = launch_team_1d(kind, L, stream, (int)((n + thr * T - 1) / (thr * T)));
   if (ls != FS1_OK) return (fs1_status)ls;
+  note_launches(1);
   PairResult r;
   if ((e = cudaMemcpyAsync(&r, sc + kOffRes, sizeof r, cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
       (e = cudaStreamSynchronize(stream)) != cudaSuccess) {

@@ -36,3 +36,11 @@ def test_workload_table_is_consistent():
         assert k in bench.GENERATORS
         assert W["variant"] in ("log", "plain", "paper") and W["precision"] in ("fp32", "fp64")
         assert W["bytes_per_nit"] in (28.0, 56.0)
+
+
+def test_cpu_sample_uses_every_core():
+    # one pair per host thread on every core, never more threads than pairs
+    W2 = bench.WORKLOADS[2]
+    assert bench.cpu_sample_threads(W2, 16) == 16
+    assert bench.cpu_sample_threads(W2, 500) == W2["pairs"]
+    assert bench.cpu_sample_threads(bench.WORKLOADS[1], 16) == 1

@@ -42,3 +42,43 @@ def test_mix_equals_alone(env):
         assert abs(info.iters - r.iters) <= 1, (r.rid, info.iters, r.iters)
         assert abs(w - r.w1) <= 1e-4 * abs(w), (r.rid, w, r.w1)
     s.close()
+
+
+def test_served_results_against_oracle(env):
+    """Requests that run over several warm-started ticks (1D and 2D mixed, the
+    2D ones resuming from the FP64 potentials their previous tick wrote in
+    place) end at the oracle's result: W1 within 1e-4 relative and the
+    marginal error within 1e-3 relative of the FP64 oracle run to the served
+    iteration count, and a converged request stops within one iteration of
+    the oracle's own stop (Algorithm 1's while condition)."""
+    from oracle import cref
+    torch, fs1, serve = env
+    reqs = []
+    for i in range(12):
+        p = inputs.workload5(100 + i, arrival=0.01 * i, n_range=(2000, 200000), side_range=(48, 160),
+                             eps_range=(4e-3, 2e-2), itr_max=700)
+        reqs.append(serve.Request(i, p.a, p.b, tuple(p.h), p.eps, p.tol, p.itr_max, p.arrival))
+    srv = serve.Server(int(8e9), tick_iters=45)
+    summ = srv.run(reqs, max_seconds=300.0)
+    srv.close()
+    assert summ["completed"] == len(reqs)
+    assert any(r.a.ndim == 2 for r in reqs) and any(r.a.ndim == 1 for r in reqs)
+    assert max(r.ticks for r in reqs) >= 3           # several warm-started ticks
+
+    def f32(x):
+        return np.asarray(x, dtype=np.float32).astype(np.float64)
+
+    def hh(r):
+        return r.h if r.a.ndim == 2 else r.h[0]
+    at = cref.solve_many([(f32(r.a), f32(r.b), hh(r), r.eps, 0.0, r.iters) for r in reqs], tau=1e10)
+    own = cref.solve_many([(f32(r.a), f32(r.b), hh(r), r.eps, r.tol, r.itr_max) for r in reqs], tau=1e10)
+    for r, ra, ro in zip(reqs, at, own):
+        assert r.status in (fs1.FS1_OK, fs1.FS1_ENOTCONV), (r.rid, r.status)
+        assert ra.iters == r.iters
+        assert abs(r.w1 - ra.w) <= 1e-4 * abs(ra.w), (r.rid, r.w1, ra.w)
+        assert abs(r.err - ra.err) <= 1e-3 * ra.err + 2e-6, (r.rid, r.err, ra.err)
+        if r.status == fs1.FS1_OK:
+            assert r.err <= r.tol
+            assert abs(ro.iters - r.iters) <= 1, (r.rid, ro.iters, r.iters)
+        else:
+            assert r.iters == r.itr_max
