@@ -669,6 +669,21 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
   }
   const size_t o_2d = off;
   if (two_d) off = align_up(off + solve2d_workspace(desc.data(), count), 256);
+  // 2D images the cluster-resident kernel holds (first in `perm`), then the
+  // rest for the grid kernel
+  std::vector<int> perm;
+  int ncl = 0;
+  const size_t o_c2d = off;
+  if (two_d) {
+    for (int i = 0; i < count; ++i)
+      if (!h->cfg.grid2d && cluster2d_inst(desc[i]) >= 0) perm.push_back(i);
+    ncl = (int)perm.size();
+    for (int i = 0; i < count; ++i)
+      if (h->cfg.grid2d || cluster2d_inst(desc[i]) < 0) perm.push_back(i);
+    std::vector<PairDesc> dcl(ncl);
+    for (int k = 0; k < ncl; ++k) dcl[k] = desc[perm[k]];
+    if (ncl) off = align_up(off + cluster2d_workspace(dcl.data(), ncl), 256);
+  }
   // paper form: kPaperArrays FP64 arrays of N per pair
   std::vector<int64_t> poff(paper ? count : 0);
   const size_t o_paper = off;
@@ -734,11 +749,23 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
         return FS1_OK;
       }
     }
+    std::vector<PairDesc> dp(count);
+    for (int k = 0; k < count; ++k) dp[k] = desc[perm[k]];
+    PairResult* d_res = (PairResult*)(ws + o_res);   // in the order of perm
     cudaEventRecord(h->ev0, h->stream);
-    const int ls = launch_solve_2d(desc.data(), count, in_f32, (PairResult*)(ws + o_res), ws + o_2d,
-                                   h->ws_bytes - o_2d, h->cfg.spin_cap, h->stream);
-    if (ls != FS1_OK) return (fs1_status)ls;
-    g_launches.fetch_add(1);
+    long long nl = 0;
+    if (ncl) {
+      const int ls = launch_cluster_2d(dp.data(), ncl, in_f32, d_res, nullptr, ws + o_c2d, h->ws_bytes - o_c2d,
+                                       h->stream, &nl);
+      if (ls != FS1_OK) return (fs1_status)ls;
+    }
+    if (ncl < count) {
+      const int ls = launch_solve_2d(dp.data() + ncl, count - ncl, in_f32, d_res + ncl, ws + o_2d,
+                                     o_c2d - o_2d, h->cfg.spin_cap, h->stream);
+      if (ls != FS1_OK) return (fs1_status)ls;
+      ++nl;
+    }
+    g_launches.fetch_add(nl);
     cudaEventRecord(h->ev1, h->stream);
     if ((e = cudaMemcpyAsync(hres, ws + o_res, sizeof(PairResult) * count, cudaMemcpyDeviceToHost, h->stream)) !=
         cudaSuccess)
@@ -857,6 +884,34 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
     cudaGetLastError();
     *ms = NAN;
   }
+  if (two_d) {
+    res.assign(count, PairResult{});
+    for (int k = 0; k < count; ++k) res[perm[k]] = hres[k];
+    // an image whose scalings left the cluster kernel's exponent range is
+    // solved again by the grid kernel
+    std::vector<int> again;
+    for (int k = 0; k < ncl; ++k)
+      if (hres[k].status == FS1_EUNSUPPORTED) again.push_back(perm[k]);
+    if (!again.empty()) {
+      std::vector<PairDesc> dg(again.size());
+      for (size_t k = 0; k < again.size(); ++k) dg[k] = desc[again[k]];
+      PairResult* d_res = (PairResult*)(ws + o_res);
+      float ms2 = 0.f;
+      cudaEventRecord(h->ev0, h->stream);
+      const int ls = launch_solve_2d(dg.data(), (int)dg.size(), in_f32, d_res, ws + o_2d, o_c2d - o_2d,
+                                     h->cfg.spin_cap, h->stream);
+      if (ls != FS1_OK) return (fs1_status)ls;
+      g_launches.fetch_add(1);
+      cudaEventRecord(h->ev1, h->stream);
+      if ((e = cudaMemcpyAsync(hres, d_res, sizeof(PairResult) * dg.size(), cudaMemcpyDeviceToHost, h->stream)) !=
+              cudaSuccess ||
+          (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
+        return cuda_fail(e, "grid-kernel solve");
+      if (cudaEventElapsedTime(&ms2, h->ev0, h->ev1) == cudaSuccess) *ms += ms2;
+      for (size_t k = 0; k < again.size(); ++k) res[again[k]] = hres[k];
+    }
+    return FS1_OK;
+  }
   res.assign(hres, hres + count);
   if (planned) geo.team_size = plan.max_T;
   return FS1_OK;
@@ -956,6 +1011,8 @@ fs1_status fs1_config_default(fs1_config* cfg) {
   cfg->trial_iters = 48;
   cfg->use_graph = 1;
   cfg->tau = 1e10;
+  cfg->grid2d = 0;
+  cfg->reserved = 0;
   return FS1_OK;
 }
 
@@ -1153,7 +1210,7 @@ fs1_status fs1_solve_batch(fs1_handle* h, const fs1_problem* probs, int64_t coun
     for (size_t j = 0; j < idx.size(); ++j) {
       res[idx[j]] = r[j];
       pst[idx[j]] = (fs1_status)r[j].status;
-      team[idx[j]] = geo.team_size;
+      team[idx[j]] = r[j].pad > 0 ? r[j].pad : geo.team_size;   // a cluster-resident image: its CTAs
       ms[idx[j]] = gms;
     }
   }

@@ -29,7 +29,7 @@ struct PairResult {
   double err;     // marginal L1 error of the final iterate
   int64_t iters;  // completed iterations
   int status;     // fs1_status value
-  int pad;
+  int pad;        // CTAs of the cluster that solved a 2D image resident on chip (0 otherwise)
 };
 
 // Exchange slot of one CTA of a team (one per CTA and buffer parity): up to
@@ -84,6 +84,17 @@ constexpr int kMaxLine2D = 1024;   // longest line along any axis (staged in sha
 size_t solve2d_workspace(const PairDesc* host_descs, int count);
 int launch_solve_2d(const PairDesc* host_descs, int count, int in_f32, PairResult* d_results, void* ws,
                     size_t ws_bytes, long long spin_cap, void* stream);
+
+// Cluster-resident 2D solver (fs1_cluster2d.cu): an image in the shared
+// memory of one 16-CTA cluster.  cluster2d_inst: the instantiation that holds
+// the image (-1: none; the grid kernel solves it).  launch_cluster_2d solves
+// d[0 .. count), all with cluster2d_inst >= 0; an image whose scalings leave
+// the kernel's exponent range ends with FS1_EUNSUPPORTED (the caller solves it
+// again with the grid kernel).  *launches is incremented per kernel launch.
+int cluster2d_inst(const PairDesc& d);
+size_t cluster2d_workspace(const PairDesc* d, int count);
+int launch_cluster_2d(const PairDesc* d, int count, int in_f32, PairResult* results, const int* d_valid, void* ws,
+                      size_t ws_bytes, void* stream, long long* launches);
 
 // Stabilised 1D solver with the state in device memory (fs1_stream.cu), for
 // a pair beyond the team kernel's on-chip capacity: workspace bytes for N

@@ -4,27 +4,37 @@
 // shared memory of co-resident CTAs; a pair beyond that capacity runs here
 // with its state in device memory.  The grid is cut into chunks of 8192
 // points (one 512-thread CTA, 16 points per thread).  One half-step of
-// Algorithm 1 is three launches, with no waits between CTAs:
-//   carry : an exclusive scan over the chunks' stored (decay, value)
-//           aggregates of the half-step's input gives every chunk the forward
-//           value at the point before it and the backward value at its last
-//           point (one CTA, the team kernel's in-CTA scan over per-thread
-//           runs of chunks);
-//   half  : every chunk loads its input, forms the thread carries with the
-//           in-CTA scan of the team kernel plus its chunk carries, runs the
-//           recurrences of Section 3, eq. "recursion", divides the masses by
-//           them (the psi or phi update of Algorithm 1), stores the output
-//           with its chunk aggregates for the next half-step and (v-half) the
-//           chunk's marginal-error partial;
-//   decide: (v-half) the error partials are summed in a fixed order and the
-//           while condition of Algorithm 1 is taken on the device.
+// Algorithm 1 is ONE launch over the chunks:
+//   carries : every chunk forms its forward carry (the value at the point
+//             before it) and backward carry (at its last point) from the
+//             (decay, value) aggregates the previous launch stored for every
+//             chunk of its input: a decay-weighted sum over the other
+//             chunks, lam^{8192 d} from a table; the aggregates are complete
+//             when the launch starts, so no chunk waits for another;
+//   half    : the chunk loads its input (128-bit, coalesced), forms the thread
+//             carries with the team kernel's in-CTA scan plus its chunk
+//             carries, runs the recurrences of Section 3, eq. "recursion",
+//             divides the masses by them (the psi or phi update of
+//             Algorithm 1), stores the output with its chunk aggregates and
+//             (v-half) the chunk's marginal-error partial;
+//   last    : the last chunk to finish (a ticket counter, no waiting) takes
+//             the while condition of Algorithm 1 after a v-half (the error
+//             partials summed in FP64 in chunk order) and advances the
+//             iteration count after a u-half.
 // Every launch first reads the stop flag and returns once the loop has
-// ended, so the host issues iterations in blocks and reads the flag between
-// blocks.  Values are extended range (XF) per point; a thread's 16 points are
-// taken into one power-of-two frame when loaded, as the team kernel keeps its
-// registers.  The transport cost is formed as in the team kernel with the
-// distance-weighted operator (OpDist): chunk aggregates, a sequential scan
-// over the chunks, and the per-chunk sums of u (A + B) in FP64.
+// ended, so the host issues iterations in captured blocks and reads the flag
+// between blocks.
+//
+// State: per point an FP32 value relative to a power-of-two frame shared by
+// the 16 points of a thread (4 + 0.25 bytes per point), as the team kernel
+// holds its registers.  Within a chunk, thread t's points 4q .. 4q + 3 sit at
+// float4 index q * 512 + t, so every 128-bit access of a warp is contiguous.
+// The masses are copied once into the same order (FP32).  The transport cost
+// is formed as in the team kernel with the distance-weighted operator
+// (OpDist): chunk aggregates, a sequential scan over the chunks, and the
+// per-chunk sums of u (A + B) in FP64.
+#include <cmath>
+
 #include "fs1_team.cuh"
 
 namespace fs1 {
@@ -39,25 +49,30 @@ struct StreamState {
   int stop;        // 1 once the loop has ended
   int status;      // FS1_OK, FS1_ENOTCONV or FS1_ENUMERIC
   int par;         // v buffer holding the accepted v
-  int pad;
+  unsigned done;   // chunks of the running launch that have finished
   double err;      // marginal error of the last v-half
 };
 
 struct StreamArgs {
-  const void* a;
-  const void* b;
-  int in_f32;
   int nch;               // chunks
   int64_t n;             // points
   double c;              // h / eps
+  float lamf;            // lam = e^{-c} in FP32
   double h, tol;
   long long itr_max;
-  XF* U;                 // [nch * kChunk] each
-  XF* V[2];
+  const void* a;         // the caller's masses (natural order)
+  const void* b;
+  int in_f32;
+  float* AW;             // [nch * kChunk] masses in run order, zeros past n
+  float* BW;
+  float* U;              // [nch * kChunk] values relative to their run's frame
+  float* V[2];
+  int* FU;               // [nch * kThreads] frames of the runs
+  int* FV[2];
   XF* agg_f[3];          // chunk aggregates of U, V[0], V[1]: forward (value at the chunk's
   XF* agg_b[3];          // last point) and backward (value at the point before its first)
-  XF* car_f;             // chunk carries of the current half-step's input
-  XF* car_b;
+  XF* dec;               // [nch] lam^{kChunk d}
+  DecayTables<XF>* tabs; // the in-CTA decay tables (written once by the init kernel)
   float* errp;           // [2 nch] compensated error partials
   PairC<XF>* dagg_f;     // cost phase: distance-weighted chunk aggregates and carries
   PairC<XF>* dagg_b;
@@ -85,24 +100,39 @@ __device__ void fill_tables(DecayTables<XF>& tb, double c, int Eeff) {
   if (threadIdx.x == 0) tb.narrow = (c * 32.0 * Eeff <= 40.0) ? 1 : 0;
 }
 
-// a thread's kSE points of X (zeros past ne) in one power-of-two frame:
-// X[g0 + k] = x[k] * 2^frame, x[k] in [0, 1); returns the frame
-__device__ __forceinline__ int load_run(const XF* X, int64_t g0, int ne, float (&x)[kSE]) {
-  XF v[kSE];
-  int e = kZeroExp;
+// the 16 values of thread t's run in chunk ch (float4 index q 512 + t)
+__device__ __forceinline__ void ld_run(const float* X, int ch, int t, float (&x)[kSE]) {
+  const float4* p = reinterpret_cast<const float4*>(X + (size_t)ch * kChunk) + t;
 #pragma unroll
-  for (int k = 0; k < kSE; ++k) {
-    v[k] = k < ne ? X[g0 + k] : XF{0.f, kZeroExp};
-    e = (v[k].m != 0.f && v[k].e > e) ? v[k].e : e;
+  for (int q = 0; q < kSE / 4; ++q) {
+    const float4 v = p[q * kThreads];
+    x[4 * q] = v.x;
+    x[4 * q + 1] = v.y;
+    x[4 * q + 2] = v.z;
+    x[4 * q + 3] = v.w;
   }
+}
+__device__ __forceinline__ void st_run(float* X, int ch, int t, const float (&x)[kSE]) {
+  float4* p = reinterpret_cast<float4*>(X + (size_t)ch * kChunk) + t;
 #pragma unroll
-  for (int k = 0; k < kSE; ++k) x[k] = v[k].m != 0.f ? v[k].m * pow2f(v[k].e - e) : 0.f;
-  return e;
+  for (int q = 0; q < kSE / 4; ++q) p[q * kThreads] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+}
+// values given relative to frame F, renormalised so that the largest lies in
+// [0.5, 1); returns the run's frame (kZeroExp for an all-zero run)
+__device__ __forceinline__ int normalise_run(float (&x)[kSE], int F) {
+  int em = kZeroExp;
+#pragma unroll
+  for (int k = 0; k < kSE; ++k) em = max(em, fexp(x[k]));
+  if (em == kZeroExp) return kZeroExp;
+  const float s = pow2f(-em);
+#pragma unroll
+  for (int k = 0; k < kSE; ++k) x[k] *= s;
+  return F + em;
 }
 
 // Totals of the CTA from its threads' aggregates: forward to the CTA's last
 // point, backward to the point before its first point (every thread calls;
-// the totals are valid in warp 0).  sw: 32 XF of shared memory.
+// the totals are valid in warp 0).  sw: 32 entries of shared memory.
 template <class Op>
 __device__ void cta_totals(typename Op::T af, typename Op::T ab, const DecayTables<XF>& tb,
                            typename Op::T* sw, typename Op::T& tf, typename Op::T& tbk) {
@@ -146,152 +176,158 @@ __device__ __forceinline__ XF xf_of_log(double x) {
   const double e = floor(t);
   return xf_norm((float)exp2(t - e), (int)e);
 }
-__device__ __forceinline__ double log_of_xf(XF v) {
-  return v.m > 0.f ? log((double)v.m) + (double)v.e * 0.6931471805599453 : -INFINITY;
+__device__ __forceinline__ double log_of(float m, int F) {
+  return m > 0.f ? log((double)m) + (double)F * 0.6931471805599453 : -INFINITY;
 }
 
-// u = v = 1/N (or the warm start) and the chunk aggregates of u
-__global__ void __launch_bounds__(kThreads, 1) stream_init_kernel(StreamArgs A) {
-  __shared__ DecayTables<XF> tb;
-  __shared__ XF sw[2 * kWarps];
-  fill_tables(tb, A.c, kSE);
-  const int tid = threadIdx.x, ch = blockIdx.x;
-  const int64_t g0 = (int64_t)ch * kChunk + (int64_t)tid * kSE;
-  const int ne = (int)max((int64_t)0, min((int64_t)kSE, A.n - g0));
-  const XF init = xf_norm((float)(1.0 / (double)A.n), 0);
-#pragma unroll
-  for (int k = 0; k < kSE; ++k) {
-    XF u = XF{0.f, kZeroExp}, v = XF{0.f, kZeroExp};
-    if (k < ne) {
-      u = A.f_init ? xf_of_log(A.f_init[g0 + k]) : init;
-      v = A.g_init ? xf_of_log(A.g_init[g0 + k]) : init;
-    }
-    A.U[g0 + k] = u;
-    A.V[0][g0 + k] = v;
-  }
-  __syncthreads();
-  float x[kSE];
-  const int e = load_run(A.U, g0, ne, x);
-  const float lam = (float)exp(-A.c);
-  float af = 0.f, ab = 0.f, pw = 1.f;
+// forward (to the run's last point) and backward (from the point before its
+// first) totals of a run's values with decay lam between points
+__device__ __forceinline__ void run_aggregates(const float (&x)[kSE], float lam, float& af, float& ab) {
+  float pw = 1.f;
+  af = 0.f;
+  ab = 0.f;
 #pragma unroll
   for (int k = kSE - 1; k >= 0; --k) {
     af = af + pw * x[k];
     pw = pw * lam;
     ab = lam * (ab + x[k]);
   }
+}
+
+// masses in run order, u = v = 1/N (or the warm start), the chunk aggregates
+// of u, the chunk decay table and the loop state
+__global__ void __launch_bounds__(kThreads, 1) stream_init_kernel(StreamArgs A) {
+  __shared__ DecayTables<XF> tb;
+  __shared__ XF sw[2 * kWarps];
+  fill_tables(tb, A.c, kSE);
+  __syncthreads();
+  const int tid = threadIdx.x, ch = blockIdx.x;
+  const int64_t g0 = (int64_t)ch * kChunk + (int64_t)tid * kSE;
+  const int ne = (int)max((int64_t)0, min((int64_t)kSE, A.n - g0));
+  float am[kSE], bm[kSE];
+#pragma unroll
+  for (int k = 0; k < kSE; ++k) {
+    am[k] = k < ne ? (A.in_f32 ? ((const float*)A.a)[g0 + k] : (float)((const double*)A.a)[g0 + k]) : 0.f;
+    bm[k] = k < ne ? (A.in_f32 ? ((const float*)A.b)[g0 + k] : (float)((const double*)A.b)[g0 + k]) : 0.f;
+  }
+  st_run(A.AW, ch, tid, am);
+  st_run(A.BW, ch, tid, bm);
+  // u and v of the run, each in one frame
+  float u[kSE], v[kSE];
+  int fu = kZeroExp, fv = kZeroExp;
+  {
+    XF xu[kSE], xv[kSE];
+    const XF init = xf_norm((float)(1.0 / (double)A.n), 0);
+#pragma unroll
+    for (int k = 0; k < kSE; ++k) {
+      xu[k] = xv[k] = XF{0.f, kZeroExp};
+      if (k < ne) {
+        xu[k] = A.f_init ? xf_of_log(A.f_init[g0 + k]) : init;
+        xv[k] = A.g_init ? xf_of_log(A.g_init[g0 + k]) : init;
+      }
+      if (xu[k].m != 0.f) fu = max(fu, xu[k].e);
+      if (xv[k].m != 0.f) fv = max(fv, xv[k].e);
+    }
+#pragma unroll
+    for (int k = 0; k < kSE; ++k) {
+      u[k] = xu[k].m != 0.f ? xu[k].m * pow2f(xu[k].e - fu) : 0.f;
+      v[k] = xv[k].m != 0.f ? xv[k].m * pow2f(xv[k].e - fv) : 0.f;
+    }
+  }
+  st_run(A.U, ch, tid, u);
+  st_run(A.V[0], ch, tid, v);
+  A.FU[(size_t)ch * kThreads + tid] = fu;
+  A.FV[0][(size_t)ch * kThreads + tid] = fv;
+  float af, ab;
+  run_aggregates(u, A.lamf, af, ab);
   XF tf, tbk;
-  cta_totals<OpPlain<XF>>(c_from(af, e, XF{}), c_from(ab, e, XF{}), tb, sw, tf, tbk);
+  cta_totals<OpPlain<XF>>(c_from(af, fu, XF{}), c_from(ab, fu, XF{}), tb, sw, tf, tbk);
+  if (ch == 0 && tid == 0) *A.tabs = tb;
   if (tid == 0) {
     A.agg_f[0][ch] = tf;
     A.agg_b[0][ch] = tbk;
+    A.dec[ch] = c_decay((double)kChunk * (double)ch, A.c, XF{});
   }
-  if (ch == 0 && tid == 0) *A.st = StreamState{0, 0, FS1_OK, 0, 0, NAN};
+  if (ch == 0 && tid == 0) *A.st = StreamState{0, 0, FS1_OK, 0, 0u, NAN};
 }
 
-// Chunk carries of the half-step's input (which: 0 u, 1 the accepted v).
-// One CTA; thread t takes chunks [t P, t P + P).
-__global__ void __launch_bounds__(kThreads, 1) stream_carry_kernel(StreamArgs A, int which) {
-  __shared__ DecayTables<XF> tb;
-  __shared__ XchgSmem<XF> X;
-  __shared__ int sstop, spar;
-  const int tid = threadIdx.x;
-  if (tid == 0) {
-    sstop = A.st->stop;
-    spar = A.st->par;
-    X.ok = 1;
-  }
-  const int P = (A.nch + kThreads - 1) / kThreads;
-  const double cR = A.c * (double)kChunk;   // decay exponent of one chunk
-  fill_tables(tb, cR, P);
-  __syncthreads();
-  if (sstop) return;
-  const int src = which == 0 ? 0 : 1 + spar;
-  const XF* F = A.agg_f[src];
-  const XF* B = A.agg_b[src];
-  const XF lamR = c_decay(1.0, cR, XF{});
-  const XF zero = c_zero(XF{});
-  const int q0 = tid * P;
-  XF af = zero, ab = zero;
-  for (int j = 0; j < P; ++j) {
-    const int q = q0 + j;
-    af = c_add(c_mul(af, lamR), q < A.nch ? F[q] : zero);
-  }
-  for (int j = P - 1; j >= 0; --j) {
-    const int q = q0 + j;
-    ab = c_add(q < A.nch ? B[q] : zero, c_mul(ab, lamR));
-  }
-  TeamLaunch L{};
-  TeamCtx tc{0, 0, 1, 0, nullptr};
-  unsigned epoch = 0, xc = 0;
-  XF cf, cb;
-  int dec;
-  exchange<OpPlain<XF>, XF>(L, tc, epoch, xc, af, ab, 0.f, P, tb, X, cf, cb, 0.f, 0.f, dec, nullptr, nullptr);
-  XF fc = cf;
-  for (int j = 0; j < P; ++j) {
-    const int q = q0 + j;
-    if (q >= A.nch) break;
-    A.car_f[q] = fc;
-    fc = c_add(c_mul(fc, lamR), F[q]);
-  }
-  XF bc = cb;
-  for (int j = P - 1; j >= 0; --j) {
-    const int q = q0 + j;
-    if (q < A.nch) {
-      A.car_b[q] = bc;
-      bc = c_add(B[q], c_mul(bc, lamR));
-    } else {
-      bc = c_mul(bc, lamR);   // (never read: chunks past the end hold nothing)
-    }
-  }
+
+// the decay tables of the launch, copied from global memory
+__device__ __forceinline__ void copy_tables(DecayTables<XF>& tb, const DecayTables<XF>* g) {
+  constexpr int nw = (int)(sizeof(DecayTables<XF>) / sizeof(int));
+  static_assert(sizeof(DecayTables<XF>) % sizeof(int) == 0, "table size");
+  const int* src = reinterpret_cast<const int*>(g);
+  int* dst = reinterpret_cast<int*>(&tb);
+  for (int i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = src[i];
 }
 
 // One half-step over the chunks (vhalf 1: y = K^T u, v_new = b / y and the
 // error of the accepted v; vhalf 0: y = K v, u = a / y).
-__global__ void __launch_bounds__(kThreads, 2) stream_half_kernel(StreamArgs A, int vhalf) {
+__global__ void __launch_bounds__(kThreads, 2) stream_step_kernel(StreamArgs A, int vhalf) {
   __shared__ DecayTables<XF> tb;
   __shared__ XchgSmem<XF> X;
   __shared__ XF sw[2 * kWarps];
   __shared__ float sred[2 * kWarps];
-  __shared__ int sstop, spar;
+  __shared__ double sdred[kWarps];
+  __shared__ int sstop, spar, slast;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, ch = blockIdx.x;
   if (tid == 0) {
     sstop = A.st->stop;
     spar = A.st->par;
     X.ok = 1;
   }
-  fill_tables(tb, A.c, kSE);
+  copy_tables(tb, A.tabs);
   __syncthreads();
   if (sstop) return;
   const int par = spar;
-  const XF* Xin = vhalf ? A.U : A.V[par];
-  XF* Z = vhalf ? A.V[par ^ 1] : A.U;
+  // v-half: input u, output v[par ^ 1]; u-half: input the accepted v[par], output u
+  const float* Xin = vhalf ? A.U : A.V[par];
+  const int* Fin = vhalf ? A.FU : A.FV[par];
+  const int src = vhalf ? 0 : 1 + par;
+  float* Z = vhalf ? A.V[par ^ 1] : A.U;
+  int* FZ = vhalf ? A.FV[par ^ 1] : A.FU;
   const int zsrc = vhalf ? 1 + (par ^ 1) : 0;
-  const void* M = vhalf ? A.b : A.a;
-  const XF* Vold = A.V[par];
-  const int64_t g0 = (int64_t)ch * kChunk + (int64_t)tid * kSE;
-  const int ne = (int)max((int64_t)0, min((int64_t)kSE, A.n - g0));
-  const float lam = (float)exp(-A.c);
+  const float* M = vhalf ? A.BW : A.AW;
+  const float lam = A.lamf;
+  const size_t run = (size_t)ch * kThreads + tid;
+  const XF zero = XF{0.f, kZeroExp};
 
   float x[kSE];
-  const int e = load_run(Xin, g0, ne, x);
-  // carries of the input: in-CTA scan, then the chunk carries placed at the thread
+  ld_run(Xin, ch, tid, x);
+  const int e = Fin[run];
+  // chunk carries of the input: decay-weighted sums of the other chunks'
+  // aggregates, each thread over chunks tid, tid + 512, ..., then the CTA
+  XF CF, CB;
+  {
+    const XF* AF = A.agg_f[src];
+    const XF* AB = A.agg_b[src];
+    XF tf = zero, tk = zero;
+    for (int j = tid; j < A.nch; j += kThreads) {
+      if (j < ch) tf = c_add(tf, c_mul(AF[j], A.dec[ch - 1 - j]));
+      if (j > ch) tk = c_add(tk, c_mul(AB[j], A.dec[j - ch - 1]));
+    }
+    tf = warp_sum_c(tf);
+    tk = warp_sum_c(tk);
+    if (lane == 0) {
+      sw[warp] = tf;
+      sw[kWarps + warp] = tk;
+    }
+    __syncthreads();
+    CF = warp_sum_c(lane < kWarps ? sw[lane] : zero);
+    CB = warp_sum_c(lane < kWarps ? sw[kWarps + lane] : zero);
+    __syncthreads();   // sw is reused below
+  }
+  // thread carries: the in-CTA scan, plus the chunk carries placed at the thread
   XF cf, cb;
   {
-    float af = 0.f, ab = 0.f, pw = 1.f;
-#pragma unroll
-    for (int k = kSE - 1; k >= 0; --k) {
-      af = af + pw * x[k];
-      pw = pw * lam;
-      ab = lam * (ab + x[k]);
-    }
+    float af, ab;
+    run_aggregates(x, lam, af, ab);
     TeamLaunch L{};
     TeamCtx tc{0, 0, 1, 0, nullptr};
     unsigned epoch = 0, xc = 0;
     int dec;
     exchange<OpPlain<XF>, XF>(L, tc, epoch, xc, c_from(af, e, XF{}), c_from(ab, e, XF{}), 0.f, kSE, tb, X, cf,
-                              cb, 0.f, 0.f, dec, nullptr, nullptr);
-    const XF CF = A.car_f[ch], CB = A.car_b[ch];
+                              cb, 0.0, dec, nullptr);
     cf = c_add(cf, c_mul(CF, c_mul(tb.dt[lane], tb.dw[warp])));
     cb = c_add(cb, c_mul(CB, c_mul(tb.dt[31 - lane], tb.dw[kWarps - 1 - warp])));
   }
@@ -305,28 +341,34 @@ __global__ void __launch_bounds__(kThreads, 2) stream_half_kernel(StreamArgs A, 
     r = lam * r + x[k] * sc;
     xn[k] = r;
   }
-  float s = c_to(cb, F), af = 0.f, ab = 0.f, pw = 1.f, ep = 0.f;
+  const float4* mq = reinterpret_cast<const float4*>(M + (size_t)ch * kChunk) + tid;
+  const float4* vq = reinterpret_cast<const float4*>(A.V[par] + (size_t)ch * kChunk) + tid;
+  const int fo = vhalf ? A.FV[par][run] : 0;
+  float s = c_to(cb, F), ep = 0.f;
 #pragma unroll
-  for (int k = kSE - 1; k >= 0; --k) {
-    const float y = xn[k] + s;
-    const float m = k < ne ? load_mass<float>(M, g0 + k, A.in_f32) : 0.f;
-    const float z = k < ne ? vdiv(m, y) : 0.f;
-    if (vhalf && k < ne) {
-      const XF vo = Vold[g0 + k];
-      ep += fabsf(vo.m * y * pow2f(vo.e + F) - m);
+  for (int q = kSE / 4 - 1; q >= 0; --q) {
+    const float4 m4 = mq[q * kThreads];
+    float4 v4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (vhalf) v4 = vq[q * kThreads];
+    const float mm[4] = {m4.x, m4.y, m4.z, m4.w};
+    const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+    for (int i = 3; i >= 0; --i) {
+      const int k = 4 * q + i;
+      const float y = xn[k] + s;
+      // masses past the end are zero, so are their outputs and error terms
+      if (vhalf) ep += fabsf(c_to(c_mul(XF{vv[i], fo}, XF{y, F}), 0) - mm[i]);
+      xn[k] = vdiv(mm[i], y);
+      s = lam * (s + x[k] * sc);
     }
-    xn[k] = z;
-    af = af + pw * z;
-    pw = pw * lam;
-    ab = lam * (ab + z);
-    s = lam * (s + x[k] * sc);
   }
-  const int fz = -F;
-#pragma unroll
-  for (int k = 0; k < kSE; ++k)
-    if (k < ne) Z[g0 + k] = xf_norm(xn[k], fz);
+  const int fz = normalise_run(xn, -F);
+  st_run(Z, ch, tid, xn);
+  FZ[run] = fz;
+  float zf, zb;
+  run_aggregates(xn, lam, zf, zb);
   XF tf, tbk;
-  cta_totals<OpPlain<XF>>(c_from(af, fz, XF{}), c_from(ab, fz, XF{}), tb, sw, tf, tbk);
+  cta_totals<OpPlain<XF>>(c_from(zf, fz, XF{}), c_from(zb, fz, XF{}), tb, sw, tf, tbk);
   if (tid == 0) {
     A.agg_f[zsrc][ch] = tf;
     A.agg_b[zsrc][ch] = tbk;
@@ -338,50 +380,64 @@ __global__ void __launch_bounds__(kThreads, 2) stream_half_kernel(StreamArgs A, 
       A.errp[2 * ch] = h;
       A.errp[2 * ch + 1] = l;
     }
-  } else if (ch == 0 && tid == 0) {
-    A.st->ell += 1;   // a full iteration done (read by the next decide)
+  }
+  // the last chunk to finish takes the loop's bookkeeping
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    slast = atomicAdd(&A.st->done, 1u) == (unsigned)A.nch - 1u;
+  }
+  __syncthreads();
+  if (!slast) return;
+  __threadfence();
+  if (vhalf) {
+    // the while condition of Algorithm 1: the chunks' error pairs summed in
+    // FP64 (each thread over chunks tid, tid + 512, ..., then a fixed tree)
+    double ev = 0.0;
+    for (int j = tid; j < A.nch; j += kThreads) ev += (double)__ldcg(A.errp + 2 * j) + (double)__ldcg(A.errp + 2 * j + 1);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
+    if (lane == 0) sdred[warp] = ev;
+    __syncthreads();
+    if (tid == 0) {
+      double err = 0.0;
+      for (int w = 0; w < kWarps; ++w) err += sdred[w];
+      StreamState* st = A.st;
+      st->err = err;
+      if (!isfinite(err)) {
+        st->stop = 1;
+        st->status = FS1_ENUMERIC;
+      } else if (err <= A.tol) {
+        st->stop = 1;
+        st->status = FS1_OK;
+      } else if (st->ell >= A.itr_max) {
+        st->stop = 1;
+        st->status = FS1_ENOTCONV;
+      } else {
+        st->par = par ^ 1;   // accept v_new
+      }
+      st->done = 0u;
+    }
+  } else if (tid == 0) {
+    A.st->ell += 1;   // a full iteration done
+    A.st->done = 0u;
   }
 }
 
-// The while condition of Algorithm 1 after a v-half (one warp).
-__global__ void stream_decide_kernel(StreamArgs A) {
-  StreamState* st = A.st;
-  if (st->stop) return;
-  const int lane = threadIdx.x & 31;
-  float h = 0.f, l = 0.f;
-  for (int q = lane; q < A.nch; q += 32) df_add(h, l, A.errp[2 * q], A.errp[2 * q + 1]);
-  warp_sum_df(h, l);
-  if (lane == 0) {
-    const double err = (double)h + (double)l;
-    st->err = err;
-    if (!(isfinite(h) && isfinite(l))) {
-      st->stop = 1;
-      st->status = FS1_ENUMERIC;
-    } else if (((h - (float)A.tol) + (l - (float)(A.tol - (double)(float)A.tol))) <= 0.f) {
-      st->stop = 1;
-      st->status = FS1_OK;
-    } else if (st->ell >= A.itr_max) {
-      st->stop = 1;
-      st->status = FS1_ENOTCONV;
-    } else {
-      st->par ^= 1;   // accept v_new
-    }
-  }
-}
 
 // Cost phase 1: distance-weighted chunk aggregates of the accepted v.
 __global__ void __launch_bounds__(kThreads, 1) stream_cost_agg_kernel(StreamArgs A) {
   using DT = PairC<XF>;
   __shared__ DecayTables<XF> tb;
   __shared__ DT sw[2 * kWarps];
-  fill_tables(tb, A.c, kSE);
+  copy_tables(tb, A.tabs);
   __syncthreads();
   const int tid = threadIdx.x, ch = blockIdx.x;
-  const int64_t g0 = (int64_t)ch * kChunk + (int64_t)tid * kSE;
-  const int ne = (int)max((int64_t)0, min((int64_t)kSE, A.n - g0));
-  const float lam = (float)exp(-A.c);
+  const int par = A.st->par;
+  const float lam = A.lamf;
   float x[kSE];
-  const int e = load_run(A.V[A.st->par], g0, ne, x);
+  ld_run(A.V[par], ch, tid, x);
+  const int e = A.FV[par][(size_t)ch * kThreads + tid];
   float p = 0.f, Aa = 0.f;
 #pragma unroll
   for (int k = 0; k < kSE; ++k) {
@@ -433,14 +489,16 @@ __global__ void __launch_bounds__(kThreads, 1) stream_cost_kernel(StreamArgs A) 
   __shared__ double sred[kWarps];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, ch = blockIdx.x;
   if (tid == 0) XD.ok = 1;
-  fill_tables(tb, A.c, kSE);
+  copy_tables(tb, A.tabs);
   __syncthreads();
-  const int64_t g0 = (int64_t)ch * kChunk + (int64_t)tid * kSE;
-  const int ne = (int)max((int64_t)0, min((int64_t)kSE, A.n - g0));
-  const float lam = (float)exp(-A.c);
+  const int par = A.st->par;
+  const size_t run = (size_t)ch * kThreads + tid;
+  const float lam = A.lamf;
   float v[kSE], u[kSE];
-  const int fv = load_run(A.V[A.st->par], g0, ne, v);
-  const int fu = load_run(A.U, g0, ne, u);
+  ld_run(A.V[par], ch, tid, v);
+  ld_run(A.U, ch, tid, u);
+  const int fv = A.FV[par][run];
+  const int fu = A.FU[run];
   float p = 0.f, Aa = 0.f;
 #pragma unroll
   for (int k = 0; k < kSE; ++k) {
@@ -460,12 +518,11 @@ __global__ void __launch_bounds__(kThreads, 1) stream_cost_kernel(StreamArgs A) 
     unsigned epoch = 0, xc = 0;
     int dec;
     exchange<OpD, XF>(L, tc, epoch, xc, DT{c_from(p, fv, XF{}), c_from(Aa, fv, XF{})},
-                      DT{c_from(s, fv, XF{}), c_from(Bb, fv, XF{})}, 0.f, kSE, tb, XD, dcf, dcb, 0.f, 0.f, dec,
-                      nullptr, nullptr);
-    const int t = tid;
-    dcf = OpD::add(dcf, OpD::prop(A.dcar_f[ch], c_mul(tb.dt[lane], tb.dw[warp]), (float)(kSE * t)));
+                      DT{c_from(s, fv, XF{}), c_from(Bb, fv, XF{})}, 0.f, kSE, tb, XD, dcf, dcb, 0.0, dec,
+                      nullptr);
+    dcf = OpD::add(dcf, OpD::prop(A.dcar_f[ch], c_mul(tb.dt[lane], tb.dw[warp]), (float)(kSE * tid)));
     dcb = OpD::add(dcb, OpD::prop(A.dcar_b[ch], c_mul(tb.dt[31 - lane], tb.dw[kWarps - 1 - warp]),
-                                  (float)(kSE * (kThreads - 1 - t))));
+                                  (float)(kSE * (kThreads - 1 - tid))));
   }
   int F = max(max(c_exp(dcf.p), c_exp(dcf.a)), max(c_exp(dcb.p), c_exp(dcb.a))) + 2;
   F = max(F, fv + 12);
@@ -484,7 +541,7 @@ __global__ void __launch_bounds__(kThreads, 1) stream_cost_kernel(StreamArgs A) 
   for (int k = 0; k < kSE; ++k) {
     AA = lam * (AA + pp);
     pp = lam * pp + v[k] * sc;
-    if (k < ne) wpart += ldexp((double)u[k] * (double)(AA + BBk[k]), fu + F);
+    if (u[k] != 0.f) wpart += ldexp((double)u[k] * (double)(AA + BBk[k]), fu + F);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) wpart += __shfl_xor_sync(0xffffffffu, wpart, o);
@@ -514,8 +571,13 @@ __global__ void stream_final_kernel(StreamArgs A) {
   if (A.f_out || A.g_out) {
     const int par = A.st->par;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A.n; i += (int64_t)gridDim.x * blockDim.x) {
-      if (A.f_out) A.f_out[i] = log_of_xf(A.U[i]);
-      if (A.g_out) A.g_out[i] = log_of_xf(A.V[par][i]);
+      // point i = chunk ch, thread t, point k of the thread's run
+      const int64_t ch = i / kChunk;
+      const int r = (int)(i - ch * kChunk), t = r / kSE, k = r % kSE;
+      const size_t at = (size_t)ch * kChunk + (size_t)(k >> 2) * (4 * kThreads) + (size_t)t * 4 + (k & 3);
+      const size_t run = (size_t)ch * kThreads + t;
+      if (A.f_out) A.f_out[i] = log_of(A.U[at], A.FU[run]);
+      if (A.g_out) A.g_out[i] = log_of(A.V[par][at], A.FV[par][run]);
     }
   }
 }
@@ -527,11 +589,10 @@ size_t align256s(size_t x) { return (x + 255) / 256 * 256; }
 size_t stream_workspace(int64_t n) {
   const size_t nch = (size_t)((n + kChunk - 1) / kChunk);
   const size_t pts = nch * kChunk;
-  return 3 * align256s(sizeof(XF) * pts) + 8 * align256s(sizeof(XF) * nch) + align256s(sizeof(float) * 2 * nch) +
+  return 5 * align256s(sizeof(float) * pts) + 3 * align256s(sizeof(int) * nch * kThreads) +
+         7 * align256s(sizeof(XF) * nch) + align256s(sizeof(DecayTables<XF>)) + align256s(sizeof(float) * 2 * nch) +
          4 * align256s(sizeof(PairC<XF>) * nch) + align256s(sizeof(double) * nch) + 256 + 256;
 }
-
-int stream_launches_per_iteration() { return 5; }
 
 int solve_stream_1d(const PairDesc& P, int in_f32, PairResult* d_result, void* ws, size_t ws_bytes, void* stream,
                     long long* launches) {
@@ -542,6 +603,7 @@ int solve_stream_1d(const PairDesc& P, int in_f32, PairResult* d_result, void* w
   if (nch64 > (1 << 30)) return FS1_EUNSUPPORTED;
   const int nch = (int)nch64;
   const size_t pts = (size_t)nch * kChunk;
+  const size_t runs = (size_t)nch * kThreads;
   char* p = (char*)ws;
   StreamArgs A{};
   A.a = P.a;
@@ -550,18 +612,24 @@ int solve_stream_1d(const PairDesc& P, int in_f32, PairResult* d_result, void* w
   A.nch = nch;
   A.n = P.n;
   A.c = P.h_fast / P.eps;
+  A.lamf = (float)std::exp(-A.c);
   A.h = P.h_fast;
   A.tol = P.tol;
   A.itr_max = P.itr_max;
-  A.U = (XF*)p; p += align256s(sizeof(XF) * pts);
-  A.V[0] = (XF*)p; p += align256s(sizeof(XF) * pts);
-  A.V[1] = (XF*)p; p += align256s(sizeof(XF) * pts);
+  A.AW = (float*)p; p += align256s(sizeof(float) * pts);
+  A.BW = (float*)p; p += align256s(sizeof(float) * pts);
+  A.U = (float*)p; p += align256s(sizeof(float) * pts);
+  A.V[0] = (float*)p; p += align256s(sizeof(float) * pts);
+  A.V[1] = (float*)p; p += align256s(sizeof(float) * pts);
+  A.FU = (int*)p; p += align256s(sizeof(int) * runs);
+  A.FV[0] = (int*)p; p += align256s(sizeof(int) * runs);
+  A.FV[1] = (int*)p; p += align256s(sizeof(int) * runs);
   for (int i = 0; i < 3; ++i) {
     A.agg_f[i] = (XF*)p; p += align256s(sizeof(XF) * nch);
     A.agg_b[i] = (XF*)p; p += align256s(sizeof(XF) * nch);
   }
-  A.car_f = (XF*)p; p += align256s(sizeof(XF) * nch);
-  A.car_b = (XF*)p; p += align256s(sizeof(XF) * nch);
+  A.dec = (XF*)p; p += align256s(sizeof(XF) * nch);
+  A.tabs = (DecayTables<XF>*)p; p += align256s(sizeof(DecayTables<XF>));
   A.errp = (float*)p; p += align256s(sizeof(float) * 2 * nch);
   A.dagg_f = (PairC<XF>*)p; p += align256s(sizeof(PairC<XF>) * nch);
   A.dagg_b = (PairC<XF>*)p; p += align256s(sizeof(PairC<XF>) * nch);
@@ -579,18 +647,15 @@ int solve_stream_1d(const PairDesc& P, int in_f32, PairResult* d_result, void* w
   cudaError_t e;
   stream_init_kernel<<<nch, kThreads, 0, st>>>(A);
   ++nl;
-  // Iterations in blocks of 16, captured once as a CUDA graph (direct
-  // launches if capture is unavailable).  One block stays in flight ahead of
-  // the host: the stop flag copied after block k is read after block k + 1
-  // has been issued (launches after the stop return at once).
+  // Iterations in blocks of 16 (two launches each), captured once as a CUDA
+  // graph (direct launches if capture is unavailable).  One block stays in
+  // flight ahead of the host: the stop flag copied after block k is read
+  // after block k + 1 has been issued (launches after the stop return at once).
   const int block = 16;
   auto issue_block = [&]() {
     for (int i = 0; i < block; ++i) {
-      stream_carry_kernel<<<1, kThreads, 0, st>>>(A, 0);
-      stream_half_kernel<<<nch, kThreads, 0, st>>>(A, 1);
-      stream_decide_kernel<<<1, 32, 0, st>>>(A);
-      stream_carry_kernel<<<1, kThreads, 0, st>>>(A, 1);
-      stream_half_kernel<<<nch, kThreads, 0, st>>>(A, 0);
+      stream_step_kernel<<<nch, kThreads, 0, st>>>(A, 1);
+      stream_step_kernel<<<nch, kThreads, 0, st>>>(A, 0);
     }
   };
   cudaGraph_t graph = nullptr;
@@ -616,7 +681,7 @@ int solve_stream_1d(const PairDesc& P, int in_f32, PairResult* d_result, void* w
       cudaGraphLaunch(exec, st);
     else
       issue_block();
-    nl += 5 * block;
+    nl += 2 * block;
     cudaMemcpyAsync(h_stop + slot, &A.st->stop, sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaEventRecord(ev[slot], st);
   };

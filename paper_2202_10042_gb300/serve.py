@@ -11,7 +11,9 @@ that arrived meanwhile are admitted, first come first served, while the HBM
 budget allows, and join the next tick.  Work of all admitted requests of a
 tick runs in the same persistent launches (1D pairs of all sizes share one
 launch; 2D images share one), so new arrivals overlap with running solves
-instead of waiting for them.
+instead of waiting for them; the 1D and the 2D launches of a tick are issued
+concurrently on two CUDA streams (two library handles), with one join per
+tick.
 
 The baseline `serve_one_at_a_time` solves each request alone with one call,
 in arrival order.
@@ -99,6 +101,27 @@ def library_solver(solver):
     return solve
 
 
+def split_by_dim(solve_1d: Callable, solve_2d: Callable, pool) -> Callable:
+    """solve_fn that runs a tick's 1D and 2D requests as two concurrent calls
+    (two library handles on two CUDA streams, each call ending in its own
+    stream synchronisation), so their device work overlaps; the results come
+    back in slot order."""
+
+    def solve(slots: Sequence, iters: Sequence[int]):
+        one = [k for k, s in enumerate(slots) if s.req.a.ndim == 1]
+        two = [k for k, s in enumerate(slots) if s.req.a.ndim != 1]
+        jobs = []
+        for idx, fn in ((one, solve_1d), (two, solve_2d)):
+            if idx:
+                jobs.append((idx, pool.submit(fn, [slots[k] for k in idx], [iters[k] for k in idx])))
+        out = [None] * len(slots)
+        for idx, fut in jobs:
+            for k, r in zip(idx, fut.result()):
+                out[k] = r
+        return out
+    return solve
+
+
 class Server:
     """Admission by HBM budget, ticks of `tick_iters` iterations, retire on
     convergence or cap.  `solve_fn(slots, iters)` returns per slot
@@ -118,19 +141,28 @@ class Server:
         self.ticks = 0
         self.admitted_while_busy = 0
         self._make_slot = make_slot
+        self._solvers = []
+        self._pool = None
         if solve_fn is None:
+            import concurrent.futures as cf
             import torch
             from . import fs1
             self._torch = torch
             self._device = device
-            self._solver = fs1.Solver("log", "fp32")
-            solve_fn = library_solver(self._solver)
+            # 1D and 2D requests on their own handle and stream, solved concurrently
+            self._streams = [torch.cuda.Stream(device=device) for _ in range(2)]
+            self._solvers = [fs1.Solver("log", "fp32", stream=st.cuda_stream) for st in self._streams]
+            self._pool = cf.ThreadPoolExecutor(max_workers=2)
+            solve_fn = split_by_dim(library_solver(self._solvers[0]), library_solver(self._solvers[1]), self._pool)
         self.solve_fn = solve_fn
 
     def close(self):
-        if getattr(self, "_solver", None) is not None:
-            self._solver.close()
-            self._solver = None
+        for s in self._solvers:
+            s.close()
+        self._solvers = []
+        if self._pool is not None:
+            self._pool.shutdown()
+            self._pool = None
 
     # -- admission ---------------------------------------------------------
     def submit(self, req: Request):
@@ -159,6 +191,10 @@ class Server:
             self.active.append(slot)
             self.used += slot.bytes
             n += 1
+        if n and self._make_slot is None:
+            # the new requests' uploads (on torch's stream) complete before the
+            # solver streams read them
+            self._torch.cuda.current_stream(self._device).synchronize()
         return n
 
     # -- one tick ----------------------------------------------------------

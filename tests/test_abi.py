@@ -52,6 +52,7 @@ int main(void) {
          offsetof(fs1_problem, g_init), offsetof(fs1_info, w1));
   printf("%zu %zu %zu %zu %zu\n", offsetof(fs1_config, spin_cap), offsetof(fs1_config, stream),
          offsetof(fs1_config, autotune), offsetof(fs1_config, use_graph), offsetof(fs1_config, tau));
+  printf("%zu\n", offsetof(fs1_config, grid2d));
   return 0;
 }
 '''
@@ -75,6 +76,7 @@ int main(void) {
     assert vals[9] == fs1.fs1_config.autotune.offset
     assert vals[10] == fs1.fs1_config.use_graph.offset
     assert vals[11] == fs1.fs1_config.tau.offset
+    assert vals[12] == fs1.fs1_config.grid2d.offset
 
 
 def test_status_strings_and_version(lib):

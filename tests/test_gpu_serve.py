@@ -23,7 +23,7 @@ def test_mix_equals_alone(env):
     torch, fs1, serve = env
     reqs = []
     for i in range(14):
-        p = inputs.workload5(i, arrival=0.02 * i, n_range=(1000, 60000), side_range=(32, 96),
+        p = inputs.workload5(i, arrival=0.002 * i, n_range=(1000, 60000), side_range=(32, 96),
                              eps_range=(3e-3, 2e-2), itr_max=1200)
         reqs.append(serve.Request(i, p.a, p.b, tuple(p.h), p.eps, p.tol, p.itr_max, p.arrival))
     srv = serve.Server(int(4e9), tick_iters=150)

@@ -91,3 +91,30 @@ def test_summary_percentiles():
     s = serve.summarize(rs, 100.0)
     assert s["p50_s"] == 50.0 and s["p99_s"] == 99.0 and s["completed"] == 100
     assert math.isclose(s["nit_per_s"], 100 * 10 * 10 / 100.0)
+
+
+def test_split_by_dim_runs_both_groups_and_keeps_order():
+    """The tick's 1D and 2D requests go to their own solve functions (run
+    concurrently) and the results come back in slot order."""
+    import concurrent.futures as cf
+    import threading
+
+    seen = {}
+
+    def make(tag):
+        def solve(slots, iters):
+            seen[tag] = ([s.req.rid for s in slots], list(iters), threading.get_ident())
+            return [(float(s.req.rid), 0, it, 0.0) for s, it in zip(slots, iters)]
+        return solve
+
+    slots = []
+    for rid, nd in enumerate([1, 2, 1, 2, 2]):
+        a = np.full((4,) * nd, 1.0 / 4 ** nd)
+        slots.append(FakeSlot(serve.Request(rid, a, a.copy(), (0.25,) * nd, 0.1, 1e-6, 10)))
+    with cf.ThreadPoolExecutor(max_workers=2) as pool:
+        fn = serve.split_by_dim(make("1d"), make("2d"), pool)
+        out = fn(slots, [5, 6, 7, 8, 9])
+    assert seen["1d"][:2] == ([0, 2], [5, 7])
+    assert seen["2d"][:2] == ([1, 3, 4], [6, 8, 9])
+    assert [o[0] for o in out] == [0.0, 1.0, 2.0, 3.0, 4.0]
+    assert [o[2] for o in out] == [5, 6, 7, 8, 9]
