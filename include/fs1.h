@@ -92,9 +92,10 @@ typedef struct fs1_config {
                            graph; 0: direct launches */
   double tau;           /* absorption threshold of FS1_VARIANT_PAPER (default 1e10) */
   int grid2d;           /* 2D solver: 0 (default) keeps an image resident in the shared
-                           memory of one 16-CTA thread-block cluster when it fits (2D
-                           grids of at most 512 x 512 points); 1 always uses the grid
-                           kernel that keeps the state in device memory (also 3D) */
+                           memory of one thread-block cluster of 8 to 16 CTAs when it
+                           fits (2D grids of at most 512 x 512 points whose axes have
+                           h / eps <= 8); 1 always uses the grid kernel that keeps the
+                           state in device memory (also 3D) */
   int reserved;
 } fs1_config;
 
@@ -141,7 +142,7 @@ typedef struct fs1_info {
   int precision;
   int team_size;        /* CTAs that shared the pair: 1D on chip, the team; 1D in device
                            memory, 0; 2D resident in a cluster's shared memory, the
-                           cluster's CTAs (16); 2D / 3D on the grid kernel, 0 */
+                           cluster's CTAs (8 to 16); 2D / 3D on the grid kernel, 0 */
   int64_t iters;        /* completed Sinkhorn iterations l */
   double marginal_err;  /* || diag(v) K^T u - b ||_1 of the returned iterate (FP64) */
   double w1;            /* transport cost <P, C> of the returned iterate (FP64) */

@@ -10,19 +10,19 @@
 
 namespace fs1 {
 
-int c2d_max_clusters_p4r8();
-int c2d_max_clusters_p8r16();
-int c2d_max_clusters_p16r32();
-cudaError_t c2d_launch_p4r8(const c2d::Launch& L, int clusters, cudaStream_t st);
-cudaError_t c2d_launch_p8r16(const c2d::Launch& L, int clusters, cudaStream_t st);
-cudaError_t c2d_launch_p16r32(const c2d::Launch& L, int clusters, cudaStream_t st);
+int c2d_max_clusters_p4r8(int cs);
+int c2d_max_clusters_p8r16(int cs);
+int c2d_max_clusters_p16r32(int cs);
+cudaError_t c2d_launch_p4r8(const c2d::Launch& L, int cs, int clusters, cudaStream_t st);
+cudaError_t c2d_launch_p8r16(const c2d::Launch& L, int cs, int clusters, cudaStream_t st);
+cudaError_t c2d_launch_p16r32(const c2d::Launch& L, int cs, int clusters, cudaStream_t st);
 
 namespace {
 
 struct Inst {
   int PF, RS;
-  int (*clusters)();
-  cudaError_t (*launch)(const c2d::Launch&, int, cudaStream_t);
+  int (*clusters)(int cs);
+  cudaError_t (*launch)(const c2d::Launch&, int cs, int clusters, cudaStream_t);
 };
 // smallest first: an image takes the first instantiation that holds it
 const Inst kInst[] = {{4, 8, c2d_max_clusters_p4r8, c2d_launch_p4r8},
@@ -30,41 +30,71 @@ const Inst kInst[] = {{4, 8, c2d_max_clusters_p4r8, c2d_launch_p4r8},
                       {16, 32, c2d_max_clusters_p16r32, c2d_launch_p16r32}};
 constexpr int kNInst = 3;
 
-// co-resident clusters per instantiation on each device (queried once)
+// Per instantiation and device (queried once): how many clusters of each
+// size fit at once (the sizes that fit depend on how the SMs are grouped).
 constexpr int kMaxDev = 64;
-int g_clusters[kMaxDev][kNInst];
+constexpr int kMinCS = 8;
+int g_fit[kMaxDev][kNInst][c2d::kMaxCS + 1];
 bool g_known[kMaxDev];
 
-int clusters_of(int k) {
+int clusters_of(int k, int cs) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 0;
   if (!g_known[dev]) {
-    for (int i = 0; i < kNInst; ++i) g_clusters[dev][i] = kInst[i].clusters();
+    for (int i = 0; i < kNInst; ++i)
+      for (int c = 0; c <= c2d::kMaxCS; ++c) g_fit[dev][i][c] = c >= kMinCS ? kInst[i].clusters(c) : 0;
     g_known[dev] = true;
   }
-  return g_clusters[dev][k];
+  return g_fit[dev][k][cs];
+}
+
+// The launch shape of an image: the first instantiation whose rows hold its
+// row length, and the cluster size that puts the most SMs to work (clusters
+// that fit at once x CTAs per cluster) while every CTA's rows fit the
+// instantiation.  (k, cs) = (-1, 0) when none does.
+struct Shape {
+  int k, cs;
+};
+Shape shape_of(const PairDesc& d) {
+  for (int k = 0; k < kNInst; ++k) {
+    if (32 * kInst[k].PF < d.n_fast) continue;
+    Shape best{-1, 0};
+    int cover = 0;
+    for (int cs = c2d::kMaxCS; cs >= kMinCS; --cs) {
+      if ((d.n_slow + cs - 1) / cs > kInst[k].RS) continue;
+      const int n = clusters_of(k, cs);
+      if (n > 0 && n * cs > cover) {
+        cover = n * cs;
+        best = Shape{k, cs};
+      }
+    }
+    if (best.k >= 0) return best;
+  }
+  return Shape{-1, 0};
 }
 
 size_t al(size_t x) { return (x + 255) / 256 * 256; }
 
 size_t slots(const PairDesc& d, int k) { return (size_t)d.n_slow * 32 * kInst[k].PF; }
+// frames of the saved u: [cluster size][RS / kSub][SW]
+size_t frames(Shape sh) { return (size_t)sh.cs * (kInst[sh.k].RS / c2d::kSub) * 32 * kInst[sh.k].PF; }
 
 }  // namespace
 
 int cluster2d_inst(const PairDesc& d) {
   if (d.n_mid != 1 || d.n_fast < 1 || d.n_slow < 1) return -1;
-  const int64_t R = (d.n_slow + c2d::kCS - 1) / c2d::kCS;
-  for (int k = 0; k < kNInst; ++k)
-    if (32 * kInst[k].PF >= d.n_fast && kInst[k].RS >= R) return clusters_of(k) > 0 ? k : -1;
-  return -1;
+  // FP32-frame sweeps on both axes (larger c: the grid kernel); an axis of
+  // one point has no recurrence, so its c does not matter
+  if (d.n_fast > 1 && !(d.h_fast / d.eps <= c2d::kFrameC)) return -1;
+  if (d.n_slow > 1 && !(d.h_slow / d.eps <= c2d::kFrameC)) return -1;
+  return shape_of(d).k;
 }
 
 size_t cluster2d_workspace(const PairDesc* d, int count) {
-  size_t b = al(sizeof(c2d::Img) * count) + al(sizeof(int) * count) + al(sizeof(int) * kNInst);
+  size_t b = al(sizeof(c2d::Img) * count) + al(sizeof(int) * count) + al(sizeof(int) * kNInst * (c2d::kMaxCS + 1));
   for (int i = 0; i < count; ++i) {
     const int k = cluster2d_inst(d[i]);
-    if (k >= 0) b += 2 * al(sizeof(float) * slots(d[i], k)) + al(sizeof(float) * slots(d[i], k)) +
-                     al(sizeof(short) * slots(d[i], k));
+    if (k >= 0) b += 3 * al(sizeof(float) * slots(d[i], k)) + al(sizeof(int) * frames(shape_of(d[i])));
   }
   return b;
 }
@@ -82,24 +112,23 @@ int launch_cluster_2d(const PairDesc* d, int count, int in_f32, PairResult* resu
   int* d_order = (int*)p;
   p += al(sizeof(int) * count);
   int* d_next = (int*)p;
-  p += al(sizeof(int) * kNInst);
+  p += al(sizeof(int) * kNInst * (c2d::kMaxCS + 1));
   std::vector<c2d::Img> imgs(count);
-  std::vector<int> inst(count);
+  std::vector<int> group(count);   // k (kMaxCS + 1) + cs
   for (int i = 0; i < count; ++i) {
     const PairDesc& D = d[i];
-    const int k = cluster2d_inst(D);
-    if (k < 0) return FS1_EINVAL;
-    inst[i] = k;
+    if (cluster2d_inst(D) < 0) return FS1_EINVAL;
+    const Shape sh = shape_of(D);
+    const int k = sh.k;
+    group[i] = k * (c2d::kMaxCS + 1) + sh.cs;
     c2d::Img I{};
     I.a = D.a;
     I.b = D.b;
     I.nf = (int)D.n_fast;
     I.ns = (int)D.n_slow;
-    I.R = (int)((D.n_slow + c2d::kCS - 1) / c2d::kCS);
+    I.R = (int)((D.n_slow + sh.cs - 1) / sh.cs);
     I.cf = D.h_fast / D.eps;
     I.cs = D.h_slow / D.eps;
-    I.frame_f = I.cf <= c2d::kFrameC ? 1 : 0;
-    I.frame_s = I.cs <= c2d::kFrameC ? 1 : 0;
     I.hf = D.h_fast;
     I.hs = D.h_slow;
     I.tol = D.tol;
@@ -111,32 +140,34 @@ int launch_cluster_2d(const PairDesc* d, int count, int in_f32, PairResult* resu
     const size_t n = slots(D, k);
     I.aw = (float*)p; p += al(sizeof(float) * n);
     I.bw = (float*)p; p += al(sizeof(float) * n);
-    I.usm = (float*)p; p += al(sizeof(float) * n);
-    I.use = (short*)p; p += al(sizeof(short) * n);
+    I.us = (float*)p; p += al(sizeof(float) * n);
+    I.usf = (int*)p; p += al(sizeof(int) * frames(sh));
     imgs[i] = I;
   }
-  // one queue per instantiation, longest (points x cap) first
+  // one queue per (instantiation, cluster size), longest (points x cap) first
+  const int ng = kNInst * (c2d::kMaxCS + 1);
   std::vector<int> order;
-  std::vector<int> first(kNInst + 1, 0);
-  for (int k = 0; k < kNInst; ++k) {
-    first[k] = (int)order.size();
+  std::vector<int> first(ng + 1, 0);
+  for (int g = 0; g < ng; ++g) {
+    first[g] = (int)order.size();
     std::vector<int> mine;
     for (int i = 0; i < count; ++i)
-      if (inst[i] == k) mine.push_back(i);
+      if (group[i] == g) mine.push_back(i);
     std::stable_sort(mine.begin(), mine.end(), [&](int x, int y) {
       return (double)d[x].n * (double)d[x].itr_max > (double)d[y].n * (double)d[y].itr_max;
     });
     order.insert(order.end(), mine.begin(), mine.end());
   }
-  first[kNInst] = (int)order.size();
+  first[ng] = (int)order.size();
   cudaError_t e = cudaMemcpyAsync(d_imgs, imgs.data(), sizeof(c2d::Img) * count, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_order, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d_next, 0, sizeof(int) * kNInst, st);
-  for (int k = 0; k < kNInst && e == cudaSuccess; ++k) {
-    const int n = first[k + 1] - first[k];
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_next, 0, sizeof(int) * ng, st);
+  for (int g = 0; g < ng && e == cudaSuccess; ++g) {
+    const int n = first[g + 1] - first[g];
     if (n == 0) continue;
-    c2d::Launch L{d_imgs, results, d_order + first[k], n, in_f32, d_valid, d_next + k};
-    e = kInst[k].launch(L, std::min(n, clusters_of(k)), st);
+    const int k = g / (c2d::kMaxCS + 1), cs = g % (c2d::kMaxCS + 1);
+    c2d::Launch L{d_imgs, results, d_order + first[g], n, in_f32, d_valid, d_next + g};
+    e = kInst[k].launch(L, cs, std::min(n, clusters_of(k, cs)), st);
     if (launches) ++*launches;
   }
   if (e != cudaSuccess) {

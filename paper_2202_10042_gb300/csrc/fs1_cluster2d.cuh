@@ -3,9 +3,10 @@
 //
 // K = K_slow (x) K_fast (Section 4, block form) is applied as a pass of the 1D
 // recurrences of eq. "recursion" along every row and a pass along every
-// column ("2d recursion").  One cluster of kCS CTAs owns one image at a time
-// and keeps its scalings u, v in shared memory for the whole solve: CTA k of
-// the cluster holds the rows [k R, k R + R) (R = ceil(n_slow / kCS)).
+// column ("2d recursion").  One cluster of S CTAs (the launch's cluster size)
+// owns one image at a time and keeps its scalings u, v in shared memory for
+// the whole solve: CTA k of the cluster holds the rows [k R, k R + R),
+// R = ceil(n_slow / S).
 //   row pass    : rows are local to a CTA; a warp scans a row, each lane a
 //                 chunk of PF points, lanes joined by a Kogge-Stone scan of the
 //                 (decay, value) chunk aggregates;
@@ -16,15 +17,17 @@
 //                 through distributed shared memory (Horner over CTAs with
 //                 lam^R).  HBM is read only for a and b (their working set
 //                 stays in L2) and written once per solve.
-// Storage per point and scaling: an FP32 mantissa in [0.5, 1) and a 16-bit
-// power-of-two exponent (6 bytes), so the scalings keep FP32 relative
-// precision at any magnitude 2^+-32000 (the log-domain stabilisation of the
-// Remarks in Sections 2 and 3, with the absorbed potentials held exactly as
-// exponents).  The sweeps run in FP32 inside one power-of-two frame per
-// sub-chunk of kSub points when c = h / eps <= kFrameC on the axis (every
-// output of a sub-chunk is at least lam^kSub = e^-64 of its largest term, so
-// what the frame flushes stays below FP32 rounding), and in extended range
-// (struct XF) point by point otherwise.
+// State.  A value is an FP32 number times a power-of-two frame shared by a
+// block of kSub points (the log-domain stabilisation of the Remarks in
+// Sections 2 and 3, the frames holding the absorbed potentials exactly):
+// u and v (outputs of a column pass) keep one frame per column slot and kSub
+// consecutive rows; the row-pass output Y keeps one frame per row, lane and
+// kSub consecutive points of the lane's chunk.  Values lie in [0, 1] of
+// their frame.  The sweeps run in FP32 inside such a frame: with
+// c = h / eps <= kFrameC on both axes every output of a block is at least
+// lam^kSub = e^-64 of the block's largest term, so what a frame flushes stays
+// below FP32 rounding.  Images with a larger c on an axis, or beyond the
+// shared-memory capacity, go to the grid kernel (fs1_solve2d.cu).
 //
 // Row slots.  A row of n_fast points occupies SW = 32 PF slots; point j of the
 // row sits in slot (j % PF) 32 + j / PF, so lane l's k-th point is slot
@@ -35,8 +38,9 @@
 // One iteration of Algorithm 2 (v-half, then u-half):
 //   v-half: Y = (I (x) K_f) u written over u (u is recomputed from v at the
 //           stop), column pass on Y -> y = K^T u in registers, error terms
-//           |v (K^T u) - b|, cluster sum of the error (fixed order, every CTA
-//           decides alike), then v = b / y unless the iteration stops;
+//           |v (K^T u) - b|, cluster sum of the error (FP64, fixed order,
+//           every CTA decides alike), then v = b / y unless the iteration
+//           stops;
 //   u-half: Y = (I (x) K_f) v into the u arrays, column pass -> u = a / y.
 // The stop test of iteration l is on (u^l, v^l); at the stop v^l is still in
 // place and u^l = a / (K v^l) is recomputed bit-identically by the same
@@ -56,21 +60,19 @@
 namespace fs1 {
 namespace c2d {
 
-constexpr int kCS = 16;             // CTAs per cluster (a non-portable cluster size)
+constexpr int kMaxCS = 16;          // largest cluster (a non-portable size)
 constexpr int kThr = 512;           // threads per CTA
 constexpr int kWarps = kThr / 32;
-constexpr int kSub = 8;             // points per FP32 frame
-constexpr double kFrameC = 8.0;     // frame sweeps when c = h / eps <= kFrameC (lam^kSub >= e^-64)
-constexpr int kE16Zero = -32768;    // exponent stored for a zero value
-constexpr int kE16Max = 32000;      // exponents beyond +-kE16Max end the solve (range)
+constexpr int kSub = 8;             // points per frame block
+constexpr double kFrameC = 8.0;     // FP32-frame sweeps need c = h / eps <= kFrameC (lam^kSub >= e^-64)
+constexpr int kHead = 6;            // headroom bits above a block's largest term
 
 // per-image descriptor (device memory)
 struct Img {
   const void* a;
   const void* b;
   int nf, ns;            // fast (contiguous) and slow lengths
-  int R;                 // rows per CTA: ceil(ns / kCS)
-  int frame_f, frame_s;  // 1: FP32-frame sweeps on the axis
+  int R;                 // rows per CTA: ceil(ns / cluster size)
   double cf, cs;         // h / eps per axis
   double hf, hs;
   double tol;
@@ -81,8 +83,8 @@ struct Img {
   double* g_out;
   float* aw;             // [ns][SW] a, b in slot order (workspace; L2-resident while
   float* bw;             //   the image is solved)
-  float* usm;            // [ns][SW] mantissas of u, saved for the cost phase
-  short* use;            // [ns][SW] exponents of u
+  float* us;             // [ns][SW] u saved for the cost phase, and its column frames
+  int* usf;              //   [cluster size][RS / kSub][SW]
 };
 
 struct Launch {
@@ -98,7 +100,7 @@ struct Launch {
 // decay tables of the image being solved (shared memory)
 struct Tabs {
   float lamf, lams;      // lam as FP32 (frame sweeps)
-  XF xlamf, xlams;       // lam as extended range (point-by-point sweeps)
+  XF xlamf, xlams;       // lam as extended range (cost phase)
   XF subf[kSub + 1];     // lam_f^k, k <= kSub
   XF subs[kSub + 1];     // lam_s^k
   XF ks[5];              // lam_f^{PF 2^lv}: the warp scan of the row pass
@@ -112,6 +114,11 @@ __device__ __forceinline__ unsigned cluster_rank() {
   unsigned r;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
   return r;
+}
+__device__ __forceinline__ unsigned cluster_size() {
+  unsigned n;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(n));
+  return n;
 }
 __device__ __forceinline__ void cluster_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
@@ -145,65 +152,71 @@ __device__ __forceinline__ double dsm_ld_f64(unsigned addr) {
   return v;
 }
 
-// ---------------------------------------------------------------------------
-// the 6-byte state: FP32 mantissa in [0.5, 1) (or 0) and a 16-bit exponent
-// ---------------------------------------------------------------------------
-// value m 2^e as (mantissa, exponent) slots; `bad` is set when the exponent
-// leaves the 16-bit range
-__device__ __forceinline__ void st6(float* pm, short* pe, XF v, bool& bad) {
-  if (v.m == 0.f) {
-    *pm = 0.f;
-    *pe = (short)kE16Zero;
-    return;
-  }
-  bad |= v.e > kE16Max || v.e < -kE16Max;
-  *pm = v.m;
-  *pe = (short)max(-kE16Max, min(kE16Max, v.e));
+__device__ __forceinline__ float load_in(const void* p, int64_t i, int f32) {
+  return f32 ? reinterpret_cast<const float*>(p)[i] : (float)reinterpret_cast<const double*>(p)[i];
 }
-// y in frame F, normalised and stored
-__device__ __forceinline__ void st6f(float* pm, short* pe, float y, int F, bool& bad) {
-  st6(pm, pe, xf_norm(y, F), bad);
+// e^x in extended range (x = -inf gives zero)
+__device__ __forceinline__ XF from_log(double x) {
+  if (!(x > -INFINITY)) return XF{0.f, kZeroExp};
+  const double t = x * 1.4426950408889634;
+  const double e = floor(t);
+  return xf_norm((float)exp2(t - e), (int)e);
 }
-__device__ __forceinline__ XF ld6(const float* pm, const short* pe) {
-  const float m = *pm;
-  return m == 0.f ? XF{0.f, kZeroExp} : XF{m, (int)*pe};
+__device__ __forceinline__ double to_log(float x, int F) {
+  return x > 0.f ? log((double)x) + (double)F * 0.6931471805599453 : -INFINITY;
 }
-// m 2^(e - F) for a mantissa in [0.5, 1): an exponent add (flushed to zero
-// more than 125 binades below the frame)
-__device__ __forceinline__ float in_frame(XF v, int F) {
-  const int d = v.e - F;
-  return (v.m == 0.f || d < -125) ? 0.f : __int_as_float(__float_as_int(v.m) + (d << 23));
+// u d as FP64
+__device__ __forceinline__ double prod64(XF u, XF d) {
+  if (u.m == 0.f || d.m == 0.f) return 0.0;
+  return ldexp((double)u.m * (double)d.m, u.e + d.e);
+}
+
+// N extended-range values as FP32 numbers in one frame (returned), the
+// largest in [0.5, 1); zeros stay zero
+template <int N>
+__device__ __forceinline__ int to_block(const XF (&v)[N], float (&x)[N]) {
+  int em = kZeroExp;
+#pragma unroll
+  for (int k = 0; k < N; ++k)
+    if (v[k].m != 0.f) em = max(em, v[k].e + fexp(v[k].m));
+#pragma unroll
+  for (int k = 0; k < N; ++k) x[k] = v[k].m * pow2f(v[k].e - em);
+  return em;
 }
 
 
 // ---------------------------------------------------------------------------
 // row pass: one warp, one row; lane l holds points l PF .. l PF + PF - 1 in
-// slots 32 k + l of (im, ie); the output goes to (om, oe) (may alias)
+// slots 32 k + l.  Input: values im with the frames icf of their column
+// blocks (same slots).  Output: values om in [0, 1] and the frames
+// orf[l NSB + s] of the lane's sub-blocks of SUB = min(PF, kSub) points.
+// om may alias im.
 // ---------------------------------------------------------------------------
-// FP32 frames of SUB = min(PF, kSub) points
 template <int PF>
-__device__ __forceinline__ void row_frame(const float* im, const short* ie, float* om, short* oe, int lane,
-                                          const Tabs& T, bool& bad) {
+__device__ __forceinline__ void row_pass_f(const float* im, const int* icf, float* om, int* orf, int lane,
+                                           const Tabs& T) {
   constexpr int SUB = PF < kSub ? PF : kSub;
   constexpr int NSB = PF / SUB;
   float x[PF];
   int fe[NSB];
 #pragma unroll
   for (int s = 0; s < NSB; ++s) {
-    XF v[SUB];
+    int f[SUB];
     int emax = kZeroExp;
 #pragma unroll
     for (int k = 0; k < SUB; ++k) {
-      v[k] = ld6(im + (s * SUB + k) * 32 + lane, ie + (s * SUB + k) * 32 + lane);
-      if (v[k].m != 0.f) emax = max(emax, v[k].e);
+      const int slot = (s * SUB + k) * 32 + lane;
+      x[s * SUB + k] = im[slot];
+      f[k] = icf[slot];
+      emax = max(emax, f[k]);
     }
     fe[s] = emax;
 #pragma unroll
-    for (int k = 0; k < SUB; ++k) x[s * SUB + k] = in_frame(v[k], emax);
+    for (int k = 0; k < SUB; ++k) x[s * SUB + k] *= pow2f(f[k] - emax);
   }
   const float lam = T.lamf;
-  // sub-chunk aggregates: forward to the sub-chunk's last point, backward
-  // from one before its first; lane aggregates over PF points
+  // sub-block aggregates: forward to the block's last point, backward from
+  // one before its first; lane aggregates over PF points
   XF af[NSB], ab[NSB];
   XF A = XF{0.f, kZeroExp}, B = XF{0.f, kZeroExp};
 #pragma unroll
@@ -231,14 +244,14 @@ __device__ __forceinline__ void row_frame(const float* im, const short* ie, floa
   XF C = shfl_up(xs, 1), D = shfl_down(zs, 1);
   if (lane == 0) C = XF{0.f, kZeroExp};
   if (lane == 31) D = XF{0.f, kZeroExp};
-  // backward carries at the last point of every sub-chunk
+  // backward carries at the last point of every sub-block
   XF Ds[NSB];
   Ds[NSB - 1] = D;
 #pragma unroll
   for (int s = NSB - 2; s >= 0; --s) Ds[s] = c_add(c_mul(Ds[s + 1], T.subf[SUB]), ab[s + 1]);
 #pragma unroll
   for (int s = 0; s < NSB; ++s) {
-    const int F = max(fe[s], max(C.e, Ds[s].e)) + 6;
+    const int F = max(fe[s], max(C.e, Ds[s].e)) + kHead;
     const float sc = pow2f(fe[s] - F);
     float t[SUB];
     float sb = c_to(Ds[s], F);
@@ -251,62 +264,23 @@ __device__ __forceinline__ void row_frame(const float* im, const short* ie, floa
 #pragma unroll
     for (int k = 0; k < SUB; ++k) {
       p = fmaf(lam, p, x[s * SUB + k] * sc);
-      const int slot = (s * SUB + k) * 32 + lane;
-      st6f(om + slot, oe + slot, p + t[k], F, bad);
+      om[(s * SUB + k) * 32 + lane] = p + t[k];
     }
-    C = c_add(c_mul(C, T.subf[SUB]), af[s]);   // forward carry into the next sub-chunk
+    orf[lane * NSB + s] = F;
+    C = c_add(c_mul(C, T.subf[SUB]), af[s]);   // forward carry into the next sub-block
   }
 }
-
-// extended range point by point (any c)
-template <int PF>
-__device__ __forceinline__ void row_xf(const float* im, const short* ie, float* om, short* oe, int lane,
-                                       const Tabs& T, bool& bad) {
-  XF x[PF];
-#pragma unroll
-  for (int k = 0; k < PF; ++k) x[k] = ld6(im + k * 32 + lane, ie + k * 32 + lane);
-  const XF lam = T.xlamf;
-  XF A = XF{0.f, kZeroExp}, B = XF{0.f, kZeroExp};
-#pragma unroll
-  for (int k = 0; k < PF; ++k) A = c_add(c_mul(A, lam), x[k]);
-#pragma unroll
-  for (int k = PF - 1; k >= 0; --k) B = c_mul(c_add(B, x[k]), lam);
-  XF xs = A, zs = B;
-#pragma unroll
-  for (int lv = 0; lv < 5; ++lv) {
-    const int o = 1 << lv;
-    const XF y = shfl_up(xs, o), w = shfl_down(zs, o);
-    if (lane >= o) xs = c_add(c_mul(y, T.ks[lv]), xs);
-    if (lane + o < 32) zs = c_add(zs, c_mul(w, T.ks[lv]));
-  }
-  XF p = shfl_up(xs, 1), sb = shfl_down(zs, 1);
-  if (lane == 0) p = XF{0.f, kZeroExp};
-  if (lane == 31) sb = XF{0.f, kZeroExp};
-  // the input is in registers: park the backward partials in the output slots
-#pragma unroll
-  for (int k = PF - 1; k >= 0; --k) {
-    st6(om + k * 32 + lane, oe + k * 32 + lane, sb, bad);
-    sb = c_mul(c_add(sb, x[k]), lam);
-  }
-#pragma unroll
-  for (int k = 0; k < PF; ++k) {
-    p = c_add(c_mul(p, lam), x[k]);
-    const XF t = ld6(om + k * 32 + lane, oe + k * 32 + lane);
-    st6(om + k * 32 + lane, oe + k * 32 + lane, c_add(p, t), bad);
-  }
-}
-
 
 // distance-weighted row pass (transport cost), extended range: for every
-// point k of the row, sum_j lam^{|k-j|} |k-j| x_j, handed to acc(k, value)
+// point k of the row, sum_j lam^{|k-j|} |k-j| x_j, handed to acc(slot,
+// value).  Input with column frames as row_pass_f.
 template <int PF, class Acc>
-__device__ __forceinline__ void row_dist(const float* im, const short* ie, float* tm, short* te, int lane,
-                                         const Tabs& T, bool& bad, Acc acc) {
+__device__ __forceinline__ void row_dist(const float* im, const int* icf, int lane, const Tabs& T, Acc acc) {
   using Op = OpDist<XF>;
   using P = PairC<XF>;
   XF x[PF];
 #pragma unroll
-  for (int k = 0; k < PF; ++k) x[k] = ld6(im + k * 32 + lane, ie + k * 32 + lane);
+  for (int k = 0; k < PF; ++k) x[k] = XF{im[k * 32 + lane], icf[k * 32 + lane]};
   const XF lam = T.xlamf;
   const XF z = XF{0.f, kZeroExp};
   XF p = z, A = z, s = z, B = z;
@@ -331,11 +305,12 @@ __device__ __forceinline__ void row_dist(const float* im, const short* ie, float
   P cf = Op::up(xs, 1), cb = Op::down(zs, 1);
   if (lane == 0) cf = Op::zero();
   if (lane == 31) cb = Op::zero();
+  XF tb[PF];
   s = cb.p;
   B = cb.a;
 #pragma unroll
-  for (int k = PF - 1; k >= 0; --k) {   // backward partials parked in (tm, te)
-    st6(tm + k * 32 + lane, te + k * 32 + lane, B, bad);
+  for (int k = PF - 1; k >= 0; --k) {
+    tb[k] = B;
     B = c_mul(c_add(c_add(B, s), x[k]), lam);
     s = c_mul(c_add(s, x[k]), lam);
   }
@@ -345,7 +320,7 @@ __device__ __forceinline__ void row_dist(const float* im, const short* ie, float
   for (int k = 0; k < PF; ++k) {
     A = c_mul(c_add(A, p), lam);
     p = c_add(c_mul(p, lam), x[k]);
-    acc(k * 32 + lane, c_add(A, ld6(tm + k * 32 + lane, te + k * 32 + lane)));
+    acc(k * 32 + lane, c_add(A, tb[k]));
   }
 }
 
@@ -355,146 +330,131 @@ __device__ __forceinline__ void row_dist(const float* im, const short* ie, float
 // Phase A forms the chunk aggregates and publishes them (forward: measured at
 // the chunk's last row; backward: from one row before its first); after a
 // cluster barrier, phase B reads the other CTAs' aggregates, forms the
-// carries and runs the final sweeps.  The result y_r = (K_s Y)_r of every row
-// is left in (y[r], ye[r]) as an extended-range value.
+// carries and runs the final sweeps.  The input's values are ym[r SW + t]
+// with frames fr(r); the result y_r = (K_s Y)_r is left as y[r] in [0, 1]
+// of the frame fe[r / kSub].
 // ---------------------------------------------------------------------------
 template <int RS>
-struct ColF {   // FP32-frame column state
-  static constexpr int SUB = kSub;
-  static constexpr int NSB = RS / SUB;
+struct ColF {
+  static constexpr int NSB = RS / kSub;
   float y[RS];
   int fe[NSB];   // input frames; after phase B the output frames
   XF af[NSB], ab[NSB];
-  __device__ __forceinline__ XF get(int r) const { return XF{y[r], fe[r / SUB]}; }
+  __device__ __forceinline__ XF get(int r) const { return XF{y[r], fe[r / kSub]}; }
 };
 
-template <int RS>
-__device__ __forceinline__ void colf_a(ColF<RS>& c, const float* ym, const short* yex, int SW, int t, int nr,
-                                       const Tabs& T, XF* pubf, XF* pubb) {
-  constexpr int SUB = ColF<RS>::SUB, NSB = ColF<RS>::NSB;
+template <int RS, class FR>
+__device__ __forceinline__ void colf_a(ColF<RS>& c, const float* ym, FR fr, int SW, int t, int nr, const Tabs& T,
+                                       XF* pubf, XF* pubb) {
+  constexpr int NSB = ColF<RS>::NSB;
   const float lam = T.lams;
   XF A = XF{0.f, kZeroExp}, B = XF{0.f, kZeroExp};
 #pragma unroll
   for (int s = 0; s < NSB; ++s) {
-    XF v[SUB];
+    int f[kSub];
     int emax = kZeroExp;
 #pragma unroll
-    for (int k = 0; k < SUB; ++k) {
-      const int r = s * SUB + k;
-      v[k] = r < nr ? ld6(ym + r * SW + t, yex + r * SW + t) : XF{0.f, kZeroExp};
-      if (v[k].m != 0.f) emax = max(emax, v[k].e);
+    for (int k = 0; k < kSub; ++k) {
+      const int r = s * kSub + k;
+      c.y[r] = r < nr ? ym[r * SW + t] : 0.f;
+      f[k] = r < nr ? fr(r) : kZeroExp;
+      emax = max(emax, f[k]);
     }
     c.fe[s] = emax;
     float rr = 0.f, qq = 0.f;
 #pragma unroll
-    for (int k = 0; k < SUB; ++k) {
-      c.y[s * SUB + k] = in_frame(v[k], emax);
-      rr = fmaf(s * SUB + k < nr ? lam : 1.f, rr, c.y[s * SUB + k]);
+    for (int k = 0; k < kSub; ++k) {
+      c.y[s * kSub + k] *= pow2f(f[k] - emax);
+      rr = fmaf(s * kSub + k < nr ? lam : 1.f, rr, c.y[s * kSub + k]);
     }
 #pragma unroll
-    for (int k = SUB - 1; k >= 0; --k) qq = (s * SUB + k < nr ? lam : 1.f) * (qq + c.y[s * SUB + k]);
+    for (int k = kSub - 1; k >= 0; --k) qq = (s * kSub + k < nr ? lam : 1.f) * (qq + c.y[s * kSub + k]);
     c.af[s] = xf_norm(rr, emax);
     c.ab[s] = xf_norm(qq, emax);
-    const int len = max(0, min(SUB, nr - s * SUB));
+    const int len = max(0, min(kSub, nr - s * kSub));
     A = c_add(c_mul(A, T.subs[len]), c.af[s]);
   }
 #pragma unroll
   for (int s = NSB - 1; s >= 0; --s) {
-    const int len = max(0, min(SUB, nr - s * SUB));
+    const int len = max(0, min(kSub, nr - s * kSub));
     B = c_add(c.ab[s], c_mul(B, T.subs[len]));
   }
   pubf[t] = A;
   pubb[t] = B;
 }
 
-// forward and backward carries of this CTA's chunk from the other CTAs'
-// aggregates (Horner over CTAs, lam^R per CTA)
-__device__ __forceinline__ void col_carries(const XF* pubf, const XF* pubb, int t, unsigned rank, const Tabs& T,
-                                            XF& C, XF& D) {
-  C = XF{0.f, kZeroExp};
-  D = XF{0.f, kZeroExp};
-  for (unsigned k = 0; k < rank; ++k) C = c_add(c_mul(C, T.lamR), dsm_ld_xf(dsm_addr(pubf + t, k)));
-  for (unsigned k = kCS - 1; k > rank; --k) D = c_add(dsm_ld_xf(dsm_addr(pubb + t, k)), c_mul(D, T.lamR));
+// Forward and backward carries of this CTA's chunk from the other CTAs'
+// aggregates (Horner over the ncta CTAs, lam^R per CTA); the remote loads
+// are issued four at a time, so their latencies overlap.
+__device__ __forceinline__ void col_carries(const XF* pubf, const XF* pubb, int t, unsigned rank, unsigned ncta,
+                                            const Tabs& T, XF& C, XF& D) {
+  constexpr int kB = 4;
+  const XF z = XF{0.f, kZeroExp};
+  C = z;
+  D = z;
+  for (unsigned k0 = 0; k0 < rank; k0 += kB) {
+    XF x[kB];
+#pragma unroll
+    for (int i = 0; i < kB; ++i) x[i] = k0 + i < rank ? dsm_ld_xf(dsm_addr(pubf + t, k0 + i)) : z;
+#pragma unroll
+    for (int i = 0; i < kB; ++i)
+      if (k0 + i < rank) C = c_add(c_mul(C, T.lamR), x[i]);
+  }
+  for (int k1 = (int)ncta - 1; k1 > (int)rank; k1 -= kB) {   // CTAs k1, k1 - 1, ... (> rank)
+    XF x[kB];
+#pragma unroll
+    for (int i = 0; i < kB; ++i) x[i] = k1 - i > (int)rank ? dsm_ld_xf(dsm_addr(pubb + t, (unsigned)(k1 - i))) : z;
+#pragma unroll
+    for (int i = 0; i < kB; ++i)
+      if (k1 - i > (int)rank) D = c_add(x[i], c_mul(D, T.lamR));
+  }
 }
 
 template <int RS>
-__device__ __forceinline__ void colf_b(ColF<RS>& c, int t, int nr, unsigned rank, const Tabs& T, const XF* pubf,
-                                       const XF* pubb) {
-  constexpr int SUB = ColF<RS>::SUB, NSB = ColF<RS>::NSB;
+__device__ __forceinline__ void colf_b(ColF<RS>& c, int t, int nr, unsigned rank, unsigned ncta, const Tabs& T,
+                                       const XF* pubf, const XF* pubb) {
+  constexpr int NSB = ColF<RS>::NSB;
   const float lam = T.lams;
   XF C, D;
-  col_carries(pubf, pubb, t, rank, T, C, D);
+  col_carries(pubf, pubb, t, rank, ncta, T, C, D);
   XF Ds[NSB];
   Ds[NSB - 1] = D;
 #pragma unroll
   for (int s = NSB - 2; s >= 0; --s) {
-    const int len = max(0, min(SUB, nr - (s + 1) * SUB));
+    const int len = max(0, min(kSub, nr - (s + 1) * kSub));
     Ds[s] = c_add(c_mul(Ds[s + 1], T.subs[len]), c.ab[s + 1]);
   }
 #pragma unroll
   for (int s = 0; s < NSB; ++s) {
-    const int F = max(c.fe[s], max(C.e, Ds[s].e)) + 6;
+    const int F = max(c.fe[s], max(C.e, Ds[s].e)) + kHead;
     const float sc = pow2f(c.fe[s] - F);
-    float tb[SUB];
+    float tb[kSub];
     float sb = c_to(Ds[s], F);
 #pragma unroll
-    for (int k = SUB - 1; k >= 0; --k) {
+    for (int k = kSub - 1; k >= 0; --k) {
       tb[k] = sb;
-      sb = (s * SUB + k < nr ? lam : 1.f) * fmaf(c.y[s * SUB + k], sc, sb);
+      sb = (s * kSub + k < nr ? lam : 1.f) * fmaf(c.y[s * kSub + k], sc, sb);
     }
     float p = c_to(C, F);
 #pragma unroll
-    for (int k = 0; k < SUB; ++k) {
-      p = fmaf(s * SUB + k < nr ? lam : 1.f, p, c.y[s * SUB + k] * sc);
-      c.y[s * SUB + k] = p + tb[k];
+    for (int k = 0; k < kSub; ++k) {
+      p = fmaf(s * kSub + k < nr ? lam : 1.f, p, c.y[s * kSub + k] * sc);
+      c.y[s * kSub + k] = p + tb[k];
     }
     c.fe[s] = F;
-    const int len = max(0, min(SUB, nr - s * SUB));
+    const int len = max(0, min(kSub, nr - s * kSub));
     C = c_add(c_mul(C, T.subs[len]), c.af[s]);
   }
 }
 
 // extended-range column pass with the operator Op (OpPlain<XF> or
-// OpDist<XF>); the backward partials are parked in the input slots (free
-// once the input is in registers).  Output: the plain sum (OpPlain) or the
-// distance-weighted sum (OpDist) of every row, left in x.
+// OpDist<XF>) for the transport cost (once per solve); input values ym with
+// frames fr(r).  Output: the plain sum (OpPlain) or the distance-weighted
+// sum (OpDist) of every row, left in x.
 template <int RS, class Op>
 struct ColX {
   XF x[RS];
-  typename Op::T agf, agb;
 };
-
-template <int RS, class Op>
-__device__ __forceinline__ void colx_a(ColX<RS, Op>& c, const float* ym, const short* yex, int SW, int t, int nr,
-                                       const Tabs& T, typename Op::T* pubf, typename Op::T* pubb) {
-  const XF lam = T.xlams;
-  const XF z = XF{0.f, kZeroExp};
-  XF p = z, A = z, s = z, B = z;
-#pragma unroll
-  for (int r = 0; r < RS; ++r) {
-    c.x[r] = r < nr ? ld6(ym + r * SW + t, yex + r * SW + t) : z;
-    if (r < nr) {
-      if constexpr (!std::is_same<Op, OpPlain<XF>>::value) A = c_mul(c_add(A, p), lam);
-      p = c_add(c_mul(p, lam), c.x[r]);
-    }
-  }
-#pragma unroll
-  for (int r = RS - 1; r >= 0; --r) {
-    if (r < nr) {
-      if constexpr (!std::is_same<Op, OpPlain<XF>>::value) B = c_mul(c_add(c_add(B, s), c.x[r]), lam);
-      s = c_mul(c_add(s, c.x[r]), lam);
-    }
-  }
-  if constexpr (std::is_same<Op, OpPlain<XF>>::value) {
-    c.agf = p;
-    c.agb = s;
-  } else {
-    c.agf = PairC<XF>{p, A};
-    c.agb = PairC<XF>{s, B};
-  }
-  pubf[t] = c.agf;
-  pubb[t] = c.agb;
-}
 
 template <class T>
 __device__ __forceinline__ T dsm_ld_op(const T* p, unsigned rank);
@@ -508,25 +468,56 @@ __device__ __forceinline__ PairC<XF> dsm_ld_op<PairC<XF>>(const PairC<XF>* p, un
   return PairC<XF>{dsm_ld_xf(a), dsm_ld_xf(a + 8)};
 }
 
+template <int RS, class Op, class FR>
+__device__ __forceinline__ void colx_a(ColX<RS, Op>& c, const float* ym, FR fr, int SW, int t, int nr,
+                                       const Tabs& T, typename Op::T* pubf, typename Op::T* pubb) {
+  constexpr bool W = !std::is_same<Op, OpPlain<XF>>::value;
+  const XF lam = T.xlams;
+  const XF z = XF{0.f, kZeroExp};
+  XF p = z, A = z, s = z, B = z;
+#pragma unroll
+  for (int r = 0; r < RS; ++r) {
+    c.x[r] = r < nr ? XF{ym[r * SW + t], fr(r)} : z;
+    if (r < nr) {
+      if (W) A = c_mul(c_add(A, p), lam);
+      p = c_add(c_mul(p, lam), c.x[r]);
+    }
+  }
+#pragma unroll
+  for (int r = RS - 1; r >= 0; --r) {
+    if (r < nr) {
+      if (W) B = c_mul(c_add(c_add(B, s), c.x[r]), lam);
+      s = c_mul(c_add(s, c.x[r]), lam);
+    }
+  }
+  if constexpr (W) {
+    pubf[t] = PairC<XF>{p, A};
+    pubb[t] = PairC<XF>{s, B};
+  } else {
+    pubf[t] = p;
+    pubb[t] = s;
+  }
+}
+
 template <int RS, class Op>
-__device__ __forceinline__ void colx_b(ColX<RS, Op>& c, float* ym, short* yex, int SW, int t, int nr, int R,
-                                       unsigned rank, const Tabs& T, const typename Op::T* pubf,
-                                       const typename Op::T* pubb, bool& bad) {
+__device__ __forceinline__ void colx_b(ColX<RS, Op>& c, int t, int nr, int R, unsigned rank, unsigned ncta,
+                                       const Tabs& T, const typename Op::T* pubf, const typename Op::T* pubb) {
   constexpr bool W = !std::is_same<Op, OpPlain<XF>>::value;
   const XF lam = T.xlams;
   typename Op::T C = Op::zero(), D = Op::zero();
   for (unsigned k = 0; k < rank; ++k) C = Op::fwd(C, dsm_ld_op(pubf + t, k), T.lamR, (float)R);
-  for (unsigned k = kCS - 1; k > rank; --k) D = Op::bwd(dsm_ld_op(pubb + t, k), D, T.lamR, (float)R);
+  for (int k = (int)ncta - 1; k > (int)rank; --k) D = Op::bwd(dsm_ld_op(pubb + t, (unsigned)k), D, T.lamR, (float)R);
   XF s, B, p, A;
   if constexpr (W) {
     s = D.p; B = D.a; p = C.p; A = C.a;
   } else {
     s = D; B = XF{0.f, kZeroExp}; p = C; A = XF{0.f, kZeroExp};
   }
+  XF tb[RS];
 #pragma unroll
   for (int r = RS - 1; r >= 0; --r) {
+    tb[r] = W ? B : s;
     if (r < nr) {
-      st6(ym + r * SW + t, yex + r * SW + t, W ? B : s, bad);
       if (W) B = c_mul(c_add(c_add(B, s), c.x[r]), lam);
       s = c_mul(c_add(s, c.x[r]), lam);
     }
@@ -536,34 +527,16 @@ __device__ __forceinline__ void colx_b(ColX<RS, Op>& c, float* ym, short* yex, i
     if (r < nr) {
       if (W) A = c_mul(c_add(A, p), lam);
       p = c_add(c_mul(p, lam), c.x[r]);
-      c.x[r] = c_add(W ? A : p, ld6(ym + r * SW + t, yex + r * SW + t));   // the result, in place
+      c.x[r] = c_add(W ? A : p, tb[r]);   // the result, in place
     }
   }
 }
 
 
-__device__ __forceinline__ float load_in(const void* p, int64_t i, int f32) {
-  return f32 ? reinterpret_cast<const float*>(p)[i] : (float)reinterpret_cast<const double*>(p)[i];
-}
-// e^x in extended range (x = -inf gives zero)
-__device__ __forceinline__ XF from_log(double x) {
-  if (!(x > -INFINITY)) return XF{0.f, kZeroExp};
-  const double t = x * 1.4426950408889634;
-  const double e = floor(t);
-  return xf_norm((float)exp2(t - e), (int)e);
-}
-__device__ __forceinline__ double to_log(XF v) {
-  return v.m > 0.f ? log((double)v.m) + (double)v.e * 0.6931471805599453 : -INFINITY;
-}
-// u d as FP64
-__device__ __forceinline__ double prod64(XF u, XF d) {
-  if (u.m == 0.f || d.m == 0.f) return 0.0;
-  return ldexp((double)u.m * (double)d.m, u.e + d.e);
-}
-
 // bytes of dynamic shared memory of an instantiation
 __host__ __device__ constexpr size_t smem_bytes(int PF, int RS) {
-  return (size_t)RS * 32 * PF * 12 + (size_t)32 * 32 * PF;
+  return (size_t)RS * 32 * PF * 8 + (size_t)4 * 32 * PF * 8 + (size_t)2 * (RS / kSub) * 32 * PF * 4 +
+         (size_t)RS * 32 * (PF < kSub ? 1 : PF / kSub) * 4;
 }
 
 // ---------------------------------------------------------------------------
@@ -572,25 +545,33 @@ __host__ __device__ constexpr size_t smem_bytes(int PF, int RS) {
 template <int PF, int RS>
 __global__ void __launch_bounds__(kThr, 1) fs1_cluster2d_kernel(Launch L) {
   constexpr int SW = 32 * PF;
+  constexpr int SUBF = PF < kSub ? PF : kSub;
+  constexpr int NSF = PF / SUBF;      // row-frame blocks of a lane's chunk
+  constexpr int NSB = RS / kSub;      // column-frame blocks of a slot
+  static_assert(RS % kSub == 0, "RS");
   extern __shared__ __align__(16) unsigned char c2d_smem[];
-  float* const um = reinterpret_cast<float*>(c2d_smem);   // [RS][SW] u (and the row-pass output)
+  float* const um = reinterpret_cast<float*>(c2d_smem);   // [RS][SW] u (and the row-pass output Y)
   float* const vm = um + RS * SW;                          // [RS][SW] v
   XF* const xbf = reinterpret_cast<XF*>(vm + RS * SW);    // [2][SW] forward aggregates by half-step
   XF* const xbb = xbf + 2 * SW;                            // [2][SW] backward aggregates
-  short* const ue = reinterpret_cast<short*>(xbb + 2 * SW);
-  short* const ve = ue + RS * SW;
+  int* const cfu = reinterpret_cast<int*>(xbb + 2 * SW);  // [NSB][SW] column frames of u
+  int* const cfv = cfu + NSB * SW;                         // [NSB][SW] column frames of v
+  int* const rfy = cfv + NSB * SW;                         // [RS][32][NSF] row frames of Y
   __shared__ Tabs T;
   __shared__ __align__(16) float s_err[4];   // this CTA's error partial (hi, lo) and range flag
   __shared__ float s_red[2 * kWarps];
   __shared__ double s_wred[kWarps];
-  __shared__ __align__(8) double s_w;   // this CTA's transport-cost partial
-  __shared__ double s_dec;            // the cluster's error sum
-  __shared__ int s_decbad;
+  __shared__ __align__(8) double s_w;        // this CTA's transport-cost partial
+  __shared__ double s_dec;                   // the cluster's error sum
   __shared__ int s_img;
-  const unsigned rank = cluster_rank();
+  const unsigned rank = cluster_rank(), ncta = cluster_size();
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const bool act = tid < SW;          // a column-pass thread
+  const bool act = tid < SW;                 // a column-pass thread
   const XF zero = XF{0.f, kZeroExp};
+  // frames of (row r, slot tid): Y by rows, u and v by column blocks
+  auto yfr = [&](int r) { return rfy[(r * 32 + (tid & 31)) * NSF + (tid >> 5) / SUBF]; };
+  auto ufr = [&](int r) { return cfu[(r / kSub) * SW + tid]; };
+  auto vfr = [&](int r) { return cfv[(r / kSub) * SW + tid]; };
 
   for (;;) {
     if (rank == 0 && tid == 0) s_img = atomicAdd(L.next, 1);
@@ -607,7 +588,10 @@ __global__ void __launch_bounds__(kThr, 1) fs1_cluster2d_kernel(Launch L) {
     const int nf = I.nf, ns = I.ns, R = I.R;
     const int row0 = (int)rank * R;
     const int nr = max(0, min(R, ns - row0));   // rows of this CTA
-    const bool ff = I.frame_f != 0, fsl = I.frame_s != 0;
+    const float* const aw = I.aw + (size_t)row0 * SW;
+    const float* const bw = I.bw + (size_t)row0 * SW;
+    const double tol = I.tol;
+    const int64_t itr_max = I.itr_max;
     if (tid == 0) {
       T.lamf = (float)exp(-I.cf);
       T.lams = (float)exp(-I.cs);
@@ -620,101 +604,102 @@ __global__ void __launch_bounds__(kThr, 1) fs1_cluster2d_kernel(Launch L) {
       for (int lv = 0; lv < 5; ++lv) T.ks[lv] = c_decay((double)(PF << lv), I.cf, XF{});
       T.lamR = c_decay((double)R, I.cs, XF{});
     }
-    bool bad = false;
     // ---- a, b into slot order; u = v = 1 / N (Algorithm 2) or the warm start
     const XF init = xf_norm((float)(1.0 / ((double)nf * (double)ns)), 0);
-    auto init_u = [&](bool with_ab) {
-      for (int idx = tid; idx < RS * SW; idx += kThr) {
-        const int r = idx / SW, slot = idx - r * SW;
-        const int j = (slot & 31) * PF + (slot >> 5);
-        const bool real = r < nr && j < nf;
-        const int64_t gp = (int64_t)(row0 + r) * nf + j;
-        XF u0 = zero, v0 = zero;
-        if (real) u0 = I.f_init ? from_log(I.f_init[gp]) : init;
-        st6(um + idx, ue + idx, u0, bad);
-        if (with_ab) {
-          float av = 0.f, bv = 0.f;
+    auto init_state = [&](bool all) {
+      if (!act) return;
+      const int j = (tid & 31) * PF + (tid >> 5);
+#pragma unroll
+      for (int s = 0; s < NSB; ++s) {
+        XF uv[kSub], vv[kSub];
+#pragma unroll
+        for (int k = 0; k < kSub; ++k) {
+          const int r = s * kSub + k;
+          const bool real = r < nr && j < nf;
+          const int64_t gp = (int64_t)(row0 + r) * nf + j;
+          uv[k] = vv[k] = zero;
           if (real) {
-            av = load_in(I.a, gp, L.in_f32);
-            bv = load_in(I.b, gp, L.in_f32);
-            v0 = I.g_init ? from_log(I.g_init[gp]) : init;
+            uv[k] = I.f_init ? from_log(I.f_init[gp]) : init;
+            if (all) vv[k] = I.g_init ? from_log(I.g_init[gp]) : init;
           }
-          if (r < nr) {
-            I.aw[(int64_t)(row0 + r) * SW + slot] = av;
-            I.bw[(int64_t)(row0 + r) * SW + slot] = bv;
+          if (all && r < nr) {
+            I.aw[(int64_t)(row0 + r) * SW + tid] = real ? load_in(I.a, gp, L.in_f32) : 0.f;
+            I.bw[(int64_t)(row0 + r) * SW + tid] = real ? load_in(I.b, gp, L.in_f32) : 0.f;
           }
-          st6(vm + idx, ve + idx, v0, bad);
+        }
+        float x[kSub];
+        cfu[s * SW + tid] = to_block(uv, x);
+#pragma unroll
+        for (int k = 0; k < kSub; ++k) um[(s * kSub + k) * SW + tid] = x[k];
+        if (all) {
+          cfv[s * SW + tid] = to_block(vv, x);
+#pragma unroll
+          for (int k = 0; k < kSub; ++k) vm[(s * kSub + k) * SW + tid] = x[k];
         }
       }
     };
-    init_u(true);
+    init_state(true);
     __syncthreads();
 
-    // row pass over this CTA's rows: (im, ie) -> (om, oe)
-    auto row_pass = [&](const float* im, const short* ie, float* om, short* oe) {
-      for (int r = warp; r < nr; r += kWarps) {
-        if (ff)
-          row_frame<PF>(im + r * SW, ie + r * SW, om + r * SW, oe + r * SW, lane, T, bad);
-        else
-          row_xf<PF>(im + r * SW, ie + r * SW, om + r * SW, oe + r * SW, lane, T, bad);
-      }
+    // row pass over this CTA's rows: (im, column frames icf) -> (um, rfy)
+    auto row_pass = [&](const float* im, const int* icf) {
+      for (int r = warp; r < nr; r += kWarps)
+        row_pass_f<PF>(im + r * SW, icf + (r / kSub) * SW, um + r * SW, rfy + r * 32 * NSF, lane, T);
       __syncthreads();
     };
-    // column pass of the u arrays (which hold the row-pass output) with the
-    // exchange buffers of half-step h; epi(get_y) consumes the result (all
-    // threads call epi; get_y(r) is valid for act threads and r < nr)
-    auto col_pass = [&](int h, auto epi) {
-      XF* pf = xbf + h * SW;
-      XF* pb = xbb + h * SW;
-      if (fsl) {
-        ColF<RS> c;
-        if (act) colf_a<RS>(c, um, ue, SW, tid, nr, T, pf, pb);
-        cluster_sync();
-        if (act) colf_b<RS>(c, tid, nr, rank, T, pf, pb);
-        epi([&](int r) { return c.get(r); });
-      } else {
-        ColX<RS, OpPlain<XF>> c;
-        if (act) colx_a<RS, OpPlain<XF>>(c, um, ue, SW, tid, nr, T, pf, pb);
-        cluster_sync();
-        if (act) colx_b<RS, OpPlain<XF>>(c, um, ue, SW, tid, nr, R, rank, T, pf, pb, bad);
-        epi([&](int r) { return c.x[r]; });
+    // m_r / y_r of the rows of this slot, block by block, into (xm, cf)
+    auto divide_into = [&](const ColF<RS>& c, const float* mw, float* xm, int* cf) {
+#pragma unroll
+      for (int s = 0; s < NSB; ++s) {
+        XF z[kSub];
+#pragma unroll
+        for (int k = 0; k < kSub; ++k) {
+          const int r = s * kSub + k;
+          z[k] = zero;
+          if (r < nr) {
+            const float m = mw[r * SW + tid];
+            const XF y = xf_norm(c.y[r], c.fe[s]);
+            if (m > 0.f) z[k] = XF{__fdividef(m, y.m), -y.e};
+          }
+        }
+        float x[kSub];
+        cf[s * SW + tid] = to_block(z, x);
+#pragma unroll
+        for (int k = 0; k < kSub; ++k) xm[(s * kSub + k) * SW + tid] = x[k];
       }
     };
     // u-half: Y = (I (x) K_f) v, u = a / ((K_s (x) I) Y)
     auto u_half = [&]() {
-      row_pass(vm, ve, um, ue);
-      col_pass(1, [&](auto gy) {
-        if (act) {
-#pragma unroll
-          for (int r = 0; r < RS; ++r) {
-            if (r < nr) {
-              const float aa = I.aw[(int64_t)(row0 + r) * SW + tid];
-              const XF y = gy(r);
-              st6(um + r * SW + tid, ue + r * SW + tid, aa > 0.f ? xf_norm(__fdividef(aa, y.m), -y.e) : zero, bad);
-            }
-          }
-        }
-      });
+      row_pass(vm, cfv);
+      ColF<RS> c;
+      if (act) colf_a<RS>(c, um, yfr, SW, tid, nr, T, xbf + SW, xbb + SW);
+      cluster_sync();
+      if (act) {
+        colf_b<RS>(c, tid, nr, rank, ncta, T, xbf + SW, xbb + SW);
+        divide_into(c, aw, um, cfu);
+      }
       __syncthreads();
     };
 
     int64_t ell = 0;
     double err = 0.0;
-    int anybad = 0;
     for (;; ++ell) {
       // ---- v-half: Y = (I (x) K_f) u over u, y = (K_s (x) I) Y, error, v = b / y
-      row_pass(um, ue, um, ue);
-      bool stop = false;
-      col_pass(0, [&](auto gy) {
+      row_pass(um, cfu);
+      bool stop;
+      {
+        ColF<RS> c;
+        if (act) colf_a<RS>(c, um, yfr, SW, tid, nr, T, xbf, xbb);
+        cluster_sync();
         float eh = 0.f, el = 0.f;
         if (act) {
+          colf_b<RS>(c, tid, nr, rank, ncta, T, xbf, xbb);
 #pragma unroll
           for (int r = 0; r < RS; ++r) {
             if (r < nr) {
-              const float bb = I.bw[(int64_t)(row0 + r) * SW + tid];
-              const XF vo = ld6(vm + r * SW + tid, ve + r * SW + tid);
-              const float pv = c_to(c_mul(vo, gy(r)), 0);   // v (K^T u) at the point
-              df_add(eh, el, fabsf(pv - bb), 0.f);
+              const XF vo = XF{vm[r * SW + tid], vfr(r)};
+              const float pv = c_to(c_mul(vo, c.get(r)), 0);   // v (K^T u) at the point
+              df_add(eh, el, fabsf(pv - bw[r * SW + tid]), 0.f);
             }
           }
         }
@@ -723,55 +708,37 @@ __global__ void __launch_bounds__(kThr, 1) fs1_cluster2d_kernel(Launch L) {
           s_red[2 * warp] = eh;
           s_red[2 * warp + 1] = el;
         }
-        const int cbad = __syncthreads_or((int)bad);
+        __syncthreads();
         if (tid == 0) {
           float h = 0.f, l = 0.f;
           for (int w = 0; w < kWarps; ++w) df_add(h, l, s_red[2 * w], s_red[2 * w + 1]);
           s_err[0] = h;
           s_err[1] = l;
-          s_err[2] = cbad ? 1.f : 0.f;
         }
         cluster_sync();
         // the cluster's sum in FP64, in one fixed order in every CTA
         if (warp == 0) {
           double e = 0.0;
-          int b = 0;
-          if (lane < kCS) {
-            const unsigned a = dsm_addr(s_err, (unsigned)lane);
-            const float2 hl = dsm_ld_f2(a);
+          if (lane < (int)ncta) {
+            const float2 hl = dsm_ld_f2(dsm_addr(s_err, (unsigned)lane));
             e = (double)hl.x + (double)hl.y;
-            b = __float_as_int(dsm_ld_f2(a + 8).x) != 0;
           }
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-          b = __any_sync(0xffffffffu, b);
-          if (lane == 0) {
-            s_dec = e;
-            s_decbad = b;
-          }
+          if (lane == 0) s_dec = e;
         }
         __syncthreads();
         err = s_dec;
-        anybad = s_decbad;
-        stop = anybad || !isfinite(err) || err <= I.tol || ell >= I.itr_max;
-        if (!stop && act) {
-#pragma unroll
-          for (int r = 0; r < RS; ++r) {
-            if (r < nr) {
-              const float bb = I.bw[(int64_t)(row0 + r) * SW + tid];
-              const XF y = gy(r);
-              st6(vm + r * SW + tid, ve + r * SW + tid, bb > 0.f ? xf_norm(__fdividef(bb, y.m), -y.e) : zero, bad);
-            }
-          }
-        }
-      });
+        stop = !isfinite(err) || err <= tol || ell >= itr_max;
+        if (!stop && act) divide_into(c, bw, vm, cfv);
+      }
       __syncthreads();
       // At the stop, u^l is rebuilt: the initial u when no iteration ran,
       // else by this same u-half from v^l, which is how iteration l - 1 made
       // it (one code path, so the result is bit-identical and a resumed
       // solve continues exactly)
       if (stop && ell == 0) {
-        init_u(false);
+        init_state(false);
         __syncthreads();
         break;
       }
@@ -780,42 +747,36 @@ __global__ void __launch_bounds__(kThr, 1) fs1_cluster2d_kernel(Launch L) {
       if (stop) break;
     }
     cluster_sync();   // every CTA is done with the exchange buffers
-    const int status = anybad ? FS1_EUNSUPPORTED
-                              : (!isfinite(err) ? FS1_ENUMERIC : (err <= I.tol ? FS1_OK : FS1_ENOTCONV));
+    const int status = !isfinite(err) ? FS1_ENUMERIC : (err <= tol ? FS1_OK : FS1_ENOTCONV);
     // ---- optional potentials out
-    if (I.f_out || I.g_out) {
-      for (int idx = tid; idx < nr * SW; idx += kThr) {
-        const int r = idx / SW, slot = idx - r * SW;
-        const int j = (slot & 31) * PF + (slot >> 5);
-        if (j >= nf) continue;
+    if ((I.f_out || I.g_out) && act) {
+      const int j = (tid & 31) * PF + (tid >> 5);
+      for (int r = 0; r < nr && j < nf; ++r) {
         const int64_t gp = (int64_t)(row0 + r) * nf + j;
-        if (I.f_out) I.f_out[gp] = to_log(ld6(um + idx, ue + idx));
-        if (I.g_out) I.g_out[gp] = to_log(ld6(vm + idx, ve + idx));
+        if (I.f_out) I.f_out[gp] = to_log(um[r * SW + tid], ufr(r));
+        if (I.g_out) I.g_out[gp] = to_log(vm[r * SW + tid], vfr(r));
       }
     }
     // ---- transport cost (a9): h_s u . ((K_s^(c) (x) K_f) v) + h_f u . ((K_s (x) K_f^(c)) v)
     double acc = 0.0;
-    if (status == FS1_OK || status == FS1_ENOTCONV) {
-      for (int idx = tid; idx < nr * SW; idx += kThr) {   // u, saved in slot order
-        I.usm[(int64_t)row0 * SW + idx] = um[idx];
-        I.use[(int64_t)row0 * SW + idx] = ue[idx];
-      }
+    if (status != FS1_ENUMERIC) {
+      float* const us = I.us + (size_t)row0 * SW;
+      int* const usf = I.usf + (size_t)rank * NSB * SW;
+      for (int idx = tid; idx < nr * SW; idx += kThr) us[idx] = um[idx];
+      for (int idx = tid; idx < NSB * SW; idx += kThr) usf[idx] = cfu[idx];
       __syncthreads();
-      auto ug = [&](int r, int slot) {
-        const int64_t g = (int64_t)(row0 + r) * SW + slot;
-        return ld6(I.usm + g, I.use + g);
-      };
-      // slow axis: Z = (I (x) K_f) v, then (K_s^(c) (x) I) Z by columns
-      row_pass(vm, ve, um, ue);
+      auto ug = [&](int r, int slot) { return XF{us[r * SW + slot], usf[(r / kSub) * SW + slot]}; };
+      // slow axis: Z = (I (x) K_f) v by rows, then (K_s^(c) (x) I) Z by columns
+      row_pass(vm, cfv);
       {
         using OpD = OpDist<XF>;
         PairC<XF>* pf = reinterpret_cast<PairC<XF>*>(xbf);
         PairC<XF>* pb = reinterpret_cast<PairC<XF>*>(xbb);
         ColX<RS, OpD> c;
-        if (act) colx_a<RS, OpD>(c, um, ue, SW, tid, nr, T, pf, pb);
+        if (act) colx_a<RS, OpD>(c, um, yfr, SW, tid, nr, T, pf, pb);
         cluster_sync();
         if (act) {
-          colx_b<RS, OpD>(c, um, ue, SW, tid, nr, R, rank, T, pf, pb, bad);
+          colx_b<RS, OpD>(c, tid, nr, R, rank, ncta, T, pf, pb);
 #pragma unroll
           for (int r = 0; r < RS; ++r)
             if (r < nr) acc += I.hs * prod64(ug(r, tid), c.x[r]);
@@ -826,17 +787,24 @@ __global__ void __launch_bounds__(kThr, 1) fs1_cluster2d_kernel(Launch L) {
       // (I (x) K_f^(c)) Z by rows
       {
         ColX<RS, OpPlain<XF>> c;
-        if (act) colx_a<RS, OpPlain<XF>>(c, vm, ve, SW, tid, nr, T, xbf, xbb);
+        if (act) colx_a<RS, OpPlain<XF>>(c, vm, vfr, SW, tid, nr, T, xbf, xbb);
         cluster_sync();
         if (act) {
-          colx_b<RS, OpPlain<XF>>(c, vm, ve, SW, tid, nr, R, rank, T, xbf, xbb, bad);
+          colx_b<RS, OpPlain<XF>>(c, tid, nr, R, rank, ncta, T, xbf, xbb);
 #pragma unroll
-          for (int r = 0; r < RS; ++r)
-            if (r < nr) st6(um + r * SW + tid, ue + r * SW + tid, c.x[r], bad);
+          for (int s = 0; s < NSB; ++s) {
+            XF z[kSub];
+#pragma unroll
+            for (int k = 0; k < kSub; ++k) z[k] = s * kSub + k < nr ? c.x[s * kSub + k] : zero;
+            float x[kSub];
+            cfu[s * SW + tid] = to_block(z, x);
+#pragma unroll
+            for (int k = 0; k < kSub; ++k) um[(s * kSub + k) * SW + tid] = x[k];
+          }
         }
         __syncthreads();
         for (int r = warp; r < nr; r += kWarps)
-          row_dist<PF>(um + r * SW, ue + r * SW, vm + r * SW, ve + r * SW, lane, T, bad,
+          row_dist<PF>(um + r * SW, cfu + (r / kSub) * SW, lane, T,
                        [&](int slot, XF d) { acc += I.hf * prod64(ug(r, slot), d); });
       }
     }
@@ -853,13 +821,13 @@ __global__ void __launch_bounds__(kThr, 1) fs1_cluster2d_kernel(Launch L) {
     cluster_sync();
     if (rank == 0 && tid == 0) {
       double w = 0.0;
-      for (unsigned k = 0; k < kCS; ++k) w += dsm_ld_f64(dsm_addr(&s_w, k));
+      for (unsigned k = 0; k < ncta; ++k) w += dsm_ld_f64(dsm_addr(&s_w, k));
       PairResult res;
       res.w = status == FS1_ENUMERIC ? NAN : w;
       res.err = err;
       res.iters = ell;
       res.status = status;
-      res.pad = kCS;   // CTAs that shared the image
+      res.pad = (int)ncta;   // CTAs that shared the image
       L.results[pid] = res;
     }
     cluster_sync();   // s_w and the exchange buffers are reused by the next image
@@ -867,28 +835,27 @@ __global__ void __launch_bounds__(kThr, 1) fs1_cluster2d_kernel(Launch L) {
   cluster_sync();     // no CTA leaves while another may still read its shared memory
 }
 
-
 // ---------------------------------------------------------------------------
-// launch of one instantiation: persistent clusters of kCS CTAs, as many as
-// fit at once (at most one per image)
+// launch of one instantiation: persistent clusters of cs CTAs, as many as fit
+// at once (at most one per image)
 // ---------------------------------------------------------------------------
 template <int PF, int RS>
-cudaError_t prepare(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, cudaStream_t st) {
+cudaError_t prepare(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, int cs, cudaStream_t st) {
   auto kfn = fs1_cluster2d_kernel<PF, RS>;
   const size_t smem = smem_bytes(PF, RS);
-  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  cudaStreamIsCapturing(st, &cs);
-  if (cs == cudaStreamCaptureStatusNone) {
+  cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cst);
+  if (cst == cudaStreamCaptureStatusNone) {
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kfn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
   }
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = kCS;
+  attr[0].val.clusterDim.x = cs;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg = cudaLaunchConfig_t{};
-  cfg.gridDim = dim3(kCS);
+  cfg.gridDim = dim3(cs);
   cfg.blockDim = dim3(kThr);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
@@ -897,13 +864,13 @@ cudaError_t prepare(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, cudaStre
   return cudaSuccess;
 }
 
-// clusters of this instantiation that fit on the current device at once (0:
-// none, e.g. no GPC holds kCS of its CTAs)
+// clusters of cs CTAs of this instantiation that fit on the current device at
+// once (0: none)
 template <int PF, int RS>
-int max_clusters() {
+int max_clusters(int cs) {
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
-  if (prepare<PF, RS>(cfg, attr, nullptr) != cudaSuccess) {
+  if (prepare<PF, RS>(cfg, attr, cs, nullptr) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -916,12 +883,12 @@ int max_clusters() {
 }
 
 template <int PF, int RS>
-cudaError_t launch(const Launch& L, int clusters, cudaStream_t st) {
+cudaError_t launch(const Launch& L, int cs, int clusters, cudaStream_t st) {
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
-  cudaError_t e = prepare<PF, RS>(cfg, attr, st);
+  cudaError_t e = prepare<PF, RS>(cfg, attr, cs, st);
   if (e != cudaSuccess) return e;
-  cfg.gridDim = dim3(clusters * kCS);
+  cfg.gridDim = dim3(clusters * cs);
   return cudaLaunchKernelEx(&cfg, fs1_cluster2d_kernel<PF, RS>, L);
 }
 

@@ -4,10 +4,10 @@
 
 namespace fs1 {
 
-int c2d_max_clusters_p16r32() { return c2d::max_clusters<16, 32>(); }
+int c2d_max_clusters_p16r32(int cs) { return c2d::max_clusters<16, 32>(cs); }
 
-cudaError_t c2d_launch_p16r32(const c2d::Launch& L, int clusters, cudaStream_t st) {
-  return c2d::launch<16, 32>(L, clusters, st);
+cudaError_t c2d_launch_p16r32(const c2d::Launch& L, int cs, int clusters, cudaStream_t st) {
+  return c2d::launch<16, 32>(L, cs, clusters, st);
 }
 
 }  // namespace fs1

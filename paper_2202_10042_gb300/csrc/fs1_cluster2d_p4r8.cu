@@ -4,10 +4,10 @@
 
 namespace fs1 {
 
-int c2d_max_clusters_p4r8() { return c2d::max_clusters<4, 8>(); }
+int c2d_max_clusters_p4r8(int cs) { return c2d::max_clusters<4, 8>(cs); }
 
-cudaError_t c2d_launch_p4r8(const c2d::Launch& L, int clusters, cudaStream_t st) {
-  return c2d::launch<4, 8>(L, clusters, st);
+cudaError_t c2d_launch_p4r8(const c2d::Launch& L, int cs, int clusters, cudaStream_t st) {
+  return c2d::launch<4, 8>(L, cs, clusters, st);
 }
 
 }  // namespace fs1

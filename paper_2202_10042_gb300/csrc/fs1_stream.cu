@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(kThreads, 2) stream_step_kernel(StreamArgs A, 
     unsigned epoch = 0, xc = 0;
     int dec;
     exchange<OpPlain<XF>, XF>(L, tc, epoch, xc, c_from(af, e, XF{}), c_from(ab, e, XF{}), 0.f, kSE, tb, X, cf,
-                              cb, 0.0, dec, nullptr);
+                              cb, 0.f, 0.f, dec, nullptr, nullptr);
     cf = c_add(cf, c_mul(CF, c_mul(tb.dt[lane], tb.dw[warp])));
     cb = c_add(cb, c_mul(CB, c_mul(tb.dt[31 - lane], tb.dw[kWarps - 1 - warp])));
   }
@@ -518,8 +518,8 @@ __global__ void __launch_bounds__(kThreads, 1) stream_cost_kernel(StreamArgs A) 
     unsigned epoch = 0, xc = 0;
     int dec;
     exchange<OpD, XF>(L, tc, epoch, xc, DT{c_from(p, fv, XF{}), c_from(Aa, fv, XF{})},
-                      DT{c_from(s, fv, XF{}), c_from(Bb, fv, XF{})}, 0.f, kSE, tb, XD, dcf, dcb, 0.0, dec,
-                      nullptr);
+                      DT{c_from(s, fv, XF{}), c_from(Bb, fv, XF{})}, 0.f, kSE, tb, XD, dcf, dcb, 0.f, 0.f, dec,
+                      nullptr, nullptr);
     dcf = OpD::add(dcf, OpD::prop(A.dcar_f[ch], c_mul(tb.dt[lane], tb.dw[warp]), (float)(kSE * tid)));
     dcb = OpD::add(dcb, OpD::prop(A.dcar_b[ch], c_mul(tb.dt[31 - lane], tb.dw[kWarps - 1 - warp]),
                                   (float)(kSE * (kThreads - 1 - tid))));

@@ -25,9 +25,9 @@
 //            only global synchronisation of a half-step.
 // The aggregates of a half-step's output are formed while the output is
 // produced.  The marginal error of the while condition of Algorithm 1 (FP32
-// terms, summed as compensated FP32 pairs within warps and across warps; the
-// CTAs' pairs summed in FP64 in a fixed order) rides on the same exchange,
-// and every warp of every CTA takes the stop decision from the same FP64 sum.
+// terms, summed as compensated FP32 pairs within warps, across warps and
+// across CTAs in a fixed order) rides on the same exchange, and every warp of
+// every CTA takes the stop decision from the same compensated sum.
 //
 // Variants (template parameters):
 //   V = double, C = double : plain FS-1 (Algorithm 1 as written), FP64.
@@ -101,7 +101,7 @@ struct XchgSmem {
   T wf[2][kWarps], wb[2][kWarps];
   float eh[2][kWarps], el[2][kWarps];
   T pf[kWarps], pb[kWarps];             // partial team carries (one per warp)
-  double e64;                           // team sum of the error (or cost) partials, FP64
+  float ph[kWarps], pl[kWarps];
   int ok;
   SlotPayload<T> stage[kMaxTeamCtas];   // validated team slots
 };
@@ -214,8 +214,7 @@ __device__ __forceinline__ bool warp_scan_narrow(XF af, XF ab, const DecayTables
 // [56, 64); a word left from an earlier exchange of the same parity is at
 // least two epochs old, so its tag differs.
 //   w0: frac(f) 23 | exp(f) 16 | exp(b) 16
-//   w1: frac(b) 23 | high part of the error partial (FP32 without its sign) 31
-//   w2: low part of the error partial (FP32) 32
+//   w1: frac(b) 23 | error partial (FP32 without its sign) 31
 // Exponents must fit 16 bits; pairs whose potentials could exceed that use
 // the generic slots (decided per pair from c N).
 // ---------------------------------------------------------------------------
@@ -246,11 +245,11 @@ __device__ __forceinline__ void publish(const TeamLaunch& L, const TeamCtx& tc, 
       xf_bits(f, ff, fe);
       xf_bits(b, bf, be);
       const unsigned long long tag = (unsigned long long)(epoch & 0xFFu) << 56;
+      const float ev = eh + el;
       const unsigned long long w0 = tag | ff | ((unsigned long long)fe << 23) | ((unsigned long long)be << 39);
       const unsigned long long w1 =
-          tag | bf | ((unsigned long long)(__float_as_uint(eh) & 0x7FFFFFFFu) << 23);
+          tag | bf | ((unsigned long long)(__float_as_uint(ev) & 0x7FFFFFFFu) << 23);
       st_relaxed_v2(w, w0, w1);
-      st_relaxed_u64(w + 2, tag | __float_as_uint(el));
       return;
     }
   }
@@ -265,13 +264,12 @@ __device__ __forceinline__ bool try_read(const TeamLaunch& L, const TeamCtx& tc,
       const unsigned long long* w = L.cslots + slot * kCompactWords;
       unsigned long long w0, w1;
       ld_relaxed_v2(w, w0, w1);
-      const unsigned long long w2 = ld_relaxed_u64(w + 2);
       const unsigned tg = epoch & 0xFFu;
-      if ((unsigned)(w0 >> 56) != tg || (unsigned)(w1 >> 56) != tg || (unsigned)(w2 >> 56) != tg) return false;
+      if ((unsigned)(w0 >> 56) != tg || (unsigned)(w1 >> 56) != tg) return false;
       out.f = xf_unbits((unsigned)(w0 & 0x7FFFFFu), (unsigned)(w0 >> 23));
       out.b = xf_unbits((unsigned)(w1 & 0x7FFFFFu), (unsigned)(w0 >> 39));
       out.eh = __uint_as_float((unsigned)(w1 >> 23) & 0x7FFFFFFFu);
-      out.el = __uint_as_float((unsigned)w2);
+      out.el = 0.f;
       return true;
     }
   }
@@ -323,17 +321,16 @@ __device__ __forceinline__ void hw_sum_df(float& hi, float& lo) {
 //      16 warps each reduce 16 staged slots into partial team carries of this
 //      CTA (decay-weighted by the lam^{S k} table), and after a second block
 //      barrier every warp sums the 16 partials.
-// The partials are summed as compensated FP32 pairs within a CTA; the team
-// sum of the CTA pairs is FP64 (warp 0, in slot order) and every warp takes
-// the stop decision from it, so all warps and all CTAs agree.  Returns false when a bounded wait gave
+// The stop decision is taken by every warp from the same compensated FP32 sum,
+// so all warps and all CTAs agree.  Returns false when a bounded wait gave
 // up.  decision: 0 continue, 1 error <= tol, 2 error not finite.
 // ---------------------------------------------------------------------------
 template <class Op, class C, class EV>
 __device__ __forceinline__ bool exchange(const TeamLaunch& L, const TeamCtx& tc, unsigned& epoch,
                                          unsigned& xc, typename Op::T af, typename Op::T ab, EV err_part,
                                          int Eeff, const DecayTables<C>& tb, XchgSmem<typename Op::T>& X,
-                                         typename Op::T& cf, typename Op::T& cb, double tol, int& decision,
-                                         double* err_out, bool compact = false) {
+                                         typename Op::T& cf, typename Op::T& cb, float tol_h, float tol_l,
+                                         int& decision, float* err_h, float* err_l, bool compact = false) {
   using T = typename Op::T;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int T_ = tc.T, rank = tc.rank;
@@ -365,7 +362,6 @@ __device__ __forceinline__ bool exchange(const TeamLaunch& L, const TeamCtx& tc,
   float tl = lane < kWarps ? X.el[par][lane] : 0.f;
   warp_sum_df(th, tl);
   T tcf = Op::zero(), tcb = Op::zero();
-  double e64 = 0.0;
   if (T_ > 1) {
     ++epoch;
     if (warp == 0) {
@@ -407,33 +403,38 @@ __device__ __forceinline__ bool exchange(const TeamLaunch& L, const TeamCtx& tc,
     const float Sf = (float)(kThreads * Eeff);
     const int j = 16 * warp + (lane & 15);
     T term = Op::zero();
+    float ph = 0.f, pl = 0.f;
     if (j < T_) {
       const int k = lane < 16 ? rank - 1 - j : j - rank - 1;
       if (k >= 0) term = Op::prop(lane < 16 ? X.stage[j].f : X.stage[j].b, tb.dT[k], Sf * (float)k);
+      if (lane < 16) {
+        ph = X.stage[j].eh;
+        pl = X.stage[j].el;
+      }
     }
     const T part = hw_sum(term);
-    if (lane == 0) X.pf[warp] = part;
-    if (lane == 16) X.pb[warp] = part;
-    // the team sum of the CTAs' (hi, lo) partials in FP64: warp 0, every lane
-    // in slot order, then a fixed shuffle tree (the same in every CTA)
-    if (err_out != nullptr && warp == 0) {
-      double e = 0.0;
-      for (int i = lane; i < T_; i += 32) e += (double)X.stage[i].eh + (double)X.stage[i].el;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-      if (lane == 0) X.e64 = e;
+    hw_sum_df(ph, pl);
+    if (lane == 0) {
+      X.pf[warp] = part;
+      X.ph[warp] = ph;
+      X.pl[warp] = pl;
     }
+    if (lane == 16) X.pb[warp] = part;
     __syncthreads();
     const T q = lane < 16 ? X.pf[lane] : X.pb[lane - 16];
     const T tot = hw_sum(q);
     tcf = Op::idx(tot, 0);
     tcb = Op::idx(tot, 16);
-    if (err_out != nullptr) e64 = X.e64;
+    th = lane < 16 ? X.ph[lane] : 0.f;
+    tl = lane < 16 ? X.pl[lane] : 0.f;
+    warp_sum_df(th, tl);
   }
-  // ---- decision (FP64, identical in every warp) and carries
-  if (T_ == 1) e64 = (double)th + (double)tl;
-  decision = !isfinite(e64) ? 2 : (e64 <= tol ? 1 : 0);
-  if (err_out) *err_out = e64;
+  // ---- decision (compensated FP32, identical in every warp) and carries
+  decision = !(isfinite(th) && isfinite(tl)) ? 2 : (((th - tol_h) + (tl - tol_l)) <= 0.f ? 1 : 0);
+  if (err_h) {
+    *err_h = th;
+    *err_l = tl;
+  }
   const T wcf = Op::fwd(tcf, pf, tb.dw[warp], Wf * (float)warp);
   cf = Op::fwd(wcf, excl_f, tb.dt[lane], (float)(Eeff * lane));
   const int wr = kWarps - 1 - warp;
@@ -683,14 +684,16 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
       });
       int dec;
       if (!exchange<OpP, C>(L, tc, epoch, xc, c_from(af, fu, C{}), c_from(ab, fu, C{}), (V)0, Eeff, tb, XP,
-                            cf, cb, 0.0, dec, nullptr, compact))
+                            cf, cb, 0.f, 0.f, dec, nullptr, nullptr, compact))
         goto timed_out;
     }
 
     {
       int64_t ell = 0;
       int status = FS1_OK;
-      double err_last = 0.0;
+      float eh_last = 0.f, el_last = 0.f;
+      const float tol_h = (float)P.tol;
+      const float tol_l = (float)(P.tol - (double)tol_h);
       for (;;) {
         // ---------------- v-half: y = K^T u, v_new = b / y, marginal error
         {
@@ -732,7 +735,7 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
           }
           int dec;
           if (!exchange<OpP, C>(L, tc, epoch, xc, c_from(af, fz, C{}), c_from(ab, fz, C{}), ep, Eeff, tb, XP,
-                                cf, cb, P.tol, dec, &err_last, compact))
+                                cf, cb, tol_h, tol_l, dec, &eh_last, &el_last, compact))
             goto timed_out;
           if (dec != 0 || ell >= P.itr_max) {
             if (dec == 2) status = FS1_ENUMERIC;
@@ -775,7 +778,7 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
           hu = (EXT && zmax > 0) ? fz + fexp((float)zmax) : kZeroExp;
           int dec;
           if (!exchange<OpP, C>(L, tc, epoch, xc, c_from(af, fz, C{}), c_from(ab, fz, C{}), (V)0, Eeff, tb,
-                                XP, cf, cb, 0.0, dec, nullptr, compact))
+                                XP, cf, cb, 0.f, 0.f, dec, nullptr, nullptr, compact))
             goto timed_out;
         }
         ++ell;
@@ -807,7 +810,8 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
         DT ab{c_from(s, fv, C{}), c_from(B, fv, C{})};
         DT dcf, dcb;
         int dec;
-        if (!exchange<OpD, C>(L, tc, epoch, xc, af, ab, (V)0, Eeff, tb, XD, dcf, dcb, 0.0, dec, nullptr))
+        if (!exchange<OpD, C>(L, tc, epoch, xc, af, ab, (V)0, Eeff, tb, XD, dcf, dcb, 0.f, 0.f, dec, nullptr,
+                              nullptr))
           goto timed_out;
         int F = 0;
         if (EXT) {
@@ -832,11 +836,12 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
             if (k < ne) wpart += ldexp((double)xu[k] * (double)(AA + sm_v[k * kThreads + tid]), fu + F);
           }
         wpart *= P.h_fast;
-        double wsum = 0.0;
+        float wh = 0.f, wl = 0.f;
         PT z0 = OpP::zero(), c0, c1;
-        if (!exchange<OpP, C>(L, tc, epoch, xc, z0, z0, wpart, Eeff, tb, XP, c0, c1, 0.0, dec, &wsum))
+        if (!exchange<OpP, C>(L, tc, epoch, xc, z0, z0, wpart, Eeff, tb, XP, c0, c1, 0.f, 0.f, dec, &wh,
+                              &wl))
           goto timed_out;
-        wpart = wsum;
+        wpart = (double)wh + (double)wl;
       }
       // optional potentials out
       if (P.f_out != nullptr)
@@ -848,6 +853,7 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
         for (int k = 0; k < E; ++k)
           if (k < ne) P.g_out[g0 + k] = log((double)xn[k]) + (double)fv * 0.6931471805599453;
       if (rank == 0 && tid == 0) {
+        const double err_last = (double)eh_last + (double)el_last;
         PairResult R;
         R.w = status == FS1_OK ? wpart : NAN;
         R.err = err_last;

