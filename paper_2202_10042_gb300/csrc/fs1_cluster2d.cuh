@@ -152,6 +152,38 @@ __device__ __forceinline__ double dsm_ld_f64(unsigned addr) {
   return v;
 }
 
+// one-dimensional bulk copy global -> shared (TMA), completion counted on an
+// mbarrier of this CTA; both addresses 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void mbar_init(unsigned long long* mbar) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(mbar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* mbar) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const unsigned m = (unsigned)__cvta_generic_to_shared(mbar);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(m), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d),
+               "l"(src), "r"(bytes), "r"(m)
+               : "memory");
+}
+// wait for phase `parity` of the mbarrier to complete; gives up (false)
+// after `cap` polls
+__device__ __forceinline__ bool mbar_wait(unsigned long long* mbar, unsigned parity, long long cap) {
+  const unsigned m = (unsigned)__cvta_generic_to_shared(mbar);
+  for (long long i = 0; i < cap; ++i) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(m), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
 __device__ __forceinline__ float load_in(const void* p, int64_t i, int f32) {
   return f32 ? reinterpret_cast<const float*>(p)[i] : (float)reinterpret_cast<const double*>(p)[i];
 }
@@ -173,6 +205,16 @@ __device__ __forceinline__ double prod64(XF u, XF d) {
 
 // N extended-range values as FP32 numbers in one frame (returned), the
 // largest in [0.5, 1); zeros stay zero
+// frames are stored as 16-bit integers (-32768: an all-zero block); a frame
+// beyond +-32767 sets `bad` (the image is then solved by the grid kernel)
+constexpr int kF16Zero = -32768;
+__device__ __forceinline__ int fr16(short f) { return f == (short)kF16Zero ? kZeroExp : (int)f; }
+__device__ __forceinline__ short to16(int f, bool& bad) {
+  if (f <= kZeroExp / 2) return (short)kF16Zero;
+  bad |= f > 32767 || f < -32767;
+  return (short)max(-32767, min(32767, f));
+}
+
 template <int N>
 __device__ __forceinline__ int to_block(const XF (&v)[N], float (&x)[N]) {
   int em = kZeroExp;
@@ -193,8 +235,8 @@ __device__ __forceinline__ int to_block(const XF (&v)[N], float (&x)[N]) {
 // om may alias im.
 // ---------------------------------------------------------------------------
 template <int PF>
-__device__ __forceinline__ void row_pass_f(const float* im, const int* icf, float* om, int* orf, int lane,
-                                           const Tabs& T) {
+__device__ __forceinline__ void row_pass_f(const float* im, const short* icf, float* om, short* orf, int lane,
+                                           const Tabs& T, bool& bad) {
   constexpr int SUB = PF < kSub ? PF : kSub;
   constexpr int NSB = PF / SUB;
   float x[PF];
@@ -207,7 +249,7 @@ __device__ __forceinline__ void row_pass_f(const float* im, const int* icf, floa
     for (int k = 0; k < SUB; ++k) {
       const int slot = (s * SUB + k) * 32 + lane;
       x[s * SUB + k] = im[slot];
-      f[k] = icf[slot];
+      f[k] = fr16(icf[slot]);
       emax = max(emax, f[k]);
     }
     fe[s] = emax;
@@ -266,7 +308,7 @@ __device__ __forceinline__ void row_pass_f(const float* im, const int* icf, floa
       p = fmaf(lam, p, x[s * SUB + k] * sc);
       om[(s * SUB + k) * 32 + lane] = p + t[k];
     }
-    orf[lane * NSB + s] = F;
+    orf[lane * NSB + s] = to16(F, bad);
     C = c_add(c_mul(C, T.subf[SUB]), af[s]);   // forward carry into the next sub-block
   }
 }
@@ -275,12 +317,12 @@ __device__ __forceinline__ void row_pass_f(const float* im, const int* icf, floa
 // point k of the row, sum_j lam^{|k-j|} |k-j| x_j, handed to acc(slot,
 // value).  Input with column frames as row_pass_f.
 template <int PF, class Acc>
-__device__ __forceinline__ void row_dist(const float* im, const int* icf, int lane, const Tabs& T, Acc acc) {
+__device__ __forceinline__ void row_dist(const float* im, const short* icf, int lane, const Tabs& T, Acc acc) {
   using Op = OpDist<XF>;
   using P = PairC<XF>;
   XF x[PF];
 #pragma unroll
-  for (int k = 0; k < PF; ++k) x[k] = XF{im[k * 32 + lane], icf[k * 32 + lane]};
+  for (int k = 0; k < PF; ++k) x[k] = XF{im[k * 32 + lane], fr16(icf[k * 32 + lane])};
   const XF lam = T.xlamf;
   const XF z = XF{0.f, kZeroExp};
   XF p = z, A = z, s = z, B = z;
@@ -535,8 +577,8 @@ __device__ __forceinline__ void colx_b(ColX<RS, Op>& c, int t, int nr, int R, un
 
 // bytes of dynamic shared memory of an instantiation
 __host__ __device__ constexpr size_t smem_bytes(int PF, int RS) {
-  return (size_t)RS * 32 * PF * 8 + (size_t)4 * 32 * PF * 8 + (size_t)2 * (RS / kSub) * 32 * PF * 4 +
-         (size_t)RS * 32 * (PF < kSub ? 1 : PF / kSub) * 4;
+  return (size_t)RS * 32 * PF * 8 + (size_t)4 * 32 * PF * 8 + (size_t)RS * 32 * PF * 4 +
+         (size_t)2 * (RS / kSub) * 32 * PF * 2 + (size_t)RS * 32 * (PF < kSub ? 1 : PF / kSub) * 2;
 }
 
 // ---------------------------------------------------------------------------
@@ -554,10 +596,13 @@ __global__ void __launch_bounds__(kThr, 1) fs1_cluster2d_kernel(Launch L) {
   float* const vm = um + RS * SW;                          // [RS][SW] v
   XF* const xbf = reinterpret_cast<XF*>(vm + RS * SW);    // [2][SW] forward aggregates by half-step
   XF* const xbb = xbf + 2 * SW;                            // [2][SW] backward aggregates
-  int* const cfu = reinterpret_cast<int*>(xbb + 2 * SW);  // [NSB][SW] column frames of u
-  int* const cfv = cfu + NSB * SW;                         // [NSB][SW] column frames of v
-  int* const rfy = cfv + NSB * SW;                         // [RS][32][NSF] row frames of Y
+  float* const sm_mass = reinterpret_cast<float*>(xbb + 2 * SW);   // [RS][SW] a or b of the half-step
+  short* const cfu = reinterpret_cast<short*>(sm_mass + RS * SW);  // [NSB][SW] column frames of u
+  short* const cfv = cfu + NSB * SW;                               // [NSB][SW] column frames of v
+  short* const rfy = cfv + NSB * SW;                               // [RS][32][NSF] row frames of Y
   __shared__ Tabs T;
+  __shared__ __align__(8) unsigned long long s_mbar;   // completion of the mass copy
+  __shared__ int s_flags;   // bit 0: a mass copy did not complete in time; bit 1: a frame out of range
   __shared__ __align__(16) float s_err[4];   // this CTA's error partial (hi, lo) and range flag
   __shared__ float s_red[2 * kWarps];
   __shared__ double s_wred[kWarps];
@@ -569,9 +614,15 @@ __global__ void __launch_bounds__(kThr, 1) fs1_cluster2d_kernel(Launch L) {
   const bool act = tid < SW;                 // a column-pass thread
   const XF zero = XF{0.f, kZeroExp};
   // frames of (row r, slot tid): Y by rows, u and v by column blocks
-  auto yfr = [&](int r) { return rfy[(r * 32 + (tid & 31)) * NSF + (tid >> 5) / SUBF]; };
-  auto ufr = [&](int r) { return cfu[(r / kSub) * SW + tid]; };
-  auto vfr = [&](int r) { return cfv[(r / kSub) * SW + tid]; };
+  auto yfr = [&](int r) { return fr16(rfy[(r * 32 + (tid & 31)) * NSF + (tid >> 5) / SUBF]); };
+  auto ufr = [&](int r) { return fr16(cfu[(r / kSub) * SW + tid]); };
+  auto vfr = [&](int r) { return fr16(cfv[(r / kSub) * SW + tid]); };
+  if (tid == 0) {
+    mbar_init(&s_mbar);
+    s_flags = 0;
+  }
+  __syncthreads();
+  unsigned mphase = 0;   // phase of s_mbar the next copy completes
 
   for (;;) {
     if (rank == 0 && tid == 0) s_img = atomicAdd(L.next, 1);
@@ -592,7 +643,9 @@ __global__ void __launch_bounds__(kThr, 1) fs1_cluster2d_kernel(Launch L) {
     const float* const bw = I.bw + (size_t)row0 * SW;
     const double tol = I.tol;
     const int64_t itr_max = I.itr_max;
+    bool bad = false;   // a frame of this thread's blocks left the 16-bit range
     if (tid == 0) {
+      s_flags = 0;
       T.lamf = (float)exp(-I.cf);
       T.lams = (float)exp(-I.cs);
       T.xlamf = c_decay(1.0, I.cf, XF{});
@@ -628,11 +681,11 @@ __global__ void __launch_bounds__(kThr, 1) fs1_cluster2d_kernel(Launch L) {
           }
         }
         float x[kSub];
-        cfu[s * SW + tid] = to_block(uv, x);
+        cfu[s * SW + tid] = to16(to_block(uv, x), bad);
 #pragma unroll
         for (int k = 0; k < kSub; ++k) um[(s * kSub + k) * SW + tid] = x[k];
         if (all) {
-          cfv[s * SW + tid] = to_block(vv, x);
+          cfv[s * SW + tid] = to16(to_block(vv, x), bad);
 #pragma unroll
           for (int k = 0; k < kSub; ++k) vm[(s * kSub + k) * SW + tid] = x[k];
         }
@@ -640,15 +693,28 @@ __global__ void __launch_bounds__(kThr, 1) fs1_cluster2d_kernel(Launch L) {
     };
     init_state(true);
     __syncthreads();
+    if (tid == 0) asm volatile("fence.proxy.async.global;" ::: "memory");   // aw, bw reach the bulk copies
+    // this CTA's rows of a (u-half) or b (v-half) into sm_mass with one bulk
+    // copy, issued before the row pass and waited for before the epilogue
+    const unsigned mass_bytes = (unsigned)(nr * SW * sizeof(float));
+    auto stage_mass = [&](const float* src) {
+      if (tid == 0 && mass_bytes > 0) bulk_load(sm_mass, src, mass_bytes, &s_mbar);
+    };
+    auto wait_mass = [&]() {
+      if (mass_bytes > 0) {
+        if (!mbar_wait(&s_mbar, mphase, 1ll << 26)) atomicOr(&s_flags, 1);
+        mphase ^= 1u;
+      }
+    };
 
     // row pass over this CTA's rows: (im, column frames icf) -> (um, rfy)
-    auto row_pass = [&](const float* im, const int* icf) {
+    auto row_pass = [&](const float* im, const short* icf) {
       for (int r = warp; r < nr; r += kWarps)
-        row_pass_f<PF>(im + r * SW, icf + (r / kSub) * SW, um + r * SW, rfy + r * 32 * NSF, lane, T);
+        row_pass_f<PF>(im + r * SW, icf + (r / kSub) * SW, um + r * SW, rfy + r * 32 * NSF, lane, T, bad);
       __syncthreads();
     };
     // m_r / y_r of the rows of this slot, block by block, into (xm, cf)
-    auto divide_into = [&](const ColF<RS>& c, const float* mw, float* xm, int* cf) {
+    auto divide_into = [&](const ColF<RS>& c, const float* mw, float* xm, short* cf) {
 #pragma unroll
       for (int s = 0; s < NSB; ++s) {
         XF z[kSub];
@@ -663,20 +729,22 @@ __global__ void __launch_bounds__(kThr, 1) fs1_cluster2d_kernel(Launch L) {
           }
         }
         float x[kSub];
-        cf[s * SW + tid] = to_block(z, x);
+        cf[s * SW + tid] = to16(to_block(z, x), bad);
 #pragma unroll
         for (int k = 0; k < kSub; ++k) xm[(s * kSub + k) * SW + tid] = x[k];
       }
     };
     // u-half: Y = (I (x) K_f) v, u = a / ((K_s (x) I) Y)
     auto u_half = [&]() {
+      stage_mass(aw);
       row_pass(vm, cfv);
       ColF<RS> c;
       if (act) colf_a<RS>(c, um, yfr, SW, tid, nr, T, xbf + SW, xbb + SW);
       cluster_sync();
+      wait_mass();
       if (act) {
         colf_b<RS>(c, tid, nr, rank, ncta, T, xbf + SW, xbb + SW);
-        divide_into(c, aw, um, cfu);
+        divide_into(c, sm_mass, um, cfu);
       }
       __syncthreads();
     };
@@ -685,12 +753,14 @@ __global__ void __launch_bounds__(kThr, 1) fs1_cluster2d_kernel(Launch L) {
     double err = 0.0;
     for (;; ++ell) {
       // ---- v-half: Y = (I (x) K_f) u over u, y = (K_s (x) I) Y, error, v = b / y
+      stage_mass(bw);
       row_pass(um, cfu);
       bool stop;
       {
         ColF<RS> c;
         if (act) colf_a<RS>(c, um, yfr, SW, tid, nr, T, xbf, xbb);
         cluster_sync();
+        wait_mass();
         float eh = 0.f, el = 0.f;
         if (act) {
           colf_b<RS>(c, tid, nr, rank, ncta, T, xbf, xbb);
@@ -699,7 +769,7 @@ __global__ void __launch_bounds__(kThr, 1) fs1_cluster2d_kernel(Launch L) {
             if (r < nr) {
               const XF vo = XF{vm[r * SW + tid], vfr(r)};
               const float pv = c_to(c_mul(vo, c.get(r)), 0);   // v (K^T u) at the point
-              df_add(eh, el, fabsf(pv - bw[r * SW + tid]), 0.f);
+              df_add(eh, el, fabsf(pv - sm_mass[r * SW + tid]), 0.f);
             }
           }
         }
@@ -730,7 +800,7 @@ __global__ void __launch_bounds__(kThr, 1) fs1_cluster2d_kernel(Launch L) {
         __syncthreads();
         err = s_dec;
         stop = !isfinite(err) || err <= tol || ell >= itr_max;
-        if (!stop && act) divide_into(c, bw, vm, cfv);
+        if (!stop && act) divide_into(c, sm_mass, vm, cfv);
       }
       __syncthreads();
       // At the stop, u^l is rebuilt: the initial u when no iteration ran,
@@ -747,7 +817,7 @@ __global__ void __launch_bounds__(kThr, 1) fs1_cluster2d_kernel(Launch L) {
       if (stop) break;
     }
     cluster_sync();   // every CTA is done with the exchange buffers
-    const int status = !isfinite(err) ? FS1_ENUMERIC : (err <= tol ? FS1_OK : FS1_ENOTCONV);
+    const int status = !isfinite(err) ? FS1_ENUMERIC : (err <= tol ? FS1_OK : FS1_ENOTCONV);   // cluster-uniform
     // ---- optional potentials out
     if ((I.f_out || I.g_out) && act) {
       const int j = (tid & 31) * PF + (tid >> 5);
@@ -763,7 +833,7 @@ __global__ void __launch_bounds__(kThr, 1) fs1_cluster2d_kernel(Launch L) {
       float* const us = I.us + (size_t)row0 * SW;
       int* const usf = I.usf + (size_t)rank * NSB * SW;
       for (int idx = tid; idx < nr * SW; idx += kThr) us[idx] = um[idx];
-      for (int idx = tid; idx < NSB * SW; idx += kThr) usf[idx] = cfu[idx];
+      for (int idx = tid; idx < NSB * SW; idx += kThr) usf[idx] = fr16(cfu[idx]);
       __syncthreads();
       auto ug = [&](int r, int slot) { return XF{us[r * SW + slot], usf[(r / kSub) * SW + slot]}; };
       // slow axis: Z = (I (x) K_f) v by rows, then (K_s^(c) (x) I) Z by columns
@@ -797,7 +867,7 @@ __global__ void __launch_bounds__(kThr, 1) fs1_cluster2d_kernel(Launch L) {
 #pragma unroll
             for (int k = 0; k < kSub; ++k) z[k] = s * kSub + k < nr ? c.x[s * kSub + k] : zero;
             float x[kSub];
-            cfu[s * SW + tid] = to_block(z, x);
+            cfu[s * SW + tid] = to16(to_block(z, x), bad);
 #pragma unroll
             for (int k = 0; k < kSub; ++k) um[(s * kSub + k) * SW + tid] = x[k];
           }
@@ -812,6 +882,7 @@ __global__ void __launch_bounds__(kThr, 1) fs1_cluster2d_kernel(Launch L) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) s_wred[warp] = acc;
+    if (bad) atomicOr(&s_flags, 2);
     __syncthreads();
     if (tid == 0) {
       double w = 0.0;
@@ -821,12 +892,17 @@ __global__ void __launch_bounds__(kThr, 1) fs1_cluster2d_kernel(Launch L) {
     cluster_sync();
     if (rank == 0 && tid == 0) {
       double w = 0.0;
-      for (unsigned k = 0; k < ncta; ++k) w += dsm_ld_f64(dsm_addr(&s_w, k));
+      int fl = 0;   // flags of every CTA
+      for (unsigned k = 0; k < ncta; ++k) {
+        w += dsm_ld_f64(dsm_addr(&s_w, k));
+        fl |= dsm_ld_s32(dsm_addr(&s_flags, k));
+      }
       PairResult res;
-      res.w = status == FS1_ENUMERIC ? NAN : w;
+      res.w = status == FS1_ENUMERIC || fl ? NAN : w;
       res.err = err;
       res.iters = ell;
-      res.status = status;
+      // a late copy fails the image; a frame out of range sends it to the grid kernel
+      res.status = (fl & 1) ? FS1_ETIMEOUT : ((fl & 2) ? FS1_EUNSUPPORTED : status);
       res.pad = (int)ncta;   // CTAs that shared the image
       L.results[pid] = res;
     }
