@@ -385,7 +385,10 @@ struct ColF {
   __device__ __forceinline__ XF get(int r) const { return XF{y[r], fe[r / kSub]}; }
 };
 
-template <int RS, class FR>
+// MASK: rows past nr are identity steps (decay 1).  Without it they decay as
+// real rows; that is exact when every CTA with a later CTA holding rows has
+// all RS rows (R = RS): the rows past nr then lie after the image's last row.
+template <int RS, bool MASK, class FR>
 __device__ __forceinline__ void colf_a(ColF<RS>& c, const float* ym, FR fr, int SW, int t, int nr, const Tabs& T,
                                        XF* pubf, XF* pubb) {
   constexpr int NSB = ColF<RS>::NSB;
@@ -407,18 +410,18 @@ __device__ __forceinline__ void colf_a(ColF<RS>& c, const float* ym, FR fr, int 
 #pragma unroll
     for (int k = 0; k < kSub; ++k) {
       c.y[s * kSub + k] *= pow2f(f[k] - emax);
-      rr = fmaf(s * kSub + k < nr ? lam : 1.f, rr, c.y[s * kSub + k]);
+      rr = fmaf(!MASK || s * kSub + k < nr ? lam : 1.f, rr, c.y[s * kSub + k]);
     }
 #pragma unroll
-    for (int k = kSub - 1; k >= 0; --k) qq = (s * kSub + k < nr ? lam : 1.f) * (qq + c.y[s * kSub + k]);
+    for (int k = kSub - 1; k >= 0; --k) qq = (!MASK || s * kSub + k < nr ? lam : 1.f) * (qq + c.y[s * kSub + k]);
     c.af[s] = xf_norm(rr, emax);
     c.ab[s] = xf_norm(qq, emax);
-    const int len = max(0, min(kSub, nr - s * kSub));
+    const int len = MASK ? max(0, min(kSub, nr - s * kSub)) : kSub;
     A = c_add(c_mul(A, T.subs[len]), c.af[s]);
   }
 #pragma unroll
   for (int s = NSB - 1; s >= 0; --s) {
-    const int len = max(0, min(kSub, nr - s * kSub));
+    const int len = MASK ? max(0, min(kSub, nr - s * kSub)) : kSub;
     B = c_add(c.ab[s], c_mul(B, T.subs[len]));
   }
   pubf[t] = A;
@@ -452,7 +455,7 @@ __device__ __forceinline__ void col_carries(const XF* pubf, const XF* pubb, int 
   }
 }
 
-template <int RS>
+template <int RS, bool MASK>
 __device__ __forceinline__ void colf_b(ColF<RS>& c, int t, int nr, unsigned rank, unsigned ncta, const Tabs& T,
                                        const XF* pubf, const XF* pubb) {
   constexpr int NSB = ColF<RS>::NSB;
@@ -463,7 +466,7 @@ __device__ __forceinline__ void colf_b(ColF<RS>& c, int t, int nr, unsigned rank
   Ds[NSB - 1] = D;
 #pragma unroll
   for (int s = NSB - 2; s >= 0; --s) {
-    const int len = max(0, min(kSub, nr - (s + 1) * kSub));
+    const int len = MASK ? max(0, min(kSub, nr - (s + 1) * kSub)) : kSub;
     Ds[s] = c_add(c_mul(Ds[s + 1], T.subs[len]), c.ab[s + 1]);
   }
 #pragma unroll
@@ -475,16 +478,16 @@ __device__ __forceinline__ void colf_b(ColF<RS>& c, int t, int nr, unsigned rank
 #pragma unroll
     for (int k = kSub - 1; k >= 0; --k) {
       tb[k] = sb;
-      sb = (s * kSub + k < nr ? lam : 1.f) * fmaf(c.y[s * kSub + k], sc, sb);
+      sb = (!MASK || s * kSub + k < nr ? lam : 1.f) * fmaf(c.y[s * kSub + k], sc, sb);
     }
     float p = c_to(C, F);
 #pragma unroll
     for (int k = 0; k < kSub; ++k) {
-      p = fmaf(s * kSub + k < nr ? lam : 1.f, p, c.y[s * kSub + k] * sc);
+      p = fmaf(!MASK || s * kSub + k < nr ? lam : 1.f, p, c.y[s * kSub + k] * sc);
       c.y[s * kSub + k] = p + tb[k];
     }
     c.fe[s] = F;
-    const int len = max(0, min(kSub, nr - s * kSub));
+    const int len = MASK ? max(0, min(kSub, nr - s * kSub)) : kSub;
     C = c_add(c_mul(C, T.subs[len]), c.af[s]);
   }
 }
@@ -644,6 +647,7 @@ __global__ void __launch_bounds__(kThr, 1) fs1_cluster2d_kernel(Launch L) {
     const double tol = I.tol;
     const int64_t itr_max = I.itr_max;
     bool bad = false;   // a frame of this thread's blocks left the 16-bit range
+    const bool full = R == RS;   // column scans without identity steps (see colf_a)
     if (tid == 0) {
       s_flags = 0;
       T.lamf = (float)exp(-I.cf);
@@ -739,11 +743,15 @@ __global__ void __launch_bounds__(kThr, 1) fs1_cluster2d_kernel(Launch L) {
       stage_mass(aw);
       row_pass(vm, cfv);
       ColF<RS> c;
-      if (act) colf_a<RS>(c, um, yfr, SW, tid, nr, T, xbf + SW, xbb + SW);
+      if (act) {
+        if (full) colf_a<RS, false>(c, um, yfr, SW, tid, nr, T, xbf + SW, xbb + SW);
+        else colf_a<RS, true>(c, um, yfr, SW, tid, nr, T, xbf + SW, xbb + SW);
+      }
       cluster_sync();
       wait_mass();
       if (act) {
-        colf_b<RS>(c, tid, nr, rank, ncta, T, xbf + SW, xbb + SW);
+        if (full) colf_b<RS, false>(c, tid, nr, rank, ncta, T, xbf + SW, xbb + SW);
+        else colf_b<RS, true>(c, tid, nr, rank, ncta, T, xbf + SW, xbb + SW);
         divide_into(c, sm_mass, um, cfu);
       }
       __syncthreads();
@@ -758,12 +766,16 @@ __global__ void __launch_bounds__(kThr, 1) fs1_cluster2d_kernel(Launch L) {
       bool stop;
       {
         ColF<RS> c;
-        if (act) colf_a<RS>(c, um, yfr, SW, tid, nr, T, xbf, xbb);
+        if (act) {
+          if (full) colf_a<RS, false>(c, um, yfr, SW, tid, nr, T, xbf, xbb);
+          else colf_a<RS, true>(c, um, yfr, SW, tid, nr, T, xbf, xbb);
+        }
         cluster_sync();
         wait_mass();
         float eh = 0.f, el = 0.f;
         if (act) {
-          colf_b<RS>(c, tid, nr, rank, ncta, T, xbf, xbb);
+          if (full) colf_b<RS, false>(c, tid, nr, rank, ncta, T, xbf, xbb);
+          else colf_b<RS, true>(c, tid, nr, rank, ncta, T, xbf, xbb);
 #pragma unroll
           for (int r = 0; r < RS; ++r) {
             if (r < nr) {

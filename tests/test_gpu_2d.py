@@ -148,3 +148,27 @@ def test_2d_side_above_limit_unsupported(env):
     a2, b2 = _rand2d(3, 1025, 4)
     w, infos = _solve(env, [(a2, b2, (0.25, 1 / 1025), 0.05, 0.0, 5)])
     assert infos[0].status == fs1.FS1_EUNSUPPORTED
+
+
+def test_workload4_full_length_against_stored_oracle(env):
+    """Workload 4 to its own stop (tol 1e-6, cap 5000) in one launch, against
+    the FP64 oracle's values stored by tests/golden/make_workload4_oracle.py:
+    two images that reach the cap and one that stops early (Algorithm 2's
+    while condition; the stop within one iteration)."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "workload4_oracle.json")) as fh:
+        gold = json.load(fh)["images"]
+    idx = sorted(int(k) for k in gold)
+    ps = [inputs.workload4(i) for i in idx]
+    w, infos = _solve(env, [(p.a, p.b, tuple(p.h), p.eps, p.tol, p.itr_max) for p in ps])
+    _, fs1 = env
+    for k, i in enumerate(idx):
+        g = gold[str(i)]
+        if g["iters"] == g["itr_max"]:
+            assert infos[k].iters == g["iters"] and infos[k].status == fs1.FS1_ENOTCONV
+            assert abs(infos[k].marginal_err - g["err"]) <= 1e-3 * g["err"] + 1e-7
+        else:
+            assert infos[k].status == fs1.FS1_OK and abs(infos[k].iters - g["iters"]) <= 1
+            assert infos[k].marginal_err <= g["tol"]
+        assert abs(w[k] - g["w"]) <= TOL32 * abs(g["w"]), (i, w[k], g["w"])
