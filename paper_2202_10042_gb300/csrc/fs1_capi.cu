@@ -314,13 +314,20 @@ fs1_status choose_geometry(fs1_handle* h, int kind, const std::vector<const fs1_
 
 // Heterogeneous team plan for a batch of 1D problems: problems are put in
 // classes by the fewest CTAs that hold them on chip (rounded up to a power of
-// two); CTAs are split over the classes in proportion to their estimated work
-// (N * itr_max); every class is a queue of its problems in decreasing cost
-// (longest-processing-time first) served by its teams.
+// two), and every class is a queue of its problems in decreasing cost
+// (longest-processing-time first).  With several classes the launch runs a
+// level schedule: all CTAs start in teams of the largest class's size on its
+// queue, and a team that finds its queue empty splits into teams of the next
+// size down, so that the batch's work runs largest first and no CTA waits
+// while another class still has problems (the iteration counts, and so the
+// work per class, are not known before the solve).  Team sizes that do not
+// divide each other (a class capped at the device's CTA count) fall back to a
+// static split of the CTAs over the classes in proportion to N * itr_max.
 struct Plan {
   std::vector<int> cta_team, cta_rank, team_T, team_slot, team_class, class_off, order, class_T;
-  std::vector<int> prob_T;   // team size of each problem
-  int num_teams = 0, grid = 0, max_T = 1, slots = 0;
+  std::vector<int> prob_T;    // team size of each problem
+  std::vector<int> level_T;   // level schedule: team size per level (empty: static teams)
+  int num_teams = 0, grid = 0, max_T = 1, slots = 0, tickets = 0;
 };
 
 // fewest CTAs that hold problem p on chip (0: more than fit)
@@ -399,7 +406,12 @@ fs1_status plan_teams(fs1_handle* h, int kind, const std::vector<const fs1_probl
     auto it = h->tuned.find(tune_key(h, kind, ps, maxc));
     if (it != h->tuned.end()) force = it->second;
   }
-  if (nc == 1 && force > 0) {
+  bool levels = nc > 1 && h->cfg.team_size <= 0;
+  for (int k = 1; k < nc && levels; ++k) levels = T[k] % T[k - 1] == 0;
+  if (levels) {
+    teams.assign(nc, 0);
+    teams[nc - 1] = maxc / T[nc - 1];
+  } else if (nc == 1 && force > 0) {
     T[0] = std::min(tcap, std::max(T[0], force));
     teams[0] = std::max(1, std::min(cnt[0], maxc / T[0]));
   } else if (nc == 1) {
@@ -441,6 +453,9 @@ fs1_status plan_teams(fs1_handle* h, int kind, const std::vector<const fs1_probl
     }
   }
   // queues in decreasing cost
+  P->level_T.clear();
+  if (levels)
+    for (int k = nc - 1; k >= 0; --k) P->level_T.push_back(T[k]);
   P->class_off.assign(nc + 1, 0);
   for (int k = 0; k < nc; ++k) P->class_off[k + 1] = P->class_off[k] + cnt[k];
   P->order.assign(n, 0);
@@ -474,7 +489,8 @@ fs1_status plan_teams(fs1_handle* h, int kind, const std::vector<const fs1_probl
     }
   P->num_teams = (int)P->team_T.size();
   P->grid = (int)P->cta_team.size();
-  P->slots = slot;
+  P->slots = levels ? nc * 2 * P->grid : slot;
+  P->tickets = levels ? nc * P->grid : P->num_teams;
   P->prob_T.assign(n, 0);
   for (int i = 0; i < n; ++i) P->prob_T[i] = T[cls[i]];
   return FS1_OK;
@@ -563,10 +579,10 @@ fs1_status autotune(fs1_handle* h, int kind, const std::vector<const fs1_problem
 // arguments a captured graph bakes in.  The header's contents (descriptors,
 // plan) are data copied from pinned memory on every replay.
 std::string graph_key(int kind, int mode, int in_f32, int count, int grid, int T, int teams, int nclass,
-                      size_t nslots, size_t hdr, bool validate, long long spin_cap, int exact_E) {
+                      int nlevel, size_t nslots, size_t hdr, bool validate, long long spin_cap, int exact_E) {
   char buf[192];
-  snprintf(buf, sizeof buf, "%d.%d.%d.%d.%d.%d.%d.%d.%zu.%zu.%d.%lld.%d", kind, mode, in_f32, count, grid, T, teams,
-           nclass, nslots, hdr, (int)validate, spin_cap, exact_E);
+  snprintf(buf, sizeof buf, "%d.%d.%d.%d.%d.%d.%d.%d.%d.%zu.%zu.%d.%lld.%d", kind, mode, in_f32, count, grid, T,
+           teams, nclass, nlevel, nslots, hdr, (int)validate, spin_cap, exact_E);
   return buf;
 }
 
@@ -629,14 +645,16 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
   const int in_f32 = ps[0]->dtype == FS1_FP32;
   const int nclass = planned ? (int)plan.class_T.size() : 0;
   const int pgrid = planned ? plan.grid : 0;
+  const int nlevel = planned ? (int)plan.level_T.size() : 0;
   // plan arrays: cta_team, cta_rank [grid]; team_T, team_slot, team_class
-  // [teams]; class_off [nc + 1]; order [count]; class_next [nc]
-  const size_t plan_ints = planned ? (size_t)2 * pgrid + 3 * teams + (nclass + 1) + count + nclass : 0;
+  // [teams]; class_off [nc + 1]; order [count]; class_next [nc]; level_T [nlevel]
+  const size_t plan_ints =
+      planned ? (size_t)2 * pgrid + 3 * teams + (nclass + 1) + count + nclass + nlevel : 0;
   size_t off = 0;
   const size_t o_desc = off; off = align_up(off + sizeof(PairDesc) * count, 256);
   const size_t o_res = off;  off = align_up(off + sizeof(PairResult) * count, 256);
   const size_t o_plan = off; off = align_up(off + sizeof(int) * plan_ints, 256);
-  const size_t o_tick = off; off = align_up(off + sizeof(unsigned long long) * (planned ? teams : 0), 256);
+  const size_t o_tick = off; off = align_up(off + sizeof(unsigned long long) * (planned ? plan.tickets : 0), 256);
   const size_t o_ctr = off;  off = align_up(off + sizeof(unsigned long long) * teams, 256);
   const size_t o_abt = off;  off = align_up(off + sizeof(int) * teams, 256);
   const size_t o_poff = off; off = align_up(off + sizeof(int64_t) * (paper ? count : 0), 256);
@@ -717,6 +735,7 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
       pi += v->size();
     }
     // class_next stays zero
+    std::copy(plan.level_T.begin(), plan.level_T.end(), pi + nclass);
   }
   if (paper) memcpy(hb + o_poff, poff.data(), sizeof(int64_t) * count);
   PairResult* hres = (PairResult*)h->hres;
@@ -796,10 +815,14 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
       L.order = pi + 2 * pgrid + 3 * teams + nclass + 1;
       L.class_next = pi + 2 * pgrid + 3 * teams + nclass + 1 + count;
       L.tickets = (unsigned long long*)(ws + o_tick);
+      L.nlevel = nlevel;
+      L.level_T = nlevel ? L.class_next + nclass : nullptr;
     }
     L.spin_cap = h->cfg.spin_cap;
-    const int exact_E =
-        paper ? 0 : common_points_per_thread(ps, planned ? plan.prob_T : std::vector<int>(count, T));
+    // level schedules run on the generic instantiation
+    const int exact_E = (paper || nlevel > 0)
+                            ? 0
+                            : common_points_per_thread(ps, planned ? plan.prob_T : std::vector<int>(count, T));
     // the call's stream work, issued on s (captured when s is the capture stream)
     auto issue = [&](cudaStream_t s, bool capturing) -> fs1_status {
       cudaError_t ee;
@@ -828,8 +851,8 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
     };
     const bool graphs = h->cfg.use_graph && !h->graphs_off && !h->tuning;
     const std::string gkey =
-        graphs ? graph_key(kind, mode, in_f32, count, planned ? pgrid : teams * T, T, teams, nclass, nslots, hdr,
-                           validate, h->cfg.spin_cap, exact_E)
+        graphs ? graph_key(kind, mode, in_f32, count, planned ? pgrid : teams * T, T, teams, nclass, nlevel, nslots,
+                           hdr, validate, h->cfg.spin_cap, exact_E)
                : std::string();
     cudaGraphExec_t exec = nullptr;
     for (size_t k = 0; graphs && k < h->graphs.size(); ++k)
@@ -1210,7 +1233,7 @@ fs1_status fs1_solve_batch(fs1_handle* h, const fs1_problem* probs, int64_t coun
     for (size_t j = 0; j < idx.size(); ++j) {
       res[idx[j]] = r[j];
       pst[idx[j]] = (fs1_status)r[j].status;
-      team[idx[j]] = r[j].pad > 0 ? r[j].pad : geo.team_size;   // a cluster-resident image: its CTAs
+      team[idx[j]] = r[j].pad > 0 ? r[j].pad : geo.team_size;   // the 1D team or the image's cluster
       ms[idx[j]] = gms;
     }
   }

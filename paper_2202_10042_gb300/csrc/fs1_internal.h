@@ -29,7 +29,8 @@ struct PairResult {
   double err;     // marginal L1 error of the final iterate
   int64_t iters;  // completed iterations
   int status;     // fs1_status value
-  int pad;        // CTAs of the cluster that solved a 2D image resident on chip (0 otherwise)
+  int pad;        // CTAs that solved the problem: a 1D team, or the cluster of a 2D image resident on
+                  // chip (0: the 2D grid kernel, the streamed path, the paper form)
 };
 
 // Exchange slot of one CTA of a team (one per CTA and buffer parity): up to
@@ -63,7 +64,15 @@ struct TeamLaunch {
   const int* team_class;           // [num_teams] work class served by the team
   const int* class_off;            // [nclass + 1] offsets of each class's pairs in `order`
   int* class_next;                 // [nclass] queue heads (zeroed per launch)
-  unsigned long long* tickets;     // [num_teams] pair broadcast words (zeroed per launch)
+  unsigned long long* tickets;     // [num_teams] pair broadcast words (zeroed per launch);
+                                   // [nlevel][grid] under a level schedule
+  // Level schedule (nlevel > 0): every CTA starts in a team of level_T[0]
+  // CTAs serving the queue of the largest class; a team whose queue is empty
+  // splits into the teams of the next level (level_T decreasing, each
+  // dividing the one before), which serve the next class down.  Slots are
+  // [nlevel][2 grid]; cta_team .. team_class describe level 0.
+  int nlevel;
+  const int* level_T;              // [nlevel]
   const int* valid;                // [num_pairs] 0: the pair failed the input check and is
                                    // reported FS1_EINVAL without solving; null: all valid
 };

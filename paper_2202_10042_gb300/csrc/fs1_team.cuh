@@ -83,9 +83,28 @@ struct DecayTables {
 // where a CTA sits: its team, rank, team size and the team's slots
 struct TeamCtx {
   int team, rank, T;
-  size_t slot_base;   // first slot of the team's [2][T] slot block
+  size_t slot_base;                // first slot of the team's [2][T] slot block
   int* abort;
+  int ticket;                      // index of the team's pair broadcast word (queues)
 };
+
+// Team of this CTA at level k of a level schedule: CTA c is rank c % T_k of
+// team c / T_k, the level's teams have their own slots and ticket words, and
+// the level serves the queue of the class of team size T_k (classes sorted by
+// increasing team size, levels by decreasing).  Every team of level k + 1 is
+// made of CTAs of one team of level k (T_{k+1} divides T_k), so those CTAs
+// leave level k together, when their team finds its queue empty.
+__device__ __forceinline__ void level_ctx(const TeamLaunch& L, int k, TeamCtx& tc, int& cls) {
+  const int T = L.level_T[k];
+  tc.T = T;
+  tc.rank = (int)blockIdx.x % T;
+  tc.team = (int)blockIdx.x / T;
+  const size_t first = (size_t)blockIdx.x - (size_t)tc.rank;
+  tc.slot_base = (size_t)k * 2 * (size_t)L.grid + 2 * first;
+  tc.ticket = k * L.grid + (int)first;
+  tc.abort = L.abort_flags + blockIdx.x / L.level_T[0];
+  cls = L.nlevel - 1 - k;
+}
 
 template <class T>
 struct SlotPayload {
@@ -509,21 +528,30 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
   __shared__ int sm_item;
   const int tid = threadIdx.x;
   TeamCtx tc;
-  int cls = -1;
-  if (L.cta_team) {
+  // level schedules run on the generic instantiations only (the host picks
+  // an exact one for batches of one point count per thread, which have one
+  // class), so that the exact kernels carry none of their state
+  constexpr bool kLevels = G < E;
+  int cls = -1, lvl = 0;
+  if (kLevels && L.nlevel > 0) {
+    level_ctx(L, 0, tc, cls);
+  } else if (L.cta_team) {
     tc.team = L.cta_team[blockIdx.x];
     tc.rank = L.cta_rank[blockIdx.x];
     tc.T = L.team_T[tc.team];
     tc.slot_base = (size_t)L.team_slot[tc.team];
+    tc.abort = L.abort_flags + tc.team;
+    tc.ticket = tc.team;
     cls = L.team_class[tc.team];
   } else {
     tc.T = L.team_size;
     tc.team = blockIdx.x / tc.T;
     tc.rank = blockIdx.x % tc.T;
     tc.slot_base = (size_t)tc.team * 2 * tc.T;
+    tc.abort = L.abort_flags + tc.team;
+    tc.ticket = 0;
   }
-  tc.abort = L.abort_flags + tc.team;
-  const int T = tc.T, team = tc.team, rank = tc.rank;
+  int T = tc.T, team = tc.team, rank = tc.rank;
   if (team >= L.num_teams) return;
   unsigned epoch = 0, xc = 0, seq = 0;
   if (tid == 0) {
@@ -532,6 +560,7 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
   }
   __syncthreads();
 
+  for (;;) {   // the levels of a level schedule (one pass otherwise)
   for (int pi = team;; pi += L.num_teams) {
     int pid;
     if (cls < 0) {
@@ -542,18 +571,19 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
       // broadcasts it to the other CTAs of the team through a tagged word
       ++seq;
       if (tid == 0) {
+        unsigned long long* const tk = L.tickets + (kLevels ? tc.ticket : team);
         int item;
         if (rank == 0) {
           item = atomicAdd(L.class_next + cls, 1);
           if (T > 1) {
             const unsigned long long w = ((unsigned long long)seq << 32) | (unsigned)item;
-            asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(L.tickets + team), "l"(w) : "memory");
+            asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(tk), "l"(w) : "memory");
           }
         } else {
           long long spins = 0;
           unsigned long long w = 0;
           for (;;) {
-            asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(L.tickets + team) : "memory");
+            asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(tk) : "memory");
             if ((unsigned)(w >> 32) == seq) break;
             if (++spins > L.spin_cap || ((spins & 63) == 0 && ld_relaxed(tc.abort))) {
               atomicExch(tc.abort, 1);
@@ -860,7 +890,7 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
         R.iters = ell;
         R.status = status;
         if (status == FS1_OK && !(err_last <= P.tol)) R.status = FS1_ENOTCONV;
-        R.pad = 0;
+        R.pad = T;
         L.results[pid] = R;
       }
     }
@@ -872,6 +902,17 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
       L.results[pid] = R;
     }
     return;
+  }
+  // the team's queue is empty: its CTAs go on as the teams of the next level
+  if (!kLevels || ++lvl >= L.nlevel) break;
+  level_ctx(L, lvl, tc, cls);
+  T = tc.T;
+  team = tc.team;
+  rank = tc.rank;
+  // the level's slots start zeroed (tag 0): keep the compact slots' 8-bit
+  // tags of its first two exchanges away from 0
+  if (((epoch + 1u) & 0xFFu) == 0u || ((epoch + 2u) & 0xFFu) == 0u) epoch += 2u;
+  __syncthreads();   // sm_item is rewritten by the next ticket
   }
 }
 

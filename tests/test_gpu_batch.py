@@ -69,3 +69,49 @@ def test_forced_team_size_and_order_independence(env):
     for k in range(12):
         assert abs(w_a[k] - w_b[11 - k]) <= TOL32 * abs(w_a[k])
         assert abs(w_a[k] - w_c[k]) <= TOL32 * abs(w_a[k])
+
+
+def _pair(seed, n, eps, itr):
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(0.05, 1.0, n)
+    b = rng.uniform(0.05, 1.0, n)
+    return inputs.Problem(a / a.sum(), b / b.sum(), (1.0 / n,), eps, 0.0, itr, 1, (n,), 0, seed)
+
+
+def test_level_schedule_team_sizes_and_parity(env):
+    """A batch spanning four team classes (1, 2, 4 and 8 CTAs of 16384 points)
+    runs as one level schedule: teams of 8 CTAs take the largest pairs first
+    and split into teams of 4, 2 and 1 as the queues empty.  Every pair is
+    solved by a team of its class, matches the oracle at its iteration count,
+    and gives the same result in the mix as alone; a replay of the captured
+    graph gives the same bits."""
+    torch, fs1 = env
+    itr = 200   # about 400 exchanges per pair: the compact slots' 8-bit tags wrap
+    sizes = [100000, 70000, 40000, 33000, 20000, 17000] + [500 + 701 * k for k in range(20)] + [16384, 9000]
+    ps = [_pair(700 + k, n, 0.02 if k % 2 else 0.005, itr) for k, n in enumerate(sizes)]
+    want_T = [1 << max(0, math.ceil(math.log2(math.ceil(p.a.size / 16384)))) for p in ps]
+    assert sorted(set(want_T)) == [1, 2, 4, 8]
+    keep, probs = [], []
+    for p in ps:
+        a = torch.tensor(p.a, dtype=torch.float32, device="cuda")
+        b = torch.tensor(p.b, dtype=torch.float32, device="cuda")
+        keep += [a, b]
+        probs.append(fs1.Solver.problem(a, b, p.h[0], p.eps, p.tol, p.itr_max))
+    s = fs1.Solver("log", "fp32")
+    runs = [s.solve(probs) for _ in range(3)]   # direct, captured, replayed
+    st = s.stats()
+    s.close()
+    assert st["graph_replays"] >= 1
+    _, w, infos = runs[0]
+    for _, w2, i2 in runs[1:]:
+        assert list(w2) == list(w) and [i.iters for i in i2] == [i.iters for i in infos]
+    assert [i.team_size for i in infos] == want_T
+    refs = cref.solve_many([(p.a, p.b, p.h[0], p.eps, 0.0, infos[k].iters) for k, p in enumerate(ps)], tau=1e10)
+    for k, (p, r) in enumerate(zip(ps, refs)):
+        assert infos[k].status in (fs1.FS1_OK, fs1.FS1_ENOTCONV)
+        assert abs(w[k] - r.w) <= TOL32 * abs(r.w), (k, p.a.size, w[k], r.w)
+        assert abs(infos[k].marginal_err - r.err) <= 1e-3 * r.err + 1e-9, (k, infos[k].marginal_err, r.err)
+    for k in (0, 3, 10):
+        w1, i1 = _solve(env, [ps[k]], team_size=want_T[k], autotune=False)
+        assert i1[0].iters == infos[k].iters
+        assert abs(w1[0] - w[k]) <= 1e-5 * abs(w[k])
