@@ -323,12 +323,28 @@ fs1_status choose_geometry(fs1_handle* h, int kind, const std::vector<const fs1_
 // work per class, are not known before the solve).  Team sizes that do not
 // divide each other (a class capped at the device's CTA count) fall back to a
 // static split of the CTAs over the classes in proportion to N * itr_max.
+//
+// Small stabilised pairs (at most 32 points per thread on 4 warps) go to the
+// kernel's units instead: after the teams' queues, every CTA runs 4 units of
+// 4 warps on one queue and then 16 single warps on another, a pair per unit
+// (classes nc and nc + 1 after the nc team classes); such a plan is always a
+// level schedule over all the device's CTAs.
 struct Plan {
   std::vector<int> cta_team, cta_rank, team_T, team_slot, team_class, class_off, order, class_T;
-  std::vector<int> prob_T;    // team size of each problem
+  std::vector<int> prob_T;    // team size of each problem (CTAs; 1 for a unit)
   std::vector<int> level_T;   // level schedule: team size per level (empty: static teams)
   int num_teams = 0, grid = 0, max_T = 1, slots = 0, tickets = 0;
+  int unit_class = -1;        // class of the 4-warp units' queue (-1: no units)
 };
+
+// Warps of the unit that solves problem p (4 or 1), or 0 for a team of CTAs:
+// the fewest warps holding it at <= 32 points per thread within the frame cap
+int unit_warps(int kind, const fs1_problem& p) {
+  if (kind != KK_LOG_F32 || p.ndim != 1) return 0;
+  const int64_t cap = std::min(32, elems_cap_for(kind, p.h[0] / p.eps));
+  const int64_t n = npoints(p);
+  return n <= 32 * cap ? 1 : (n <= 128 * cap ? 4 : 0);
+}
 
 // fewest CTAs that hold problem p on chip (0: more than fit)
 int64_t min_ctas(int kind, const fs1_problem& p) {
@@ -364,16 +380,22 @@ std::string tune_key(fs1_handle* h, int kind, const std::vector<const fs1_proble
   return buf;
 }
 
-fs1_status plan_teams(fs1_handle* h, int kind, const std::vector<const fs1_problem*>& ps, Plan* P) {
+fs1_status plan_teams(fs1_handle* h, int kind, const std::vector<const fs1_problem*>& ps, Plan* P, bool units) {
   const int thr = team_threads();
   const int maxc = max_coresident_ctas(kind);
   if (maxc <= 0) return FS1_ECUDA;
   const int tcap = std::min(maxc, kMaxTeamCtas);
   const int n = (int)ps.size();
-  std::vector<int> tmin(n);
+  std::vector<int> tmin(n), uw(n, 0);
   std::vector<double> cost(n);
+  bool any_unit = false;
   for (int i = 0; i < n; ++i) {
     const int64_t np = npoints(*ps[i]);
+    cost[i] = (double)np * (double)std::max<int64_t>(1, ps[i]->itr_max);
+    if (units && (uw[i] = unit_warps(kind, *ps[i])) > 0) {
+      any_unit = true;
+      continue;
+    }
     const int64_t t = min_ctas(kind, *ps[i]);
     if (t > tcap) return FS1_EUNSUPPORTED;
     tmin[i] = std::min<int>(pow2_at_least(t), tcap);
@@ -381,17 +403,22 @@ fs1_status plan_teams(fs1_handle* h, int kind, const std::vector<const fs1_probl
       if (h->cfg.team_size > tcap) return FS1_EINVAL;
       tmin[i] = std::max<int>((int)t, h->cfg.team_size);
     }
-    cost[i] = (double)np * (double)std::max<int64_t>(1, ps[i]->itr_max);
   }
-  // classes by team size
-  std::vector<int> keys(tmin);
+  // classes by team size (a batch of unit pairs only keeps one empty class of
+  // teams of one CTA), then the units' two classes
+  std::vector<int> keys;
+  for (int i = 0; i < n; ++i)
+    if (uw[i] == 0) keys.push_back(tmin[i]);
+  if (keys.empty()) keys.push_back(1);
   std::sort(keys.begin(), keys.end());
   keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
   const int nc = (int)keys.size();
-  std::vector<double> W(nc, 0.0);
-  std::vector<int> cnt(nc, 0), cls(n);
+  const int nq = nc + (any_unit ? 2 : 0);   // queues
+  std::vector<double> W(nq, 0.0);
+  std::vector<int> cnt(nq, 0), cls(n);
   for (int i = 0; i < n; ++i) {
-    cls[i] = (int)(std::lower_bound(keys.begin(), keys.end(), tmin[i]) - keys.begin());
+    cls[i] = uw[i] == 4 ? nc : (uw[i] == 1 ? nc + 1
+                                           : (int)(std::lower_bound(keys.begin(), keys.end(), tmin[i]) - keys.begin()));
     W[cls[i]] += cost[i];
     cnt[cls[i]] += 1;
   }
@@ -406,8 +433,9 @@ fs1_status plan_teams(fs1_handle* h, int kind, const std::vector<const fs1_probl
     auto it = h->tuned.find(tune_key(h, kind, ps, maxc));
     if (it != h->tuned.end()) force = it->second;
   }
-  bool levels = nc > 1 && h->cfg.team_size <= 0;
+  bool levels = (nc > 1 || any_unit) && h->cfg.team_size <= 0;
   for (int k = 1; k < nc && levels; ++k) levels = T[k] % T[k - 1] == 0;
+  if (any_unit && !levels) return FS1_EINVAL;   // the caller plans again without units
   if (levels) {
     teams.assign(nc, 0);
     teams[nc - 1] = maxc / T[nc - 1];
@@ -456,8 +484,9 @@ fs1_status plan_teams(fs1_handle* h, int kind, const std::vector<const fs1_probl
   P->level_T.clear();
   if (levels)
     for (int k = nc - 1; k >= 0; --k) P->level_T.push_back(T[k]);
-  P->class_off.assign(nc + 1, 0);
-  for (int k = 0; k < nc; ++k) P->class_off[k + 1] = P->class_off[k] + cnt[k];
+  P->unit_class = any_unit ? nc : -1;
+  P->class_off.assign(nq + 1, 0);
+  for (int k = 0; k < nq; ++k) P->class_off[k + 1] = P->class_off[k] + cnt[k];
   P->order.assign(n, 0);
   std::vector<int> idx(n);
   for (int i = 0; i < n; ++i) idx[i] = i;
@@ -492,7 +521,7 @@ fs1_status plan_teams(fs1_handle* h, int kind, const std::vector<const fs1_probl
   P->slots = levels ? nc * 2 * P->grid : slot;
   P->tickets = levels ? nc * P->grid : P->num_teams;
   P->prob_T.assign(n, 0);
-  for (int i = 0; i < n; ++i) P->prob_T[i] = T[cls[i]];
+  for (int i = 0; i < n; ++i) P->prob_T[i] = uw[i] > 0 ? 1 : T[cls[i]];
   return FS1_OK;
 }
 
@@ -579,10 +608,11 @@ fs1_status autotune(fs1_handle* h, int kind, const std::vector<const fs1_problem
 // arguments a captured graph bakes in.  The header's contents (descriptors,
 // plan) are data copied from pinned memory on every replay.
 std::string graph_key(int kind, int mode, int in_f32, int count, int grid, int T, int teams, int nclass,
-                      int nlevel, size_t nslots, size_t hdr, bool validate, long long spin_cap, int exact_E) {
+                      int nlevel, int unit_class, size_t nslots, size_t hdr, bool validate, long long spin_cap,
+                      int exact_E) {
   char buf[192];
-  snprintf(buf, sizeof buf, "%d.%d.%d.%d.%d.%d.%d.%d.%d.%zu.%zu.%d.%lld.%d", kind, mode, in_f32, count, grid, T,
-           teams, nclass, nlevel, nslots, hdr, (int)validate, spin_cap, exact_E);
+  snprintf(buf, sizeof buf, "%d.%d.%d.%d.%d.%d.%d.%d.%d.%d.%zu.%zu.%d.%lld.%d", kind, mode, in_f32, count, grid, T,
+           teams, nclass, nlevel, unit_class, nslots, hdr, (int)validate, spin_cap, exact_E);
   return buf;
 }
 
@@ -632,18 +662,34 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
     return st;
   }
   const bool planned = !two_d && !paper && mode == 0;
-  if (planned && h->cfg.autotune && h->cfg.team_size <= 0 && !h->tuning) {
+  // small stabilised pairs of a batch on the kernel's units (no team-size
+  // tuning then); a lone pair keeps whole CTAs (its serial chains are
+  // shorter there, and fs1_w1 stays the same computation as fs1_w1_noalloc)
+  bool units = planned && count > 1 && kind == KK_LOG_F32 && h->cfg.units && h->cfg.team_size <= 0 && !h->tuning;
+  if (units) {
+    bool any = false;
+    for (auto* p : ps) any = any || unit_warps(kind, *p) > 0;
+    units = any;
+  }
+  if (planned && !units && h->cfg.autotune && h->cfg.team_size <= 0 && !h->tuning) {
     const int maxc = max_coresident_ctas(kind);
     const std::string key = tune_key(h, kind, ps, maxc);
     if (!key.empty() && !h->tuned.count(key) && (st = autotune(h, kind, ps, key, maxc)) != FS1_OK) return st;
   }
   Plan plan;
-  if (planned && (st = plan_teams(h, kind, ps, &plan)) != FS1_OK) return st;
+  if (planned) {
+    st = plan_teams(h, kind, ps, &plan, units);
+    if (st == FS1_EINVAL && units) {   // no level schedule for these team sizes: teams only
+      units = false;
+      st = plan_teams(h, kind, ps, &plan, false);
+    }
+    if (st != FS1_OK) return st;
+  }
   const int T = two_d ? 1 : (planned ? plan.max_T : geo.team_size);
   const int teams = two_d ? 1 : (planned ? plan.num_teams : geo.num_teams);
   const size_t nslots = (two_d || paper) ? 0 : (planned ? (size_t)plan.slots : (size_t)teams * 2 * T);
   const int in_f32 = ps[0]->dtype == FS1_FP32;
-  const int nclass = planned ? (int)plan.class_T.size() : 0;
+  const int nclass = planned ? (int)plan.class_off.size() - 1 : 0;   // queues
   const int pgrid = planned ? plan.grid : 0;
   const int nlevel = planned ? (int)plan.level_T.size() : 0;
   // plan arrays: cta_team, cta_rank [grid]; team_T, team_slot, team_class
@@ -817,6 +863,8 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
       L.tickets = (unsigned long long*)(ws + o_tick);
       L.nlevel = nlevel;
       L.level_T = nlevel ? L.class_next + nclass : nullptr;
+      L.unit_queues = plan.unit_class >= 0 ? 1 : 0;
+      L.unit_class = plan.unit_class;
     }
     L.spin_cap = h->cfg.spin_cap;
     // level schedules run on the generic instantiation
@@ -851,8 +899,8 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
     };
     const bool graphs = h->cfg.use_graph && !h->graphs_off && !h->tuning;
     const std::string gkey =
-        graphs ? graph_key(kind, mode, in_f32, count, planned ? pgrid : teams * T, T, teams, nclass, nlevel, nslots,
-                           hdr, validate, h->cfg.spin_cap, exact_E)
+        graphs ? graph_key(kind, mode, in_f32, count, planned ? pgrid : teams * T, T, teams, nclass, nlevel,
+                           planned ? plan.unit_class : -1, nslots, hdr, validate, h->cfg.spin_cap, exact_E)
                : std::string();
     cudaGraphExec_t exec = nullptr;
     for (size_t k = 0; graphs && k < h->graphs.size(); ++k)
@@ -1035,7 +1083,7 @@ fs1_status fs1_config_default(fs1_config* cfg) {
   cfg->use_graph = 1;
   cfg->tau = 1e10;
   cfg->grid2d = 0;
-  cfg->reserved = 0;
+  cfg->units = 1;
   return FS1_OK;
 }
 

@@ -70,14 +70,30 @@ constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr int kSlotWords = 16;      // 64-bit words per exchange slot (payload <= 10)
 
-template <class C>
+template <class C, int ND = 257>
 struct DecayTables {
   C dt[33];        // lam^{Eeff j}: thread offsets inside a warp
   C dw[33];        // lam^{32 Eeff j}: warp offsets inside a CTA
-  C dT[257];       // lam^{S j}: CTA offsets inside a team (S = points per CTA)
+  C dT[ND];        // lam^{S j}: CTA offsets inside a team (S = points per CTA)
   float dtf[33];   // lam^{Eeff j} in FP32 for the narrow warp scan
   int narrow;      // 1 if c * 32 * Eeff <= 40 (a warp's decay fits one FP32 frame)
 };
+
+// Units.  A CTA of the team kernel is one unit of 16 warps (the team member),
+// or, for pairs small enough to fit a few warps, 16 / GW independent units of
+// GW warps, each solving its own pair (a team of one unit).  A unit
+// synchronises its own warps only: __syncthreads for the whole CTA, the warp
+// barrier for one warp, a named barrier (id 1 + unit) otherwise.
+template <int GW>
+__device__ __forceinline__ void unit_sync() {
+  if constexpr (GW == kWarps) {
+    __syncthreads();
+  } else if constexpr (GW == 1) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)(threadIdx.x / (32 * GW))), "n"(32 * GW) : "memory");
+  }
+}
 
 
 // where a CTA sits: its team, rank, team size and the team's slots
@@ -115,14 +131,14 @@ struct SlotPayload {
 // per-CTA shared state of an exchange; warp aggregates are double-buffered by
 // exchange parity so that a fast warp can publish the next exchange while a
 // slow one still reads the current one
-template <class T>
+template <class T, int NW = kWarps, int NST = kMaxTeamCtas>
 struct XchgSmem {
-  T wf[2][kWarps], wb[2][kWarps];
-  float eh[2][kWarps], el[2][kWarps];
-  T pf[kWarps], pb[kWarps];             // partial team carries (one per warp)
-  float ph[kWarps], pl[kWarps];
+  T wf[2][NW], wb[2][NW];
+  float eh[2][NW], el[2][NW];
+  T pf[NW], pb[NW];                     // partial team carries (one per warp)
+  float ph[NW], pl[NW];
   int ok;
-  SlotPayload<T> stage[kMaxTeamCtas];   // validated team slots
+  SlotPayload<T> stage[NST];            // validated team slots
 };
 
 // split an error partial into a compensated FP32 pair
@@ -174,9 +190,9 @@ __device__ __forceinline__ bool slot_try_read(const Slot* s, unsigned tag, SlotP
 // warp-level scans of the thread aggregates (phase A)
 // ---------------------------------------------------------------------------
 // generic: inclusive forward / backward Kogge-Stone with the operator
-template <class Op, class C>
+template <class Op, class C, class TB>
 __device__ __forceinline__ void warp_scan_generic(typename Op::T af, typename Op::T ab, int Eeff,
-                                                  const DecayTables<C>& tb, typename Op::T& excl_f,
+                                                  const TB& tb, typename Op::T& excl_f,
                                                   typename Op::T& excl_b, typename Op::T& wtot_f,
                                                   typename Op::T& wtot_b) {
   using T = typename Op::T;
@@ -198,7 +214,8 @@ __device__ __forceinline__ void warp_scan_generic(typename Op::T af, typename Op
 }
 
 // narrow stabilised path: one FP32 frame per warp (exact power-of-two shifts)
-__device__ __forceinline__ bool warp_scan_narrow(XF af, XF ab, const DecayTables<XF>& tb, XF& excl_f,
+template <class TB>
+__device__ __forceinline__ bool warp_scan_narrow(XF af, XF ab, const TB& tb, XF& excl_f,
                                                  XF& excl_b, XF& wtot_f, XF& wtot_b) {
   const int lane = threadIdx.x & 31;
   const int emax = __reduce_max_sync(0xffffffffu, max(af.e, ab.e));
@@ -344,14 +361,15 @@ __device__ __forceinline__ void hw_sum_df(float& hi, float& lo) {
 // so all warps and all CTAs agree.  Returns false when a bounded wait gave
 // up.  decision: 0 continue, 1 error <= tol, 2 error not finite.
 // ---------------------------------------------------------------------------
-template <class Op, class C, class EV>
+template <class Op, class C, int GW = kWarps, class EV, class TB, class XS>
 __device__ __forceinline__ bool exchange(const TeamLaunch& L, const TeamCtx& tc, unsigned& epoch,
                                          unsigned& xc, typename Op::T af, typename Op::T ab, EV err_part,
-                                         int Eeff, const DecayTables<C>& tb, XchgSmem<typename Op::T>& X,
+                                         int Eeff, const TB& tb, XS& X,
                                          typename Op::T& cf, typename Op::T& cb, float tol_h, float tol_l,
                                          int& decision, float* err_h, float* err_l, bool compact = false) {
   using T = typename Op::T;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = GW;   // warps of the unit
+  const int lane = threadIdx.x & 31, warp = (threadIdx.x >> 5) & (GW - 1);
   const int T_ = tc.T, rank = tc.rank;
   const int par = (int)(xc++ & 1u);
   // ---- A
@@ -368,26 +386,26 @@ __device__ __forceinline__ bool exchange(const TeamLaunch& L, const TeamCtx& tc,
     X.eh[par][warp] = eh;
     X.el[par][warp] = el;
   }
-  __syncthreads();
+  unit_sync<GW>();
   // ---- B: CTA-local carries of this warp, CTA error sum (every warp)
   const float Wf = (float)(32 * Eeff);
   T tf = Op::zero(), tbk = Op::zero();
   if (lane < warp) tf = Op::prop(X.wf[par][lane], tb.dw[warp - 1 - lane], Wf * (float)(warp - 1 - lane));
-  if (lane > warp && lane < kWarps)
+  if (lane > warp && lane < NW)
     tbk = Op::prop(X.wb[par][lane], tb.dw[lane - warp - 1], Wf * (float)(lane - warp - 1));
   const T pf = warp_sum_c(tf);
   const T pb = warp_sum_c(tbk);
-  float th = lane < kWarps ? X.eh[par][lane] : 0.f;
-  float tl = lane < kWarps ? X.el[par][lane] : 0.f;
+  float th = lane < NW ? X.eh[par][lane] : 0.f;
+  float tl = lane < NW ? X.el[par][lane] : 0.f;
   warp_sum_df(th, tl);
   T tcf = Op::zero(), tcb = Op::zero();
-  if (T_ > 1) {
+  if (GW == kWarps && T_ > 1) {
     ++epoch;
     if (warp == 0) {
       // CTA totals, published by lane 0
       T xf = Op::zero(), xb = Op::zero();
-      if (lane < kWarps) {
-        xf = Op::prop(X.wf[par][lane], tb.dw[kWarps - 1 - lane], Wf * (float)(kWarps - 1 - lane));
+      if (lane < NW) {
+        xf = Op::prop(X.wf[par][lane], tb.dw[NW - 1 - lane], Wf * (float)(NW - 1 - lane));
         xb = Op::prop(X.wb[par][lane], tb.dw[lane], Wf * (float)lane);
       }
       const T ctf = warp_sum_c(xf);
@@ -415,11 +433,11 @@ __device__ __forceinline__ bool exchange(const TeamLaunch& L, const TeamCtx& tc,
         atomicExch(&X.ok, 0);
       }
     }
-    __syncthreads();
+    unit_sync<GW>();
     if (!X.ok) return false;
     // partial team carries: warp w reduces slots 16 w .. 16 w + 15; lanes
     // 0-15 the forward terms, lanes 16-31 the backward terms
-    const float Sf = (float)(kThreads * Eeff);
+    const float Sf = (float)(32 * GW * Eeff);
     const int j = 16 * warp + (lane & 15);
     T term = Op::zero();
     float ph = 0.f, pl = 0.f;
@@ -439,7 +457,7 @@ __device__ __forceinline__ bool exchange(const TeamLaunch& L, const TeamCtx& tc,
       X.pl[warp] = pl;
     }
     if (lane == 16) X.pb[warp] = part;
-    __syncthreads();
+    unit_sync<GW>();
     const T q = lane < 16 ? X.pf[lane] : X.pb[lane - 16];
     const T tot = hw_sum(q);
     tcf = Op::idx(tot, 0);
@@ -456,7 +474,7 @@ __device__ __forceinline__ bool exchange(const TeamLaunch& L, const TeamCtx& tc,
   }
   const T wcf = Op::fwd(tcf, pf, tb.dw[warp], Wf * (float)warp);
   cf = Op::fwd(wcf, excl_f, tb.dt[lane], (float)(Eeff * lane));
-  const int wr = kWarps - 1 - warp;
+  const int wr = NW - 1 - warp;
   const T wcb = Op::bwd(pb, tcb, tb.dw[wr], Wf * (float)wr);
   cb = Op::bwd(excl_b, wcb, tb.dt[31 - lane], (float)(Eeff * (31 - lane)));
   return true;
@@ -507,33 +525,61 @@ __device__ __forceinline__ void steps_down(int Eeff, F&& f) {
   }
 }
 
-template <class V, class C, int E, int G>
-__global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int mode) {
+// Shared state of the units of one width: decay tables, exchange state (one
+// per element type, no aliasing between them) and queue tickets, per unit.
+template <class C, int GW>
+struct UnitSmem {
+  static constexpr int NU = kWarps / GW;
+  static constexpr int ND = GW == kWarps ? 257 : 1;
+  static constexpr int NST = GW == kWarps ? kMaxTeamCtas : 1;
+  DecayTables<C, ND> tb[NU];
+  XchgSmem<typename OpDist<C>::T, GW, NST> XD[NU];
+  XchgSmem<typename OpPlain<C>::T, GW, NST> XP[NU];
+  int item[NU];
+};
+
+// The pair loop of units of GW warps: the whole CTA as a member of a team
+// (static teams, uniform teams or a level schedule), or 16 / GW units each
+// solving pairs of its own queue.  tid is the thread's index in its unit.
+// Returns false when a bounded wait gave up.
+template <class V, class C, int E, int G, int GW>
+__device__ __forceinline__ bool team_body(const TeamLaunch& L, int mode, unsigned char* smem_raw,
+                                          UnitSmem<C, GW>* us) {
   constexpr bool EXT = std::is_same<C, XF>::value;
   using OpP = OpPlain<C>;
   using OpD = OpDist<C>;
   using PT = typename OpP::T;
   using DT = typename OpD::T;
 
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* sm_a = reinterpret_cast<V*>(smem_raw);
-  V* sm_b = sm_a + E * kThreads;
-  V* sm_v = sm_b + E * kThreads;   // the accepted v (for the marginal error; temp in the cost phase)
+  constexpr int NT = 32 * GW, NU = kWarps / GW;
+  const int unit = GW == kWarps ? 0 : (int)threadIdx.x / NT;
+  const int tid = GW == kWarps ? (int)threadIdx.x : (int)threadIdx.x % NT;
 
-  __shared__ DecayTables<C> tb;
-  // separate exchange state per element type (no aliasing between them)
-  __shared__ XchgSmem<DT> XD;
-  __shared__ XchgSmem<PT> XP;
+  V* sm_a = reinterpret_cast<V*>(smem_raw) + (size_t)unit * 3 * E * NT;
+  V* sm_b = sm_a + E * NT;
+  V* sm_v = sm_b + E * NT;   // the accepted v (for the marginal error; temp in the cost phase)
 
-  __shared__ int sm_item;
-  const int tid = threadIdx.x;
+  auto& tb = us->tb[unit];
+  auto& XD = us->XD[unit];
+  auto& XP = us->XP[unit];
+  int& sm_item = us->item[unit];
   TeamCtx tc;
   // level schedules run on the generic instantiations only (the host picks
   // an exact one for batches of one point count per thread, which have one
   // class), so that the exact kernels carry none of their state
-  constexpr bool kLevels = G < E;
+  constexpr bool kLevels = G < E && GW == kWarps;
   int cls = -1, lvl = 0;
-  if (kLevels && L.nlevel > 0) {
+  if constexpr (GW < kWarps) {
+    // every unit is a team of one on the units' queue of its width (a team
+    // of one never waits on another CTA: no ticket word, no abort flag)
+    tc.T = 1;
+    tc.rank = 0;
+    tc.team = (int)blockIdx.x * NU + unit;
+    tc.slot_base = 0;
+    tc.abort = L.abort_flags;
+    tc.ticket = 0;
+    cls = L.unit_class + (GW == 4 ? 0 : 1);
+  } else if (kLevels && L.nlevel > 0) {
     level_ctx(L, 0, tc, cls);
   } else if (L.cta_team) {
     tc.team = L.cta_team[blockIdx.x];
@@ -552,13 +598,13 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
     tc.ticket = 0;
   }
   int T = tc.T, team = tc.team, rank = tc.rank;
-  if (team >= L.num_teams) return;
+  if (GW == kWarps && team >= L.num_teams) return true;
   unsigned epoch = 0, xc = 0, seq = 0;
   if (tid == 0) {
     XD.ok = 1;
     XP.ok = 1;
   }
-  __syncthreads();
+  unit_sync<GW>();
 
   for (;;) {   // the levels of a level schedule (one pass otherwise)
   for (int pi = team;; pi += L.num_teams) {
@@ -595,30 +641,30 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
         }
         sm_item = item;
       }
-      __syncthreads();
+      unit_sync<GW>();
       const int item = sm_item;
-      if (item < 0) return;   // the ticket wait gave up (the other CTAs time out too)
+      if (item < 0) return false;   // the ticket wait gave up (the other CTAs time out too)
       if (item >= L.class_off[cls + 1] - L.class_off[cls]) break;
       pid = L.order[L.class_off[cls] + item];
     }
     if (L.valid != nullptr && !L.valid[pid]) {
       if (rank == 0 && tid == 0) L.results[pid] = PairResult{NAN, NAN, 0, FS1_EINVAL, 0};
-      __syncthreads();   // sm_item is rewritten by the next ticket
+      unit_sync<GW>();   // sm_item is rewritten by the next ticket
       continue;
     }
     const PairDesc P = L.pairs[pid];
     const int64_t N = P.n;
     const double c = P.h_fast / P.eps;
     const V lam = (V)exp(-c);
-    const int Eeff = (int)((N + (int64_t)T * kThreads - 1) / ((int64_t)T * kThreads));
+    const int Eeff = (int)((N + (int64_t)T * NT - 1) / ((int64_t)T * NT));
     if (Eeff > E) {
       // the host picks the kernel from the point counts; a pair that does
       // not fit this instantiation's registers and shared memory is refused
       if (rank == 0 && tid == 0) L.results[pid] = PairResult{NAN, NAN, 0, FS1_EINVAL, 0};
-      __syncthreads();
+      unit_sync<GW>();
       continue;
     }
-    const int S = kThreads * Eeff;
+    const int S = NT * Eeff;
     const int64_t s0 = (int64_t)rank * S;
     const int64_t g0 = s0 + (int64_t)tid * Eeff;   // first grid point of this thread
     const int ne = (int)max((int64_t)0, min((int64_t)Eeff, N - g0));
@@ -627,7 +673,7 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
     const bool compact = EXT && (c * (double)N + 200.0) * 1.4426950408889634 < 30000.0;
 
     // decay tables (FP64 exponent arithmetic, once per pair)
-    for (int i = tid; i < 33 + 33 + 257; i += kThreads) {
+    for (int i = tid; i < 33 + 33 + UnitSmem<C, GW>::ND; i += NT) {
       if (i < 33) {
         tb.dt[i] = c_decay((double)Eeff * i, c, C{});
         tb.dtf[i] = (float)exp(-(double)Eeff * i * c);
@@ -639,7 +685,7 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
     }
     if (tid == 0) tb.narrow = (c * 32.0 * Eeff <= 40.0) ? 1 : 0;
     // masses into shared memory, [k][thread] layout
-    for (int i = tid; i < S; i += kThreads) {
+    for (int i = tid; i < S; i += NT) {
       const int64_t gi = s0 + i;
       V va = 0, vb = 0;
       if (gi < N && mode == 0) {
@@ -647,8 +693,8 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
         vb = load_mass<V>(P.b, gi, L.in_f32);
       }
       const int tt = i / Eeff, kk = i - tt * Eeff;
-      sm_a[kk * kThreads + tt] = va;
-      sm_b[kk * kThreads + tt] = vb;
+      sm_a[kk * NT + tt] = va;
+      sm_b[kk * NT + tt] = vb;
     }
 
     // state: u in registers (xu, frame fu); v in registers (xn, frame fv)
@@ -690,14 +736,14 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
       for (int k = 0; k < E; ++k) {
         mu = xu[k] > mu ? xu[k] : mu;
         mv = xn[k] > mv ? xn[k] : mv;
-        sm_v[k * kThreads + tid] = xn[k];
+        sm_v[k * NT + tid] = xn[k];
       }
       if (EXT) {
         hu = mu > 0 ? fu + fexp((float)mu) : kZeroExp;
         hv = mv > 0 ? fv + fexp((float)mv) : kZeroExp;
       }
     }
-    __syncthreads();
+    unit_sync<GW>();
 
     // aggregates of the initial u, in the same operation order as the
     // u-half's aggregates: a warm start from the potentials of a run stopped
@@ -713,7 +759,7 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
         ab = lk * (ab + xk);
       });
       int dec;
-      if (!exchange<OpP, C>(L, tc, epoch, xc, c_from(af, fu, C{}), c_from(ab, fu, C{}), (V)0, Eeff, tb, XP,
+      if (!exchange<OpP, C, GW>(L, tc, epoch, xc, c_from(af, fu, C{}), c_from(ab, fu, C{}), (V)0, Eeff, tb, XP,
                             cf, cb, 0.f, 0.f, dec, nullptr, nullptr, compact))
         goto timed_out;
     }
@@ -744,10 +790,10 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
           steps_down<E, G>(Eeff, [&](const int k, const bool on) {
             const V lk = on ? lam : (V)1, xk = on ? xu[k] : (V)0;
             const V y = xn[k] + s;
-            const V m = sm_b[k * kThreads + tid];
+            const V m = sm_b[k * NT + tid];
             V z = (k < ne) ? vdiv(m, y) : (V)0;
             if (mode == 1) z = (k < ne) ? y : (V)0;   // kernel-apply mode: keep K^T u
-            if (k < ne) ep += fabs(sm_v[k * kThreads + tid] * y * sc2 - m);
+            if (k < ne) ep += fabs(sm_v[k * NT + tid] * y * sc2 - m);
             xn[k] = z;
             zmax = z > zmax ? z : zmax;
             af = af + pw * z;
@@ -764,19 +810,19 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
             break;
           }
           int dec;
-          if (!exchange<OpP, C>(L, tc, epoch, xc, c_from(af, fz, C{}), c_from(ab, fz, C{}), ep, Eeff, tb, XP,
+          if (!exchange<OpP, C, GW>(L, tc, epoch, xc, c_from(af, fz, C{}), c_from(ab, fz, C{}), ep, Eeff, tb, XP,
                                 cf, cb, tol_h, tol_l, dec, &eh_last, &el_last, compact))
             goto timed_out;
           if (dec != 0 || ell >= P.itr_max) {
             if (dec == 2) status = FS1_ENUMERIC;
             // the returned iterate keeps the accepted v
 #pragma unroll
-            for (int k = 0; k < E; ++k) xn[k] = sm_v[k * kThreads + tid];
+            for (int k = 0; k < E; ++k) xn[k] = sm_v[k * NT + tid];
             break;
           }
           // accept v_new
 #pragma unroll
-          for (int k = 0; k < E; ++k) sm_v[k * kThreads + tid] = xn[k];
+          for (int k = 0; k < E; ++k) sm_v[k * NT + tid] = xn[k];
           fv = fz;
           hv = (EXT && zmax > 0) ? fz + fexp((float)zmax) : kZeroExp;
         }
@@ -794,7 +840,7 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
           steps_down<E, G>(Eeff, [&](const int k, const bool on) {
             const V lk = on ? lam : (V)1, xk = on ? xn[k] : (V)0;
             const V y = xu[k] + s;
-            const V m = sm_a[k * kThreads + tid];
+            const V m = sm_a[k * NT + tid];
             const V z = (k < ne) ? vdiv(m, y) : (V)0;
             xu[k] = z;
             zmax = z > zmax ? z : zmax;
@@ -807,14 +853,14 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
           fu = fz;
           hu = (EXT && zmax > 0) ? fz + fexp((float)zmax) : kZeroExp;
           int dec;
-          if (!exchange<OpP, C>(L, tc, epoch, xc, c_from(af, fz, C{}), c_from(ab, fz, C{}), (V)0, Eeff, tb,
+          if (!exchange<OpP, C, GW>(L, tc, epoch, xc, c_from(af, fz, C{}), c_from(ab, fz, C{}), (V)0, Eeff, tb,
                                 XP, cf, cb, 0.f, 0.f, dec, nullptr, nullptr, compact))
             goto timed_out;
         }
         ++ell;
       }
       if (mode == 1) {
-        __syncthreads();
+        unit_sync<GW>();
         continue;
       }
 
@@ -840,7 +886,7 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
         DT ab{c_from(s, fv, C{}), c_from(B, fv, C{})};
         DT dcf, dcb;
         int dec;
-        if (!exchange<OpD, C>(L, tc, epoch, xc, af, ab, (V)0, Eeff, tb, XD, dcf, dcb, 0.f, 0.f, dec, nullptr,
+        if (!exchange<OpD, C, GW>(L, tc, epoch, xc, af, ab, (V)0, Eeff, tb, XD, dcf, dcb, 0.f, 0.f, dec, nullptr,
                               nullptr))
           goto timed_out;
         int F = 0;
@@ -853,7 +899,7 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
 #pragma unroll
         for (int k = E - 1; k >= 0; --k)
           if (k < Eeff) {
-            sm_v[k * kThreads + tid] = BB;   // temp: backward distance sums
+            sm_v[k * NT + tid] = BB;   // temp: backward distance sums
             BB = lam * (BB + ss + xn[k] * sc);
             ss = lam * (ss + xn[k] * sc);
           }
@@ -863,12 +909,12 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
           if (k < Eeff) {
             AA = lam * (AA + pp);
             pp = lam * pp + xn[k] * sc;
-            if (k < ne) wpart += ldexp((double)xu[k] * (double)(AA + sm_v[k * kThreads + tid]), fu + F);
+            if (k < ne) wpart += ldexp((double)xu[k] * (double)(AA + sm_v[k * NT + tid]), fu + F);
           }
         wpart *= P.h_fast;
         float wh = 0.f, wl = 0.f;
         PT z0 = OpP::zero(), c0, c1;
-        if (!exchange<OpP, C>(L, tc, epoch, xc, z0, z0, wpart, Eeff, tb, XP, c0, c1, 0.f, 0.f, dec, &wh,
+        if (!exchange<OpP, C, GW>(L, tc, epoch, xc, z0, z0, wpart, Eeff, tb, XP, c0, c1, 0.f, 0.f, dec, &wh,
                               &wl))
           goto timed_out;
         wpart = (double)wh + (double)wl;
@@ -894,14 +940,14 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
         L.results[pid] = R;
       }
     }
-    __syncthreads();
+    unit_sync<GW>();
     continue;
   timed_out:
     if (rank == 0 && tid == 0) {
       PairResult R{NAN, NAN, 0, FS1_ETIMEOUT, 0};
       L.results[pid] = R;
     }
-    return;
+    return false;
   }
   // the team's queue is empty: its CTAs go on as the teams of the next level
   if (!kLevels || ++lvl >= L.nlevel) break;
@@ -912,7 +958,40 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
   // the level's slots start zeroed (tag 0): keep the compact slots' 8-bit
   // tags of its first two exchanges away from 0
   if (((epoch + 1u) & 0xFFu) == 0u || ((epoch + 2u) & 0xFFu) == 0u) epoch += 2u;
-  __syncthreads();   // sm_item is rewritten by the next ticket
+  unit_sync<GW>();   // sm_item is rewritten by the next ticket
+  }
+  return true;
+}
+
+template <class V, class C, int E, int G, int GW>
+__device__ __noinline__ bool unit_phase(const TeamLaunch& L, unsigned char* smem_raw, UnitSmem<C, GW>* us) {
+  return team_body<V, C, E, G, GW>(L, 0, smem_raw, us);
+}
+
+// The kernel: the pair loop of 16-warp units (team members); then, in the
+// generic stabilised instantiation and when the launch has units' queues,
+// units of 4 warps, each of which goes on as 4 units of one warp once its
+// queue is empty.  The 16-warp units' shared state is reused by the narrower
+// units after a block barrier; the units of 4 and of 1 warp have separate
+// shared state (a unit of 4 may still run while its neighbour has gone on as
+// single warps).
+template <class V, class C, int E, int G>
+__global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int mode) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr bool kUnits = G < E && std::is_same<C, XF>::value;
+  using S16 = UnitSmem<C, kWarps>;
+  using S4 = UnitSmem<C, 4>;
+  using S1 = UnitSmem<C, 1>;
+  constexpr size_t kOff1 = (sizeof(S4) + 15) / 16 * 16;
+  constexpr size_t kNarrow = kOff1 + sizeof(S1);
+  constexpr size_t kStat = kUnits && kNarrow > sizeof(S16) ? kNarrow : sizeof(S16);
+  __shared__ __align__(16) unsigned char stat[kStat];
+  if (!team_body<V, C, E, G, kWarps>(L, mode, smem_raw, reinterpret_cast<S16*>(stat))) return;
+  if constexpr (kUnits) {
+    if (!L.unit_queues || mode != 0) return;
+    __syncthreads();
+    if (!unit_phase<V, C, E, G, 4>(L, smem_raw, reinterpret_cast<S4*>(stat))) return;
+    unit_phase<V, C, E, G, 1>(L, smem_raw, reinterpret_cast<S1*>(stat + kOff1));
   }
 }
 

@@ -32,7 +32,7 @@ class fs1_config(Structure):
     _fields_ = [("variant", c_int), ("precision", c_int), ("check_every", c_int),
                 ("team_size", c_int), ("spin_cap", c_longlong), ("hbm_budget", c_size_t),
                 ("stream", c_void_p), ("autotune", c_int), ("trial_iters", c_int),
-                ("use_graph", c_int), ("tau", c_double), ("grid2d", c_int), ("reserved", c_int)]
+                ("use_graph", c_int), ("tau", c_double), ("grid2d", c_int), ("units", c_int)]
 
 
 class fs1_problem(Structure):
@@ -179,7 +179,8 @@ class Solver:
 
     def __init__(self, variant: str = "log", precision: str = "fp32", team_size: int = 0,
                  stream=None, spin_cap: int = 0, hbm_budget: int = 0, autotune: bool = True,
-                 use_graph: bool = True, trial_iters: int = 0, tau: float = 0.0, grid2d: bool = False):
+                 use_graph: bool = True, trial_iters: int = 0, tau: float = 0.0, grid2d: bool = False,
+                 units: bool = True):
         cfg = fs1_config_default()
         cfg.variant = {"log": FS1_VARIANT_LOG, "plain": FS1_VARIANT_PLAIN, "paper": FS1_VARIANT_PAPER}[variant]
         cfg.precision = FS1_FP32 if precision == "fp32" else FS1_FP64
@@ -192,6 +193,7 @@ class Solver:
         if tau:
             cfg.tau = float(tau)
         cfg.grid2d = 1 if grid2d else 0
+        cfg.units = 1 if units else 0
         if trial_iters:
             cfg.trial_iters = int(trial_iters)
         if stream is not None:
