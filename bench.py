@@ -239,11 +239,12 @@ def host_cores() -> int:
 
 def solve_ms(problems, infos) -> float:
     """Solve-kernel time of one call (ms) from its per-problem infos: problems of
-    one team or grid launch share that launch's time; a 1D pair streamed through
-    device memory (team size 0) reports the time of its own solve."""
+    one team or grid launch share that launch's time, and the 1D pairs streamed
+    through device memory (team size 0) share the time of their solves, which
+    run after the launches of the others."""
     streamed = [float(i.ms) for p, i in zip(problems, infos) if p.ndim == 1 and int(i.team_size) == 0]
     shared = [float(i.ms) for p, i in zip(problems, infos) if not (p.ndim == 1 and int(i.team_size) == 0)]
-    return (max(shared) if shared else 0.0) + sum(streamed)
+    return (max(shared) if shared else 0.0) + (max(streamed) if streamed else 0.0)
 
 
 def oracle_sample(workload, pairs_idx, iters, workers):

@@ -122,10 +122,11 @@ typedef struct fs1_problem {
                            (co-resident CTAs, 152 on a GB300) x 512 threads x 32
                            points (8 for plain FP64), and in the stabilised variant
                            at most max(1, floor(24 eps / h[0])) points per thread.
-                           A larger stabilised pair is solved with its state in
-                           device memory (fs1_info.team_size 0), after the call's
-                           other problems; a larger plain pair gives
-                           FS1_EUNSUPPORTED */
+                           A larger stabilised pair with h[0] / eps <= 5 is solved
+                           with its state in device memory (fs1_info.team_size 0),
+                           after the call's other problems, up to 8 such pairs
+                           sharing each launch; a larger pair of the plain variants
+                           or with h[0] / eps > 5 gives FS1_EUNSUPPORTED */
   double h[3];          /* grid spacings of the axes in the order of n */
   double eps;           /* entropic regularisation, > 0 */
   double tol;           /* stop when the column-marginal L1 error <= tol (>= 0) */

@@ -988,64 +988,105 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
   return FS1_OK;
 }
 
-// One stabilised 1D pair beyond the on-chip capacity: input check, then the
-// solve with the state in device memory (fs1_stream.cu), in the handle's
-// workspace after a head (result | check flag | descriptor | check partials).
-fs1_status run_stream(fs1_handle* h, const fs1_problem& p, PairResult& r, float* ms) {
-  const int64_t n = npoints(p);
-  const int nblk = (int)((n + kCheckBlock - 1) / kCheckBlock);
-  const size_t head = 1024 + align_up(sizeof(double) * 3 * (size_t)nblk, 256);
-  fs1_status s;
-  if ((s = ensure_ws(h, head + stream_workspace(n))) != FS1_OK) return s;
-  if ((s = ensure_pinned(h, &h->hdr, &h->hdr_bytes, sizeof(PairDesc))) != FS1_OK) return s;
-  if ((s = ensure_pinned(h, &h->hres, &h->hres_bytes, sizeof(PairResult) + sizeof(int))) != FS1_OK) return s;
-  char* ws = (char*)h->ws;
-  PairResult* d_res = (PairResult*)ws;
-  int* d_valid = (int*)(ws + 256);
-  PairDesc* d_desc = (PairDesc*)(ws + 512);
-  PairDesc d{};
-  d.a = p.a;
-  d.b = p.b;
-  d.n = n;
-  d.n_fast = n;
-  d.n_mid = 1;
-  d.n_slow = 1;
-  d.h_fast = p.h[0];
-  d.eps = p.eps;
-  d.tol = p.tol;
-  d.itr_max = p.itr_max;
-  d.f_out = p.f_out;
-  d.g_out = p.g_out;
-  d.f_init = p.f_init;
-  d.g_init = p.g_init;
-  const int in_f32 = p.dtype == FS1_FP32;
-  memcpy(h->hdr, &d, sizeof d);
-  cudaError_t e;
-  if ((e = cudaMemcpyAsync(d_desc, h->hdr, sizeof d, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
-    return cuda_fail(e, "descriptor copy");
-  check_range_kernel<<<nblk, 256, 0, h->stream>>>(d_desc, in_f32, (double*)(ws + 1024));
-  check_final_kernel<<<1, 32, 0, h->stream>>>((const double*)(ws + 1024), nblk, d_valid);
-  g_launches.fetch_add(2);
-  int* hval = (int*)((char*)h->hres + sizeof(PairResult));
-  if ((e = cudaMemcpyAsync(hval, d_valid, sizeof(int), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
-      (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
-    return cuda_fail(e, "input check");
-  if (!*hval) {
-    r = PairResult{NAN, NAN, 0, FS1_EINVAL, 0};
+// The call's stabilised 1D pairs beyond the on-chip capacity: input checks,
+// then the solves with the state in device memory (fs1_stream.cu), up to 8
+// pairs sharing each half-step launch.  The workspace holds a head (results |
+// check flags | descriptors | check partials per pair) and the pairs' arrays;
+// when the HBM budget cannot hold all of them at once they go one by one.
+fs1_status run_stream_batch(fs1_handle* h, const std::vector<const fs1_problem*>& ps, std::vector<PairResult>& rs,
+                            float* ms) {
+  const int count = (int)ps.size();
+  std::vector<int64_t> n(count);
+  std::vector<int> nblk(count);
+  std::vector<size_t> poff(count);
+  size_t head = align_up(sizeof(PairResult) * count, 256) + align_up(sizeof(int) * count, 256) +
+                align_up(sizeof(PairDesc) * count, 256);
+  for (int i = 0; i < count; ++i) {
+    n[i] = npoints(*ps[i]);
+    nblk[i] = (int)((n[i] + kCheckBlock - 1) / kCheckBlock);
+    poff[i] = head;
+    head += align_up(sizeof(double) * 3 * (size_t)nblk[i], 256);
+  }
+  fs1_status s = ensure_ws(h, head + stream_workspace(n.data(), count));
+  if (s == FS1_ENOMEM && count > 1) {
+    rs.assign(count, PairResult{NAN, NAN, 0, FS1_ENOMEM, 0});
     *ms = 0.f;
+    for (int i = 0; i < count; ++i) {
+      std::vector<PairResult> one;
+      float m = 0.f;
+      if ((s = run_stream_batch(h, {ps[i]}, one, &m)) != FS1_OK) return s;
+      rs[i] = one[0];
+      *ms += m;
+    }
     return FS1_OK;
   }
+  if (s != FS1_OK) return s;
+  if ((s = ensure_pinned(h, &h->hdr, &h->hdr_bytes, sizeof(PairDesc) * count)) != FS1_OK) return s;
+  if ((s = ensure_pinned(h, &h->hres, &h->hres_bytes, (sizeof(PairResult) + sizeof(int)) * count)) != FS1_OK)
+    return s;
+  char* ws = (char*)h->ws;
+  PairResult* d_res = (PairResult*)ws;
+  int* d_valid = (int*)(ws + align_up(sizeof(PairResult) * count, 256));
+  PairDesc* d_desc = (PairDesc*)((char*)d_valid + align_up(sizeof(int) * count, 256));
+  std::vector<PairDesc> desc(count);
+  std::vector<int> f32(count);
+  for (int i = 0; i < count; ++i) {
+    const fs1_problem& p = *ps[i];
+    PairDesc d{};
+    d.a = p.a;
+    d.b = p.b;
+    d.n = n[i];
+    d.n_fast = n[i];
+    d.n_mid = 1;
+    d.n_slow = 1;
+    d.h_fast = p.h[0];
+    d.eps = p.eps;
+    d.tol = p.tol;
+    d.itr_max = p.itr_max;
+    d.f_out = p.f_out;
+    d.g_out = p.g_out;
+    d.f_init = p.f_init;
+    d.g_init = p.g_init;
+    desc[i] = d;
+    f32[i] = p.dtype == FS1_FP32;
+  }
+  memcpy(h->hdr, desc.data(), sizeof(PairDesc) * count);
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(d_desc, h->hdr, sizeof(PairDesc) * count, cudaMemcpyHostToDevice, h->stream)) !=
+      cudaSuccess)
+    return cuda_fail(e, "descriptor copy");
+  for (int i = 0; i < count; ++i) {
+    check_range_kernel<<<nblk[i], 256, 0, h->stream>>>(d_desc + i, f32[i], (double*)(ws + poff[i]));
+    check_final_kernel<<<1, 32, 0, h->stream>>>((const double*)(ws + poff[i]), nblk[i], d_valid + i);
+  }
+  g_launches.fetch_add(2 * count);
+  int* hval = (int*)((char*)h->hres + sizeof(PairResult) * count);
+  if ((e = cudaMemcpyAsync(hval, d_valid, sizeof(int) * count, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
+    return cuda_fail(e, "input check");
+  rs.assign(count, PairResult{NAN, NAN, 0, FS1_EINVAL, 0});
+  *ms = 0.f;
+  std::vector<PairDesc> dv;
+  std::vector<int> fv, idx;
+  for (int i = 0; i < count; ++i)
+    if (hval[i]) {
+      dv.push_back(desc[i]);
+      fv.push_back(f32[i]);
+      idx.push_back(i);
+    }
+  if (dv.empty()) return FS1_OK;
+  const int nv = (int)dv.size();
   cudaEventRecord(h->ev0, h->stream);
   long long nl = 0;
-  const int ls = solve_stream_1d(d, in_f32, d_res, ws + head, h->ws_bytes - head, h->stream, &nl);
+  const int ls = solve_stream_batch(dv.data(), fv.data(), nv, d_res, ws + head, h->ws_bytes - head, h->stream, &nl);
   g_launches.fetch_add(nl);
   if (ls != FS1_OK) return (fs1_status)ls;
   cudaEventRecord(h->ev1, h->stream);
   PairResult* hr = (PairResult*)h->hres;
-  if ((e = cudaMemcpyAsync(hr, d_res, sizeof(PairResult), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
+  if ((e = cudaMemcpyAsync(hr, d_res, sizeof(PairResult) * nv, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
       (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
     return cuda_fail(e, "streaming solve");
-  r = *hr;
+  for (int k = 0; k < nv; ++k) rs[idx[k]] = hr[k];
   if (cudaEventElapsedTime(ms, h->ev0, h->ev1) != cudaSuccess) {
     cudaGetLastError();
     *ms = NAN;
@@ -1231,8 +1272,9 @@ fs1_status fs1_solve_batch(fs1_handle* h, const fs1_problem* probs, int64_t coun
     }
   }
   // 1D pairs beyond the team kernel's on-chip capacity: the stabilised
-  // variant solves them with the state in device memory, one at a time after
-  // the launches below; the plain variants report FS1_EUNSUPPORTED for them
+  // variant solves them with the state in device memory after the launches
+  // below (h / eps at most kStreamMaxC); the plain variants and larger h / eps
+  // report FS1_EUNSUPPORTED for them
   std::vector<char> streamed(count, 0);
   if (kind != KK_PAPER_F64) {
     int maxc = -1;
@@ -1241,7 +1283,7 @@ fs1_status fs1_solve_batch(fs1_handle* h, const fs1_problem* probs, int64_t coun
       if (maxc < 0) maxc = max_coresident_ctas(kind);
       if (maxc <= 0) break;
       if (min_ctas(kind, staged[i]) > std::min(maxc, kMaxTeamCtas)) {
-        if (kind == KK_LOG_F32)
+        if (kind == KK_LOG_F32 && staged[i].h[0] / staged[i].eps <= kStreamMaxC)
           streamed[i] = 1;
         else
           pst[i] = FS1_EUNSUPPORTED;
@@ -1285,19 +1327,30 @@ fs1_status fs1_solve_batch(fs1_handle* h, const fs1_problem* probs, int64_t coun
       ms[idx[j]] = gms;
     }
   }
-  for (int64_t i = 0; i < count; ++i) {
-    if (!streamed[i]) continue;
-    PairResult r;
-    float sms = 0.f;
-    const fs1_status s = run_stream(h, staged[i], r, &sms);
-    if (s != FS1_OK) {
-      pst[i] = s;
-      continue;
+  {
+    std::vector<const fs1_problem*> sp;
+    std::vector<int64_t> si;
+    for (int64_t i = 0; i < count; ++i)
+      if (streamed[i]) {
+        sp.push_back(&staged[i]);
+        si.push_back(i);
+      }
+    if (!sp.empty()) {
+      std::vector<PairResult> r;
+      float sms = 0.f;
+      const fs1_status s = run_stream_batch(h, sp, r, &sms);
+      for (size_t k = 0; k < si.size(); ++k) {
+        const int64_t i = si[k];
+        if (s != FS1_OK) {
+          pst[i] = s;
+          continue;
+        }
+        res[i] = r[k];
+        pst[i] = (fs1_status)r[k].status;
+        team[i] = 0;
+        ms[i] = sms;
+      }
     }
-    res[i] = r;
-    pst[i] = (fs1_status)r.status;
-    team[i] = 0;
-    ms[i] = sms;
   }
   // copy host-located outputs back
   for (int64_t i = 0; i < count; ++i) {

@@ -112,11 +112,17 @@ int launch_cluster_2d(const PairDesc* d, int count, int in_f32, PairResult* resu
                       size_t ws_bytes, void* stream, long long* launches);
 
 // Stabilised 1D solver with the state in device memory (fs1_stream.cu), for
-// a pair beyond the team kernel's on-chip capacity: workspace bytes for N
-// points, and the solve (d_result: device; *launches: kernels issued).
-size_t stream_workspace(int64_t n);
-int solve_stream_1d(const PairDesc& host_desc, int in_f32, PairResult* d_result, void* ws, size_t ws_bytes,
-                    void* stream, long long* launches);
+// pairs beyond the team kernel's on-chip capacity: workspace bytes for pairs
+// of n[0 .. count) points, and the solve of count pairs (host descriptors;
+// d_results: device array of count; *launches: kernels issued), up to 8
+// pairs sharing each half-step launch.
+size_t stream_workspace(const int64_t* n, int count);
+// largest h / eps of a streamed pair: the 16 values of a thread's run share
+// one FP32 frame, so they may span at most 16 h / eps = 80 nats (e^-80 is
+// still a normal FP32 number relative to the run's largest value)
+constexpr double kStreamMaxC = 5.0;
+int solve_stream_batch(const PairDesc* host_desc, const int* in_f32, int count, PairResult* d_results, void* ws,
+                       size_t ws_bytes, void* stream, long long* launches);
 
 // Paper-form solver (fs1_paper.cu): one CTA per pair, N <= kMaxPaperN.
 constexpr int kMaxPaperN = 16384;

@@ -23,7 +23,10 @@
 //             iteration count after a u-half.
 // Every launch first reads the stop flag and returns once the loop has
 // ended, so the host issues iterations in captured blocks and reads the flag
-// between blocks.
+// between blocks.  Up to kMaxStreamPairs pairs share the launches: the grid
+// covers the chunks of all of them (each chunk finds its pair from the
+// chunk offsets), every pair keeps its own loop state and last-chunk ticket,
+// and a pair that stops lowers a count of active pairs that the host polls.
 //
 // State: per point an FP32 value relative to a power-of-two frame shared by
 // the 16 points of a thread (4 + 0.25 bytes per point), as the team kernel
@@ -33,7 +36,9 @@
 // is formed as in the team kernel with the distance-weighted operator
 // (OpDist): chunk aggregates, a sequential scan over the chunks, and the
 // per-chunk sums of u (A + B) in FP64.
+#include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "fs1_team.cuh"
 
@@ -86,6 +91,16 @@ struct StreamArgs {
   double* f_out;
   double* g_out;
 };
+
+// pairs of one batch of launches (the kernel parameter holds their arguments)
+constexpr int kMaxStreamPairs = 8;
+struct StreamBatch {
+  int npairs;
+  int* nactive;                     // pairs whose loop has not ended
+  int choff[kMaxStreamPairs + 1];   // first chunk (CTA) of each pair in the grid
+  StreamArgs A[kMaxStreamPairs];
+};
+static_assert(sizeof(StreamBatch) <= 4000, "kernel parameter size");
 
 // decay tables of a CTA whose threads hold Eeff "points" of decay exp(-c) each
 __device__ void fill_tables(DecayTables<XF>& tb, double c, int Eeff) {
@@ -261,16 +276,19 @@ __device__ __forceinline__ void copy_tables(DecayTables<XF>& tb, const DecayTabl
   for (int i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = src[i];
 }
 
-// One half-step over the chunks (vhalf 1: y = K^T u, v_new = b / y and the
-// error of the accepted v; vhalf 0: y = K v, u = a / y).
-__global__ void __launch_bounds__(kThreads, 2) stream_step_kernel(StreamArgs A, int vhalf) {
+// One half-step over the chunks of the batch's pairs (vhalf 1: y = K^T u,
+// v_new = b / y and the error of the accepted v; vhalf 0: y = K v, u = a / y).
+__global__ void __launch_bounds__(kThreads, 2) stream_step_kernel(const __grid_constant__ StreamBatch B, int vhalf) {
   __shared__ DecayTables<XF> tb;
   __shared__ XchgSmem<XF> X;
   __shared__ XF sw[2 * kWarps];
   __shared__ float sred[2 * kWarps];
   __shared__ double sdred[kWarps];
   __shared__ int sstop, spar, slast;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, ch = blockIdx.x;
+  int pr = 0;
+  while (pr + 1 < B.npairs && B.choff[pr + 1] <= (int)blockIdx.x) ++pr;
+  const StreamArgs& A = B.A[pr];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, ch = (int)blockIdx.x - B.choff[pr];
   if (tid == 0) {
     sstop = A.st->stop;
     spar = A.st->par;
@@ -344,6 +362,12 @@ __global__ void __launch_bounds__(kThreads, 2) stream_step_kernel(StreamArgs A, 
   const float4* mq = reinterpret_cast<const float4*>(M + (size_t)ch * kChunk) + tid;
   const float4* vq = reinterpret_cast<const float4*>(A.V[par] + (size_t)ch * kChunk) + tid;
   const int fo = vhalf ? A.FV[par][run] : 0;
+  // error terms v_old y - m: v_old y scaled by 2^(fo + F) in FP32 when that
+  // scale keeps the product in range (|fo + F| <= 60: v_old y is within
+  // 2^-60 .. 2^60 of the mass it is compared with), in extended range otherwise
+  const int fe = fo + F;
+  const bool fast = fe >= -60 && fe <= 60;
+  const float s2 = fast ? pow2f(fe) : 0.f;
   float s = c_to(cb, F), ep = 0.f;
 #pragma unroll
   for (int q = kSE / 4 - 1; q >= 0; --q) {
@@ -357,7 +381,12 @@ __global__ void __launch_bounds__(kThreads, 2) stream_step_kernel(StreamArgs A, 
       const int k = 4 * q + i;
       const float y = xn[k] + s;
       // masses past the end are zero, so are their outputs and error terms
-      if (vhalf) ep += fabsf(c_to(c_mul(XF{vv[i], fo}, XF{y, F}), 0) - mm[i]);
+      if (vhalf) {
+        if (fast)
+          ep += fabsf(vv[i] * y * s2 - mm[i]);
+        else
+          ep += fabsf(c_to(c_mul(XF{vv[i], fo}, XF{y, F}), 0) - mm[i]);
+      }
       xn[k] = vdiv(mm[i], y);
       s = lam * (s + x[k] * sc);
     }
@@ -404,15 +433,12 @@ __global__ void __launch_bounds__(kThreads, 2) stream_step_kernel(StreamArgs A, 
       for (int w = 0; w < kWarps; ++w) err += sdred[w];
       StreamState* st = A.st;
       st->err = err;
-      if (!isfinite(err)) {
+      const int status = !isfinite(err) ? FS1_ENUMERIC
+                                        : (err <= A.tol ? FS1_OK : (st->ell >= A.itr_max ? FS1_ENOTCONV : -1));
+      if (status >= 0) {
         st->stop = 1;
-        st->status = FS1_ENUMERIC;
-      } else if (err <= A.tol) {
-        st->stop = 1;
-        st->status = FS1_OK;
-      } else if (st->ell >= A.itr_max) {
-        st->stop = 1;
-        st->status = FS1_ENOTCONV;
+        st->status = status;
+        atomicSub(B.nactive, 1);
       } else {
         st->par = par ^ 1;   // accept v_new
       }
@@ -584,27 +610,12 @@ __global__ void stream_final_kernel(StreamArgs A) {
 
 size_t align256s(size_t x) { return (x + 255) / 256 * 256; }
 
-}  // namespace
-
-size_t stream_workspace(int64_t n) {
-  const size_t nch = (size_t)((n + kChunk - 1) / kChunk);
-  const size_t pts = nch * kChunk;
-  return 5 * align256s(sizeof(float) * pts) + 3 * align256s(sizeof(int) * nch * kThreads) +
-         7 * align256s(sizeof(XF) * nch) + align256s(sizeof(DecayTables<XF>)) + align256s(sizeof(float) * 2 * nch) +
-         4 * align256s(sizeof(PairC<XF>) * nch) + align256s(sizeof(double) * nch) + 256 + 256;
-}
-
-int solve_stream_1d(const PairDesc& P, int in_f32, PairResult* d_result, void* ws, size_t ws_bytes, void* stream,
-                    long long* launches) {
-  cudaStream_t st = (cudaStream_t)stream;
-  if (P.n < 1) return FS1_EINVAL;
-  if (stream_workspace(P.n) > ws_bytes) return FS1_ENOMEM;
-  const int64_t nch64 = (P.n + kChunk - 1) / kChunk;
-  if (nch64 > (1 << 30)) return FS1_EUNSUPPORTED;
-  const int nch = (int)nch64;
+// Lays out one pair's arrays from p (advanced past them) and fills its
+// arguments.
+StreamArgs stream_args(const PairDesc& P, int in_f32, PairResult* d_result, char*& p) {
+  const int nch = (int)((P.n + kChunk - 1) / kChunk);
   const size_t pts = (size_t)nch * kChunk;
   const size_t runs = (size_t)nch * kThreads;
-  char* p = (char*)ws;
   StreamArgs A{};
   A.a = P.a;
   A.b = P.b;
@@ -643,19 +654,43 @@ int solve_stream_1d(const PairDesc& P, int in_f32, PairResult* d_result, void* w
   A.f_out = P.f_out;
   A.g_out = P.g_out;
   if (A.f_init == nullptr || A.g_init == nullptr) A.f_init = A.g_init = nullptr;
-  long long nl = 0;
+  return A;
+}
+
+// Pairs P[0 .. count) (at most kMaxStreamPairs) through the shared launches.
+int solve_stream_group(const PairDesc* P, const int* in_f32, int count, PairResult* d_results, char* p,
+                       cudaStream_t st, long long& nl) {
+  StreamBatch B{};
+  B.npairs = count;
+  B.nactive = (int*)p;
+  p += 256;
+  int grid = 0;
+  long long itr_max = 0;
+  for (int i = 0; i < count; ++i) {
+    B.A[i] = stream_args(P[i], in_f32[i], d_results + i, p);
+    B.choff[i] = grid;
+    grid += B.A[i].nch;
+    itr_max = std::max<long long>(itr_max, (long long)P[i].itr_max);
+  }
+  B.choff[count] = grid;
   cudaError_t e;
-  stream_init_kernel<<<nch, kThreads, 0, st>>>(A);
-  ++nl;
+  if ((e = cudaMemcpyAsync(B.nactive, &B.npairs, sizeof(int), cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+    fprintf(stderr, "fs1: streaming solve failed: %s\n", cudaGetErrorString(e));
+    return FS1_ECUDA;
+  }
+  for (int i = 0; i < count; ++i) {
+    stream_init_kernel<<<B.A[i].nch, kThreads, 0, st>>>(B.A[i]);
+    ++nl;
+  }
   // Iterations in blocks of 16 (two launches each), captured once as a CUDA
   // graph (direct launches if capture is unavailable).  One block stays in
-  // flight ahead of the host: the stop flag copied after block k is read
+  // flight ahead of the host: the active count copied after block k is read
   // after block k + 1 has been issued (launches after the stop return at once).
   const int block = 16;
   auto issue_block = [&]() {
     for (int i = 0; i < block; ++i) {
-      stream_step_kernel<<<nch, kThreads, 0, st>>>(A, 1);
-      stream_step_kernel<<<nch, kThreads, 0, st>>>(A, 0);
+      stream_step_kernel<<<grid, kThreads, 0, st>>>(B, 1);
+      stream_step_kernel<<<grid, kThreads, 0, st>>>(B, 0);
     }
   };
   cudaGraph_t graph = nullptr;
@@ -667,9 +702,9 @@ int solve_stream_1d(const PairDesc& P, int in_f32, PairResult* d_result, void* w
       exec = nullptr;
   }
   cudaGetLastError();
-  int* h_stop = nullptr;
+  int* h_active = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};
-  if ((e = cudaMallocHost(&h_stop, 2 * sizeof(int))) != cudaSuccess) {
+  if ((e = cudaMallocHost(&h_active, 2 * sizeof(int))) != cudaSuccess) {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     return FS1_ENOMEM;
@@ -682,35 +717,74 @@ int solve_stream_1d(const PairDesc& P, int in_f32, PairResult* d_result, void* w
     else
       issue_block();
     nl += 2 * block;
-    cudaMemcpyAsync(h_stop + slot, &A.st->stop, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(h_active + slot, B.nactive, sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaEventRecord(ev[slot], st);
   };
-  const long long max_blocks = P.itr_max / block + 3;   // the loop ends by then in any case
+  const long long max_blocks = itr_max / block + 3;   // every loop ends by then in any case
   run_block(0);
   for (long long k = 0;; ++k) {
     if (k + 1 < max_blocks) run_block((int)((k + 1) & 1));
     if ((e = cudaEventSynchronize(ev[k & 1])) != cudaSuccess) break;
-    if (h_stop[k & 1] || k + 1 >= max_blocks) break;
+    if (h_active[k & 1] <= 0 || k + 1 >= max_blocks) break;
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e == cudaSuccess) e = cudaGetLastError();
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
-  cudaFreeHost(h_stop);
+  cudaFreeHost(h_active);
   if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
     fprintf(stderr, "fs1: streaming solve failed: %s\n", cudaGetErrorString(e));
     return FS1_ECUDA;
   }
-  stream_cost_agg_kernel<<<nch, kThreads, 0, st>>>(A);
-  stream_cost_carry_kernel<<<1, 32, 0, st>>>(A);
-  stream_cost_kernel<<<nch, kThreads, 0, st>>>(A);
-  stream_final_kernel<<<(P.f_out || P.g_out) ? 1024 : 1, 256, 0, st>>>(A);
-  nl += 4;
+  for (int i = 0; i < count; ++i) {
+    const StreamArgs& A = B.A[i];
+    stream_cost_agg_kernel<<<A.nch, kThreads, 0, st>>>(A);
+    stream_cost_carry_kernel<<<1, 32, 0, st>>>(A);
+    stream_cost_kernel<<<A.nch, kThreads, 0, st>>>(A);
+    stream_final_kernel<<<(A.f_out || A.g_out) ? 1024 : 1, 256, 0, st>>>(A);
+    nl += 4;
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) {
     fprintf(stderr, "fs1: streaming solve failed: %s\n", cudaGetErrorString(e));
     return FS1_ECUDA;
+  }
+  return FS1_OK;
+}
+
+}  // namespace
+
+size_t stream_workspace(const int64_t* n, int count) {
+  size_t b = 0;
+  for (int i = 0; i < count; ++i) {
+    if (i % kMaxStreamPairs == 0) b += 256;   // a group's active count
+    const size_t nch = (size_t)((n[i] + kChunk - 1) / kChunk);
+    const size_t pts = nch * kChunk;
+    b += 5 * align256s(sizeof(float) * pts) + 3 * align256s(sizeof(int) * nch * kThreads) +
+         7 * align256s(sizeof(XF) * nch) + align256s(sizeof(DecayTables<XF>)) + align256s(sizeof(float) * 2 * nch) +
+         4 * align256s(sizeof(PairC<XF>) * nch) + align256s(sizeof(double) * nch) + 256;
+  }
+  return b;
+}
+
+int solve_stream_batch(const PairDesc* P, const int* in_f32, int count, PairResult* d_results, void* ws,
+                       size_t ws_bytes, void* stream, long long* launches) {
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<int64_t> n(count);
+  for (int i = 0; i < count; ++i) {
+    if (P[i].n < 1) return FS1_EINVAL;
+    if ((P[i].n + kChunk - 1) / kChunk > (1 << 30)) return FS1_EUNSUPPORTED;
+    n[i] = P[i].n;
+  }
+  if (stream_workspace(n.data(), count) > ws_bytes) return FS1_ENOMEM;
+  char* p = (char*)ws;
+  long long nl = 0;
+  for (int g = 0; g < count; g += kMaxStreamPairs) {
+    const int m = std::min(kMaxStreamPairs, count - g);
+    const int r = solve_stream_group(P + g, in_f32 + g, m, d_results + g, p, st, nl);
+    if (r != FS1_OK) return r;
+    p += stream_workspace(n.data() + g, m);
   }
   if (launches) *launches = nl;
   return FS1_OK;

@@ -24,10 +24,11 @@ def test_solve_ms_shared_launch():
     assert bench.solve_ms([_p(2), _p(3)], [_i(7.5, 0), _i(7.5, 0)]) == 7.5
 
 
-def test_solve_ms_streamed_pairs_add_up():
-    # 1D pairs streamed through device memory (team size 0) run one after another
-    assert bench.solve_ms([_p(1)] * 4, [_i(2.0, 0), _i(3.0, 0), _i(2.5, 0), _i(1.5, 0)]) == 9.0
-    # a mixed call: the team launch plus the streamed pair
+def test_solve_ms_streamed_pairs_share_their_solve():
+    # 1D pairs streamed through device memory (team size 0) share the launches
+    # of one streamed solve, which report its time
+    assert bench.solve_ms([_p(1)] * 4, [_i(9.0, 0)] * 4) == 9.0
+    # a mixed call: the team launch, then the streamed pairs
     assert bench.solve_ms([_p(1), _p(1), _p(1)], [_i(4.0, 8), _i(4.0, 8), _i(6.0, 0)]) == 10.0
 
 

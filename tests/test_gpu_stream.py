@@ -1,7 +1,7 @@
 """Stabilised 1D pairs beyond the team kernel's on-chip capacity: the solve
-with the state in device memory (chunks of 8192 points, three launches per
-half-step) against the FP64 oracle at the GPU's iteration count.  Tolerance:
-relative W1 1e-4 (FP32 variant)."""
+with the state in device memory (chunks of 8192 points, one launch per
+half-step shared by up to 8 pairs) against the FP64 oracle at the GPU's
+iteration count.  Tolerance: relative W1 1e-4 (FP32 variant)."""
 import numpy as np
 import pytest
 
@@ -133,3 +133,53 @@ def test_stream_input_check(env):
     assert infos[2].status == fs1.FS1_ENOTCONV
     ref = cref.solve(*small[:2], small[2], small[3], 0.0, 5, tau=1e10)
     assert abs(w[2] - ref.w) <= TOL32 * abs(ref.w)
+
+
+def test_stream_pairs_share_launches(env):
+    """Ten streamed pairs in one call (two groups of shared launches: 8 and 2)
+    ending at different iterations (caps, and one meeting tol), and one
+    refused by the input check: every pair gives the same bits as alone, and
+    two match the oracle."""
+    torch, fs1 = env
+    # h / eps = 4.8 allows 5 points per thread: 390 000 points and more stream
+    pairs = [_pair(60 + k, 400_000 + 7919 * k, 4.8) for k in range(9)] + [_pair(33, N_BEYOND, 1e-4)]
+    caps = [120, 40, 77, 100, 13, 120, 64, 90, 31, 300]
+    tols = [0.0] * 9 + [1e-3]   # the last pair stops at iteration 21 (as alone)
+    bad_a = pairs[3][0].copy()
+    bad_a[100] = -1e-6
+    pairs.insert(4, (bad_a, pairs[3][1], pairs[3][2], pairs[3][3]))
+    caps.insert(4, 50)
+    tols.insert(4, 0.0)
+    keep, probs = [], []
+    for (a, b, h, eps), cap, tol in zip(pairs, caps, tols):
+        ta = torch.tensor(a, dtype=torch.float32, device="cuda")
+        tb = torch.tensor(b, dtype=torch.float32, device="cuda")
+        keep += [ta, tb]
+        probs.append(fs1.Solver.problem(ta, tb, h, eps, tol, cap))
+    s = fs1.Solver("log", "fp32", autotune=False)
+    _, w, infos = s.solve(probs)
+    s.close()
+    assert infos[4].status == fs1.FS1_EINVAL
+    for k, (pair, cap, tol) in enumerate(zip(pairs, caps, tols)):
+        if k == 4:
+            continue
+        assert infos[k].team_size == 0, k
+        _, w1, i1 = _solve(env, [pair], cap, tol=tol)
+        assert (w1[0], i1[0].iters, i1[0].marginal_err) == (w[k], infos[k].iters, infos[k].marginal_err), k
+        if tol == 0.0:
+            assert infos[k].iters == cap and infos[k].status == fs1.FS1_ENOTCONV
+    assert infos[-1].status == fs1.FS1_OK and infos[-1].iters < 300
+    for k in (1, 5):
+        ref = _ref(pairs[k], int(infos[k].iters))
+        assert abs(w[k] - ref.w) <= TOL32 * abs(ref.w), (k, w[k], ref.w)
+
+
+def test_stream_refuses_large_h_over_eps(env):
+    """h / eps = 12 allows 2 points per thread on chip, and a streamed run of 16
+    points would span e^192, beyond one FP32 frame: a pair of 160 000 points is
+    refused (FS1_EUNSUPPORTED) while the call's other pair is solved."""
+    torch, fs1 = env
+    pairs = [_pair(80, 160_000, 12.0), _pair(81, 3000, 0.1)]
+    st, w, infos = _solve(env, pairs, 10)
+    assert infos[0].status == fs1.FS1_EUNSUPPORTED
+    assert infos[1].status == fs1.FS1_ENOTCONV and infos[1].iters == 10
