@@ -265,4 +265,51 @@ __device__ __forceinline__ int ld_relaxed(const int* p) {
   return v;
 }
 
+// one-dimensional bulk copy global -> shared (TMA), completion counted on an
+// mbarrier of this CTA; both addresses 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void mbar_init(unsigned long long* mbar) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(mbar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* mbar) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const unsigned m = (unsigned)__cvta_generic_to_shared(mbar);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(m), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d),
+               "l"(src), "r"(bytes), "r"(m)
+               : "memory");
+}
+// wait for phase `parity` of the mbarrier to complete; gives up (false)
+// after `cap` polls
+__device__ __forceinline__ bool mbar_wait(unsigned long long* mbar, unsigned parity, long long cap) {
+  const unsigned m = (unsigned)__cvta_generic_to_shared(mbar);
+  for (long long i = 0; i < cap; ++i) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(m), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// expect `bytes` more of transaction on the mbarrier's current phase (one
+// arrival: call once per phase, then issue the copies with bulk_copy)
+__device__ __forceinline__ void mbar_expect(unsigned long long* mbar, unsigned bytes) {
+  const unsigned m = (unsigned)__cvta_generic_to_shared(mbar);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(m), "r"(bytes) : "memory");
+}
+// a bulk copy counted against the bytes announced by mbar_expect
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes, unsigned long long* mbar) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const unsigned m = (unsigned)__cvta_generic_to_shared(mbar);
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d),
+               "l"(src), "r"(bytes), "r"(m)
+               : "memory");
+}
+
 }  // namespace fs1

@@ -52,10 +52,11 @@ constexpr int kChunk = kThreads * kSE;   // points per chunk (one CTA)
 struct StreamState {
   long long ell;   // completed iterations
   int stop;        // 1 once the loop has ended
-  int status;      // FS1_OK, FS1_ENOTCONV or FS1_ENUMERIC
+  int status;      // FS1_OK, FS1_ENOTCONV, FS1_ENUMERIC or FS1_ETIMEOUT
   int par;         // v buffer holding the accepted v
   unsigned done;   // chunks of the running launch that have finished
   double err;      // marginal error of the last v-half
+  int fail;        // 1: a chunk's staging copy did not complete in its bounded wait
 };
 
 struct StreamArgs {
@@ -263,7 +264,7 @@ __global__ void __launch_bounds__(kThreads, 1) stream_init_kernel(StreamArgs A) 
     A.agg_b[0][ch] = tbk;
     A.dec[ch] = c_decay((double)kChunk * (double)ch, A.c, XF{});
   }
-  if (ch == 0 && tid == 0) *A.st = StreamState{0, 0, FS1_OK, 0, 0u, NAN};
+  if (ch == 0 && tid == 0) *A.st = StreamState{0, 0, FS1_OK, 0, 0u, NAN, 0};
 }
 
 
@@ -278,7 +279,13 @@ __device__ __forceinline__ void copy_tables(DecayTables<XF>& tb, const DecayTabl
 
 // One half-step over the chunks of the batch's pairs (vhalf 1: y = K^T u,
 // v_new = b / y and the error of the accepted v; vhalf 0: y = K v, u = a / y).
+// The chunk's masses (and, in a v-half, its accepted v) are staged in shared
+// memory by bulk copies issued at the start, so that they arrive while the
+// carries are formed; dynamic shared memory: kChunk floats per staged array.
+constexpr unsigned kStageBytes = kChunk * sizeof(float);
 __global__ void __launch_bounds__(kThreads, 2) stream_step_kernel(const __grid_constant__ StreamBatch B, int vhalf) {
+  extern __shared__ __align__(16) float4 s_stage[];   // [masses | accepted v], kChunk / 4 each
+  __shared__ __align__(8) unsigned long long s_mbar;
   __shared__ DecayTables<XF> tb;
   __shared__ XchgSmem<XF> X;
   __shared__ XF sw[2 * kWarps];
@@ -293,11 +300,18 @@ __global__ void __launch_bounds__(kThreads, 2) stream_step_kernel(const __grid_c
     sstop = A.st->stop;
     spar = A.st->par;
     X.ok = 1;
+    mbar_init(&s_mbar);
   }
   copy_tables(tb, A.tabs);
   __syncthreads();
   if (sstop) return;
   const int par = spar;
+  if (tid == 0) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect(&s_mbar, vhalf ? 2 * kStageBytes : kStageBytes);
+    bulk_copy(s_stage, (vhalf ? A.BW : A.AW) + (size_t)ch * kChunk, kStageBytes, &s_mbar);
+    if (vhalf) bulk_copy(s_stage + kChunk / 4, A.V[par] + (size_t)ch * kChunk, kStageBytes, &s_mbar);
+  }
   // v-half: input u, output v[par ^ 1]; u-half: input the accepted v[par], output u
   const float* Xin = vhalf ? A.U : A.V[par];
   const int* Fin = vhalf ? A.FU : A.FV[par];
@@ -305,7 +319,6 @@ __global__ void __launch_bounds__(kThreads, 2) stream_step_kernel(const __grid_c
   float* Z = vhalf ? A.V[par ^ 1] : A.U;
   int* FZ = vhalf ? A.FV[par ^ 1] : A.FU;
   const int zsrc = vhalf ? 1 + (par ^ 1) : 0;
-  const float* M = vhalf ? A.BW : A.AW;
   const float lam = A.lamf;
   const size_t run = (size_t)ch * kThreads + tid;
   const XF zero = XF{0.f, kZeroExp};
@@ -359,8 +372,12 @@ __global__ void __launch_bounds__(kThreads, 2) stream_step_kernel(const __grid_c
     r = lam * r + x[k] * sc;
     xn[k] = r;
   }
-  const float4* mq = reinterpret_cast<const float4*>(M + (size_t)ch * kChunk) + tid;
-  const float4* vq = reinterpret_cast<const float4*>(A.V[par] + (size_t)ch * kChunk) + tid;
+  // the staged masses and accepted v (bounded wait; a copy that does not
+  // complete marks the pair failed and is waited for again before the CTA ends)
+  const bool staged = mbar_wait(&s_mbar, 0, 1ll << 24);
+  if (!staged && tid == 0) atomicExch(&A.st->fail, 1);
+  const float4* mq = s_stage + tid;
+  const float4* vq = s_stage + kChunk / 4 + tid;
   const int fo = vhalf ? A.FV[par][run] : 0;
   // error terms v_old y - m: v_old y scaled by 2^(fo + F) in FP32 when that
   // scale keeps the product in range (|fo + F| <= 60: v_old y is within
@@ -410,6 +427,7 @@ __global__ void __launch_bounds__(kThreads, 2) stream_step_kernel(const __grid_c
       A.errp[2 * ch + 1] = l;
     }
   }
+  if (!staged) mbar_wait(&s_mbar, 0, 1ll << 24);   // no copy may land after the CTA ends
   // the last chunk to finish takes the loop's bookkeeping
   __syncthreads();
   if (tid == 0) {
@@ -433,8 +451,10 @@ __global__ void __launch_bounds__(kThreads, 2) stream_step_kernel(const __grid_c
       for (int w = 0; w < kWarps; ++w) err += sdred[w];
       StreamState* st = A.st;
       st->err = err;
-      const int status = !isfinite(err) ? FS1_ENUMERIC
-                                        : (err <= A.tol ? FS1_OK : (st->ell >= A.itr_max ? FS1_ENOTCONV : -1));
+      const int status = st->fail ? FS1_ETIMEOUT
+                         : !isfinite(err)
+                             ? FS1_ENUMERIC
+                             : (err <= A.tol ? FS1_OK : (st->ell >= A.itr_max ? FS1_ENOTCONV : -1));
       if (status >= 0) {
         st->stop = 1;
         st->status = status;
@@ -445,8 +465,14 @@ __global__ void __launch_bounds__(kThreads, 2) stream_step_kernel(const __grid_c
       st->done = 0u;
     }
   } else if (tid == 0) {
-    A.st->ell += 1;   // a full iteration done
-    A.st->done = 0u;
+    StreamState* st = A.st;
+    st->ell += 1;   // a full iteration done
+    if (st->fail) {
+      st->stop = 1;
+      st->status = FS1_ETIMEOUT;
+      atomicSub(B.nactive, 1);
+    }
+    st->done = 0u;
   }
 }
 
@@ -689,10 +715,15 @@ int solve_stream_group(const PairDesc* P, const int* in_f32, int count, PairResu
   const int block = 16;
   auto issue_block = [&]() {
     for (int i = 0; i < block; ++i) {
-      stream_step_kernel<<<grid, kThreads, 0, st>>>(B, 1);
-      stream_step_kernel<<<grid, kThreads, 0, st>>>(B, 0);
+      stream_step_kernel<<<grid, kThreads, 2 * kStageBytes, st>>>(B, 1);
+      stream_step_kernel<<<grid, kThreads, kStageBytes, st>>>(B, 0);
     }
   };
+  if ((e = cudaFuncSetAttribute(stream_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(2 * kStageBytes))) != cudaSuccess) {
+    fprintf(stderr, "fs1: streaming solve failed: %s\n", cudaGetErrorString(e));
+    return FS1_ECUDA;
+  }
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
