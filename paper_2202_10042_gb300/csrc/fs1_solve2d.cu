@@ -81,6 +81,15 @@ struct Img2D {
                        // tiles (compensated pairs)
   double* wp;          // [nf nm] cost partials of the slow lines
   int* stop;           // 0 while active; 1 + k once stopped with the final v in V[k]
+  // FP32 block-frame state (launches of the FP32 path; see f32_geom)
+  int lp;              // padded row length (nf rounded up to 8)
+  int pf[3];           // points per lane of a line, per axis
+  float* U32;          // [ns][lp] u, frames U32F [ceil(ns / 8)][lp]
+  float* V32[2];       // v by iteration parity, frames V32F
+  float* Y32;          // [ns][lp] fast-pass output, frames Y32F [ns][lp / 8]
+  int* U32F;
+  int* V32F[2];
+  int* Y32F;
 };
 
 struct Launch2D {
@@ -442,7 +451,336 @@ __device__ void cta_sum_df(float& h, float& l, float* red) {
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
+// ---------------------------------------------------------------------------
+// FP32 block-frame path: 2D images whose lane chunks span at most 64 nats on
+// every axis of more than one point (c P <= 64 with c = h / eps and P the
+// points per lane: c <= 8 for lines of up to 256 points, about 4 up to 512,
+// 2 up to 1024).  Values are FP32 relative to a power-of-two frame shared by a
+// block of 8 points: u and v in blocks of 8 rows of one column (frames
+// [ceil(ns / 8)][Lp]), the fast pass's output Y in blocks of 8 columns of one
+// row (frames [ns][Lp / 8]); rows are padded to Lp = nf rounded up to 8, so
+// that lane chunks start 32-byte aligned.  Within a block values span at
+// most e^{8 c} <= e^64, and a value dropped below 2^-126 of its block's
+// largest contributes less than 2^-68 of that value's share to any output
+// (lam^{|i-j|} differs by at most e^{8 c} across the block): below FP32
+// rounding.  A pass converts its input blocks into one frame per lane chunk
+// (the chunk's largest value), runs the recurrences in FP32 as
+// line_scan_frame does, and writes its output normalised per block of its own
+// axis.  Per point this is FP32 arithmetic and a few exponent operations
+// instead of the per-point extended-range state of the general path.
+// ---------------------------------------------------------------------------
+constexpr int kBlk = 8;
+
+// lanes per line and points per lane (a multiple of 8: whole blocks per lane)
+__host__ __device__ inline void f32_geom(int L, int& G, int& P) {
+  G = L <= 128 ? 8 : (L <= 256 ? 16 : 32);
+  P = ((L + G - 1) / G + kBlk - 1) / kBlk * kBlk;
+}
+// floats per column of a slow-pass tile: G chunks of P + 1, rounded up to 4
+// mod 32
+__host__ __device__ inline int f32_cs(int G, int P) {
+  const int c = G * (P + 1);
+  return c + ((4 - c % 32) + 32) % 32;
+}
+// A lane chunk of P points of an axis with c = h / eps spans at most e^{c P};
+// one FP32 frame per chunk holds that when c P <= 64 nats (2^92, leaving 2^34
+// below FP32 rounding for the smallest value kept)
+constexpr double kF32MaxNats = 64.0;
+
+// Scan of the lane chunks of a segment of G lanes: x[0 .. n) holds the lane's
+// values in frame em (n = 0: no points); on return x[k] = (K x)_k of the line
+// in frame F (the return value).  The lane aggregates are joined by a
+// Kogge-Stone scan in extended range (tab: lam^j at j <= 32, lam^{P 2^i} at
+// kTabSeg + i); the lane's backward partials go to tb[k * ts] (shared memory).
+// Every lane of the warp calls.
+template <int P>
+__device__ __forceinline__ int chunk_scan(float (&x)[P], int n, int em, int G, const XF* tab, float lam, float* tb,
+                                          int ts) {
+  const int lane = threadIdx.x & (G - 1);
+  float r = 0.f, q = 0.f;
+#pragma unroll
+  for (int k = 0; k < P; ++k)
+    if (k < n) r = fmaf(lam, r, x[k]);
+#pragma unroll
+  for (int k = P - 1; k >= 0; --k)
+    if (k < n) q = lam * (q + x[k]);
+  XF xa = xf_norm(r, em), za = xf_norm(q, em);
+  if (n < P) xa = c_mul(xa, tab[P - n]);
+#pragma unroll
+  for (int lv = 0; lv < 5; ++lv) {
+    const int o = 1 << lv;
+    if (o >= G) break;
+    const XF y = shw_up(xa, o, G);
+    const XF w = shw_down(za, o, G);
+    if (lane >= o) xa = c_add(c_mul(y, tab[kTabSeg + lv]), xa);
+    if (lane + o < G) za = c_add(za, c_mul(w, tab[kTabSeg + lv]));
+  }
+  XF cfw = shw_up(xa, 1, G), cbw = shw_down(za, 1, G);
+  if (lane == 0) cfw = XF{0.f, kZeroExp};
+  if (lane == G - 1) cbw = XF{0.f, kZeroExp};
+  if (n <= 0) return kZeroExp;
+  const int F = max(em, max(cfw.e, cbw.e)) + 6;
+  const float s = pow2f(em - F);
+  const float sc_tail = n < P ? tab[P - n].m * pow2f(tab[P - n].e) : 1.f;
+  float sb = c_to(cbw, F) * sc_tail;
+#pragma unroll
+  for (int k = P - 1; k >= 0; --k)
+    if (k < n) {
+      tb[k * ts] = sb;
+      sb = lam * (sb + x[k] * s);
+    }
+  float p = c_to(cfw, F);
+#pragma unroll
+  for (int k = 0; k < P; ++k)
+    if (k < n) {
+      p = fmaf(lam, p, x[k] * s);
+      x[k] = p + tb[k * ts];
+    }
+  return F;
+}
+
+// Fast pass of a group of 32 / G rows (one warp, one G-lane segment per row)
+// on the FP32 state: row r of X (u or v, frames per 8-row block of a column)
+// to row r of Y (frames per 8-column block).  tb: the warp's P x 32 floats of
+// shared memory.
+template <int P>
+__device__ void row_pass_f32(const float* X, const int* XFr, float* Y, int* YFr, int nrows, int r0, int L, int Lp,
+                             int G, const XF* tab, float lam, float* tb) {
+  const int lane = threadIdx.x & 31, seg = lane / G, ls = lane & (G - 1);
+  const int r = r0 + seg;
+  const int j0 = ls * P;
+  const int n = r < nrows ? max(0, min(P, L - j0)) : 0;
+  float x[P];
+  int em = kZeroExp;
+  const float* xr = X + (int64_t)r * Lp + j0;
+  const int* fr = XFr + (int64_t)(r / kBlk) * Lp + j0;
+#pragma unroll
+  for (int k4 = 0; k4 < P / 4; ++k4) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    int4 f = make_int4(0, 0, 0, 0);
+    if (4 * k4 < n) {
+      v = *reinterpret_cast<const float4*>(xr + 4 * k4);
+      f = *reinterpret_cast<const int4*>(fr + 4 * k4);
+    }
+    const float vv[4] = {v.x, v.y, v.z, v.w};
+    const int ff[4] = {f.x, f.y, f.z, f.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int k = 4 * k4 + i;
+      x[k] = k < n ? vv[i] : 0.f;
+      if (x[k] != 0.f) em = max(em, ff[i] + fexp(x[k]));
+    }
+  }
+#pragma unroll
+  for (int k4 = 0; k4 < P / 4; ++k4)
+    if (4 * k4 < n) {
+      const int4 f = *reinterpret_cast<const int4*>(fr + 4 * k4);
+      const int ff[4] = {f.x, f.y, f.z, f.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) x[4 * k4 + i] *= pow2f(ff[i] - em);
+    }
+  const int F = chunk_scan<P>(x, n, em, G, tab, lam, tb + lane, 32);
+  if (n <= 0) return;
+  float* yr = Y + (int64_t)r * Lp + j0;
+  int* yf = YFr + (int64_t)r * (Lp / kBlk) + j0 / kBlk;
+#pragma unroll
+  for (int b = 0; b < P / kBlk; ++b)
+    if (kBlk * b < n) {
+      int fb = kZeroExp;
+#pragma unroll
+      for (int i = 0; i < kBlk; ++i)
+        if (kBlk * b + i < n) fb = max(fb, fexp(x[kBlk * b + i]));
+      const float sc = fb == kZeroExp ? 0.f : pow2f(-fb);
+      float o[kBlk];
+#pragma unroll
+      for (int i = 0; i < kBlk; ++i) o[i] = kBlk * b + i < n ? x[kBlk * b + i] * sc : 0.f;
+      reinterpret_cast<float4*>(yr + kBlk * b)[0] = make_float4(o[0], o[1], o[2], o[3]);
+      reinterpret_cast<float4*>(yr + kBlk * b)[1] = make_float4(o[4], o[5], o[6], o[7]);
+      yf[b] = fb == kZeroExp ? kZeroExp : F + fb;
+    }
+}
+
+// Slow pass of one tile of TW = 8 x 32 / G columns (the whole CTA) on the
+// FP32 state: stage the tile of Y and its block frames, scan every column in
+// G-lane segments, then the update z = mass / y of the half-step, normalised
+// per block of 8 rows of a column, with (v-half) the marginal-error terms of
+// the accepted v.  Shared memory: values [TW][CS] with chunks of P + 1 (an
+// odd stride: the lanes of a column read distinct banks) and CS = 4 mod 32
+// (a warp's staging writes, 8 columns x 4 rows, hit distinct banks); frames
+// [ns + ns / P][TW / 8], row r at r + r / P (the lanes of a column read
+// distinct banks); lane frames [TW][G].
+template <int P>
+__device__ void col_pass_f32(const Img2D& I, int tile, const float* Yv, const int* YFr, const void* mass, int in_f32,
+                             const float* Vold, const int* VFold, float* Z, int* ZF, bool vhalf, const XF* tab,
+                             float* sbuf, float& eh, float& el) {
+  const int G = I.g[1];
+  const int spw = 32 / G, TW = kTileCols * spw, nbt = TW / kBlk;
+  const int W = I.nf, Lp = I.lp, ns = I.ns;
+  const int col0 = tile * TW;
+  const int CS = f32_cs(G, P);
+  float* vals = sbuf;                                   // [TW][CS]
+  int* frs = reinterpret_cast<int*>(sbuf + TW * CS);    // [ns + ns / P][nbt]
+  int* lfs = frs + (ns + ns / P) * nbt;                 // [TW][G]
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < ns * TW; idx += kThreads2) {
+    const int r = idx / TW, c = idx - r * TW;
+    const int col = col0 + c;
+    const float v = col < W ? __ldcg(Yv + (int64_t)r * Lp + col) : 0.f;
+    vals[c * CS + (r / P) * (P + 1) + r % P] = v;
+  }
+  for (int idx = tid; idx < ns * nbt; idx += kThreads2) {
+    const int r = idx / nbt, b = idx - r * nbt;
+    const int blk = col0 / kBlk + b;
+    frs[(r + r / P) * nbt + b] = blk < Lp / kBlk ? __ldcg(YFr + (int64_t)r * (Lp / kBlk) + blk) : kZeroExp;
+  }
+  __syncthreads();
+  {
+    const int warp = tid >> 5, lane = tid & 31;
+    const int seg = lane / G, ls = lane & (G - 1);
+    const int c = warp * spw + seg;
+    const int n = col0 + c < W ? max(0, min(P, ns - ls * P)) : 0;
+    float* chunk = vals + c * CS + ls * (P + 1);
+    const int* fc = frs + (ls * (P + 1)) * nbt + c / kBlk;   // row ls P + k at (ls P + k + ls) nbt
+    float x[P];
+    int em = kZeroExp;
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      x[k] = k < n ? chunk[k] : 0.f;
+      if (x[k] != 0.f) em = max(em, fc[k * nbt] + fexp(x[k]));
+    }
+#pragma unroll
+    for (int k = 0; k < P; ++k)
+      if (k < n) x[k] *= pow2f(fc[k * nbt] - em);
+    const float lam = tab[1].m * pow2f(tab[1].e);
+    // backward partials in the chunk's own slots (x holds the chunk)
+    const int F = chunk_scan<P>(x, n, em, G, tab, lam, chunk, 1);
+#pragma unroll
+    for (int k = 0; k < P; ++k)
+      if (k < n) chunk[k] = x[k];
+    lfs[c * G + ls] = F;
+  }
+  __syncthreads();
+  // update: thread t takes column t % TW and blocks t / TW, t / TW + 256 / TW, ...
+  const int c = tid % TW;
+  const int col = col0 + c;
+  if (col < W) {
+    const int nb = (ns + kBlk - 1) / kBlk;
+    for (int blk = tid / TW; blk < nb; blk += kThreads2 / TW) {
+      const int r0 = blk * kBlk;
+      const int ls = r0 / P;
+      const int F = lfs[c * G + ls];
+      const float* yc = vals + c * CS + ls * (P + 1) + (r0 - ls * P);
+      float q[kBlk], m[kBlk];
+#pragma unroll
+      for (int i = 0; i < kBlk; ++i) m[i] = r0 + i < ns ? load_m(mass, (int64_t)(r0 + i) * W + col, in_f32) : 0.f;
+      int fb = kZeroExp;
+#pragma unroll
+      for (int i = 0; i < kBlk; ++i) {
+        q[i] = m[i] > 0.f ? __fdividef(m[i], yc[i]) : 0.f;
+        fb = max(fb, fexp(q[i]));
+      }
+      if (vhalf) {
+        // marginal-error terms |v_old y - m| of the accepted v
+        const int vf = __ldcg(VFold + (int64_t)blk * Lp + col);
+        const int fe = vf + F;
+        const bool fast = fe >= -60 && fe <= 60;
+        const float s2 = fast ? pow2f(fe) : 0.f;
+#pragma unroll
+        for (int i = 0; i < kBlk; ++i)
+          if (r0 + i < ns) {
+            const float vv = __ldcg(Vold + (int64_t)(r0 + i) * Lp + col);
+            const float pv = fast ? vv * yc[i] * s2 : c_to(c_mul(xf_norm(vv, vf), xf_norm(yc[i], F)), 0);
+            df_add(eh, el, fabsf(pv - m[i]), 0.f);
+          }
+      }
+      const float sc = fb == kZeroExp ? 0.f : pow2f(-fb);
+#pragma unroll
+      for (int i = 0; i < kBlk; ++i)
+        if (r0 + i < ns) Z[(int64_t)(r0 + i) * Lp + col] = q[i] * sc;
+      ZF[(int64_t)blk * Lp + col] = fb == kZeroExp ? kZeroExp : fb - F;
+    }
+  }
+  __syncthreads();   // the tile's shared memory is reused by the next tile
+}
+
+// the FP32 fast pass of row group grp of image I (dispatch on P)
+__device__ void row_f32(const Img2D& I, const float* X, const int* XFr, int grp, const XF* tab, float* tb) {
+  const int r0 = grp * (32 / I.g[0]);
+  const float lam = tab[1].m * pow2f(tab[1].e);
+  switch (I.pf[0]) {
+    case 8: row_pass_f32<8>(X, XFr, I.Y32, I.Y32F, I.ns, r0, I.nf, I.lp, I.g[0], tab, lam, tb); break;
+    case 16: row_pass_f32<16>(X, XFr, I.Y32, I.Y32F, I.ns, r0, I.nf, I.lp, I.g[0], tab, lam, tb); break;
+    case 24: row_pass_f32<24>(X, XFr, I.Y32, I.Y32F, I.ns, r0, I.nf, I.lp, I.g[0], tab, lam, tb); break;
+    default: row_pass_f32<32>(X, XFr, I.Y32, I.Y32F, I.ns, r0, I.nf, I.lp, I.g[0], tab, lam, tb); break;
+  }
+}
+
+// the FP32 slow pass of one tile (dispatch on P)
+__device__ void col_f32(const Img2D& I, int tile, const void* mass, int in_f32, const float* Vold, const int* VFold,
+                        float* Z, int* ZF, bool vhalf, const XF* tab, float* sbuf, float& eh, float& el) {
+  switch (I.pf[1]) {
+    case 8:
+      col_pass_f32<8>(I, tile, I.Y32, I.Y32F, mass, in_f32, Vold, VFold, Z, ZF, vhalf, tab, sbuf, eh, el);
+      break;
+    case 16:
+      col_pass_f32<16>(I, tile, I.Y32, I.Y32F, mass, in_f32, Vold, VFold, Z, ZF, vhalf, tab, sbuf, eh, el);
+      break;
+    case 24:
+      col_pass_f32<24>(I, tile, I.Y32, I.Y32F, mass, in_f32, Vold, VFold, Z, ZF, vhalf, tab, sbuf, eh, el);
+      break;
+    default:
+      col_pass_f32<32>(I, tile, I.Y32, I.Y32F, mass, in_f32, Vold, VFold, Z, ZF, vhalf, tab, sbuf, eh, el);
+      break;
+  }
+}
+
+// u (or v) of the FP32 state from log values (warm start) or 1 / N: one
+// thread per block of 8 rows of a column
+__device__ void init_f32(const Img2D& I, const double* logs, float* X, int* XFr) {
+  const int64_t N = (int64_t)I.nf * I.ns;
+  const XF init = xf_norm((float)(1.0 / (double)N), 0);
+  const int nb = (I.ns + kBlk - 1) / kBlk;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)nb * I.lp;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int blk = (int)(t / I.lp), col = (int)(t - (int64_t)blk * I.lp);
+    XF v[kBlk];
+    int fb = kZeroExp;
+#pragma unroll
+    for (int i = 0; i < kBlk; ++i) {
+      const int r = blk * kBlk + i;
+      v[i] = XF{0.f, kZeroExp};
+      if (r < I.ns && col < I.nf) v[i] = logs ? xf_from_log(logs[(int64_t)r * I.nf + col]) : init;
+      if (v[i].m != 0.f) fb = max(fb, v[i].e);
+    }
+#pragma unroll
+    for (int i = 0; i < kBlk; ++i) {
+      const int r = blk * kBlk + i;
+      if (r < I.ns) X[(int64_t)r * I.lp + col] = v[i].m != 0.f ? v[i].m * pow2f(v[i].e - fb) : 0.f;
+    }
+    XFr[(int64_t)blk * I.lp + col] = fb;
+  }
+}
+
+// u and the returned v of the FP32 state into the extended-range arrays the
+// cost phase and the potentials read
+__device__ void to_xf(const Img2D& I, int k) {
+  const int64_t N = (int64_t)I.nf * I.ns;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(p / I.nf), col = (int)(p - (int64_t)r * I.nf);
+    const int64_t q = (int64_t)r * I.lp + col, qf = (int64_t)(r / kBlk) * I.lp + col;
+    I.U[p] = xf_norm(I.U32[q], I.U32F[qf]);
+    I.V[k][p] = xf_norm(I.V32[k][q], I.V32F[k][qf]);
+  }
+}
+
+// F32: the launch's images all take the FP32 block-frame path (2D, lane
+// chunks of at most 64 nats on every axis); otherwise the per-point
+// extended-range state.  The FP32 path keeps a lane's chunk (up to 32
+// points) in registers; it is latency-bound, and three CTAs per SM (80
+// registers, a few spilled) ran 25 % faster on 800^2 and 1024^2 images than
+// two (121 registers, none spilled) and than four (64, spilling in the loops).
+template <bool F32>
+__global__ void __launch_bounds__(kThreads2, F32 ? 3 : 4) fs1_solve2d_kernel(Launch2D L) {
   extern __shared__ XF sline[];   // kWarps2 regions of L.line_stride XF
   __shared__ float sred[2 * kWarps2];
   __shared__ int srow[kMaxImg2D + 1], scol[kMaxImg2D + 1], stile[kMaxImg2D + 1];
@@ -474,6 +812,10 @@ __global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
       const Img2D& I = L.imgs[i];
       for (int ax = 0; ax < 3; ++ax) okd = okd && (I.g[ax] == 8 || I.g[ax] == 16 || I.g[ax] == 32);
       okd = okd && I.tw_s == kTileCols * (32 / max(1, I.g[1])) && I.tw_m == kTileCols * (32 / max(1, I.g[2]));
+      if (F32)
+        for (int ax = 0; ax < 2; ++ax)
+          okd = okd && I.nm == 1 && (I.pf[ax] == 8 || I.pf[ax] == 16 || I.pf[ax] == 24 || I.pf[ax] == 32) &&
+                I.g[ax] * I.pf[ax] >= (ax == 0 ? I.nf : I.ns) && I.lp % kBlk == 0 && I.lp >= I.nf;
     }
     if (!okd) {
       if (threadIdx.x == 0) atomicExch(L.abort_flag, 1);
@@ -494,7 +836,7 @@ __global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
     const Img2D& I = L.imgs[i];
     const double c = ax == 0 ? I.cf : (ax == 1 ? I.cs : I.cm);
     const int len = ax == 0 ? I.nf : (ax == 1 ? I.ns : I.nm);
-    const int Pseg = (len + I.g[ax] - 1) / I.g[ax], Pw = (len + 31) >> 5;
+    const int Pseg = F32 && ax < 2 ? I.pf[ax] : (len + I.g[ax] - 1) / I.g[ax], Pw = (len + 31) >> 5;
     const double k = j < kTabSeg ? (double)j
                    : (j < kTabWarp ? (double)Pseg * (double)(1 << (j - kTabSeg))
                                    : (double)Pw * (double)(1 << (j - kTabWarp)));
@@ -502,7 +844,12 @@ __global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
   }
   auto tab = [&](int i, int ax) -> const XF* { return L.tab + (i * 3 + ax) * kTab; };
   // u = v = 1 / N  (the initialisation of Algorithm 2), or a warm start
-  for (int i = 0; i < nimg; ++i) {
+  for (int i = 0; i < nimg && F32; ++i) {
+    const Img2D& I = L.imgs[i];
+    init_f32(I, I.f_init, I.U32, I.U32F);
+    init_f32(I, I.g_init, I.V32[0], I.V32F[0]);
+  }
+  for (int i = 0; i < nimg && !F32; ++i) {
     const Img2D& I = L.imgs[i];
     const int64_t N = (int64_t)I.nf * I.nm * I.ns;
     const XF init = xf_norm((float)(1.0 / (double)N), 0);
@@ -552,8 +899,11 @@ __global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
       const int i = owner(srow, nimg, t);
       if (sstate[i]) continue;
       const Img2D& I = L.imgs[i];
-      row_pass(I.U, I.Y, I.nm * I.ns, (t - srow[i]) * (32 / I.g[0]), I.nf, I.g[0], tab(i, 0), sframe[i][0], s_own,
-               t_own);
+      if (F32)
+        row_f32(I, I.U32, I.U32F, t - srow[i], tab(i, 0), reinterpret_cast<float*>(sline) + warp * 32 * 32);
+      else
+        row_pass(I.U, I.Y, I.nm * I.ns, (t - srow[i]) * (32 / I.g[0]), I.nf, I.g[0], tab(i, 0), sframe[i][0],
+                 s_own, t_own);
     }
     if (!grid_barrier(L, gen, &sok)) return;
     if (L.any3d && !mid_pass()) return;
@@ -566,11 +916,15 @@ __global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
       const TileMap M(I.g[1], I.ns);
       const int tile = t - stile[i];
       const int col0 = tile * M.TW;
-      col_tile_scan(I.nm > 1 ? I.R : I.Y, W, I.ns, col0, M, tab(i, 1), sframe[i][1], sline, L.line_stride);
-      XF* Vn = I.V[par ^ 1];
       float eh = 0.f, el = 0.f;
+      if (F32)
+        col_f32(I, tile, I.b, L.in_f32, I.V32[par], I.V32F[par], I.V32[par ^ 1], I.V32F[par ^ 1], true, tab(i, 1),
+                reinterpret_cast<float*>(sline), eh, el);
+      else
+        col_tile_scan(I.nm > 1 ? I.R : I.Y, W, I.ns, col0, M, tab(i, 1), sframe[i][1], sline, L.line_stride);
+      XF* Vn = I.V[par ^ 1];
       const int c = M.col();
-      if (col0 + c < W) {
+      if (!F32 && col0 + c < W) {
         const XF* sc = M.line(sline, L.line_stride, c);
         const int r0 = M.row0();
         const int dr = M.dr;
@@ -644,8 +998,12 @@ __global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
       const int i = owner(srow, nimg, t);
       if (sstate[i]) continue;
       const Img2D& I = L.imgs[i];
-      row_pass(I.V[par ^ 1], I.Y, I.nm * I.ns, (t - srow[i]) * (32 / I.g[0]), I.nf, I.g[0], tab(i, 0), sframe[i][0],
-               s_own, t_own);
+      if (F32)
+        row_f32(I, I.V32[par ^ 1], I.V32F[par ^ 1], t - srow[i], tab(i, 0),
+                reinterpret_cast<float*>(sline) + warp * 32 * 32);
+      else
+        row_pass(I.V[par ^ 1], I.Y, I.nm * I.ns, (t - srow[i]) * (32 / I.g[0]), I.nf, I.g[0], tab(i, 0),
+                 sframe[i][0], s_own, t_own);
     }
     if (!grid_barrier(L, gen, &sok)) return;
     if (L.any3d && !mid_pass()) return;
@@ -657,6 +1015,12 @@ __global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
       const int W = I.nf * I.nm;
       const TileMap M(I.g[1], I.ns);
       const int col0 = (t - stile[i]) * M.TW;
+      if (F32) {
+        float eh = 0.f, el = 0.f;
+        col_f32(I, t - stile[i], I.a, L.in_f32, nullptr, nullptr, I.U32, I.U32F, false, tab(i, 1),
+                reinterpret_cast<float*>(sline), eh, el);
+        continue;   // col_f32 ends with a block barrier
+      }
       col_tile_scan(I.nm > 1 ? I.R : I.Y, W, I.ns, col0, M, tab(i, 1), sframe[i][1], sline, L.line_stride);
       const int c = M.col();
       if (col0 + c < W) {
@@ -687,6 +1051,11 @@ __global__ void __launch_bounds__(kThreads2, 4) fs1_solve2d_kernel(Launch2D L) {
     if (!grid_barrier(L, gen, &sok)) return;
   }
 
+  // FP32 path: u and the returned v into the extended-range arrays
+  if (F32) {
+    for (int i = 0; i < nimg; ++i) to_xf(L.imgs[i], (ld_relaxed(L.imgs[i].stop) - 1) & 1);
+    if (!grid_barrier(L, gen, &sok)) return;
+  }
   // optional potentials out: log u and log v of the returned iterate (before
   // the cost passes, which reuse the v buffer in 3D)
   for (int i = 0; i < nimg; ++i) {
@@ -796,7 +1165,25 @@ int line_lanes(int L, double c) {
   return 32;
 }
 
+// bytes of the FP32 state of an image (values, frames)
+size_t f32_bytes(const PairDesc& d) {
+  const size_t lp = ((size_t)d.n_fast + kBlk - 1) / kBlk * kBlk, ns = (size_t)d.n_slow;
+  const size_t nb = (ns + kBlk - 1) / kBlk;
+  return 4 * align256(sizeof(float) * ns * lp) + 3 * align256(sizeof(int) * nb * lp) +
+         align256(sizeof(int) * ns * (lp / kBlk));
+}
+
 }  // namespace
+
+int solve2d_f32_ok(const PairDesc& d) {
+  if (d.n_mid != 1 || d.n_fast > kMaxLine2D || d.n_slow > kMaxLine2D) return 0;
+  int G, P;
+  f32_geom((int)d.n_fast, G, P);
+  if (d.n_fast > 1 && !(d.h_fast / d.eps * P <= kF32MaxNats)) return 0;
+  f32_geom((int)d.n_slow, G, P);
+  if (d.n_slow > 1 && !(d.h_slow / d.eps * P <= kF32MaxNats)) return 0;
+  return 1;
+}
 
 size_t solve2d_workspace(const PairDesc* d, int count) {
   size_t b = align256(sizeof(Img2D) * count) + 5 * align256(sizeof(int) * (count + 1)) + 256 + 256 +
@@ -805,6 +1192,7 @@ size_t solve2d_workspace(const PairDesc* d, int count) {
     const size_t W = (size_t)d[i].n_fast * d[i].n_mid;
     const size_t n = W * d[i].n_slow;
     b += 5 * align256(sizeof(XF) * n) + align256(sizeof(float) * 2 * W) + align256(sizeof(double) * W) + 256;
+    if (solve2d_f32_ok(d[i])) b += f32_bytes(d[i]);
   }
   return b;
 }
@@ -841,6 +1229,10 @@ int launch_solve_2d(const PairDesc* d, int count, int in_f32, PairResult* result
   int pp_max = 1;
   bool any_ext = false;   // some axis takes the per-point extended-range scan (XF partials)
   char* stops = nullptr;
+  // the FP32 block-frame path when every image of the call takes it
+  bool f32 = true;
+  for (int i = 0; i < count; ++i) f32 = f32 && solve2d_f32_ok(d[i]);
+  size_t smem_f32 = (size_t)kWarps2 * 32 * 32 * sizeof(float);   // the fast pass's backward partials
   for (int i = 0; i < count; ++i) {
     const PairDesc& D = d[i];
     Img2D I{};
@@ -884,6 +1276,26 @@ int launch_solve_2d(const PairDesc* d, int count, int in_f32, PairResult* result
         any_ext = any_ext || !I.frame[ax];
       }
     }
+    if (f32) {
+      I.lp = (I.nf + kBlk - 1) / kBlk * kBlk;
+      for (int ax = 0; ax < 3; ++ax) f32_geom(len[ax], I.g[ax], I.pf[ax]);
+      const size_t nb = ((size_t)I.ns + kBlk - 1) / kBlk, np = (size_t)I.ns * I.lp;
+      I.U32 = (float*)p; p += align256(sizeof(float) * np);
+      I.V32[0] = (float*)p; p += align256(sizeof(float) * np);
+      I.V32[1] = (float*)p; p += align256(sizeof(float) * np);
+      I.Y32 = (float*)p; p += align256(sizeof(float) * np);
+      I.U32F = (int*)p; p += align256(sizeof(int) * nb * I.lp);
+      I.V32F[0] = (int*)p; p += align256(sizeof(int) * nb * I.lp);
+      I.V32F[1] = (int*)p; p += align256(sizeof(int) * nb * I.lp);
+      I.Y32F = (int*)p; p += align256(sizeof(int) * I.ns * (I.lp / kBlk));
+      // slow pass tile: values [TW][G][P + 1], frames [ns][TW / 8], lane frames [TW][G]
+      const int TW = kTileCols * (32 / I.g[1]);
+      smem_f32 = std::max(smem_f32, sizeof(float) * ((size_t)TW * f32_cs(I.g[1], I.pf[1]) +
+                                                     (size_t)(I.ns + I.ns / I.pf[1]) * (TW / kBlk) +
+                                                     (size_t)TW * I.g[1]));
+    } else if (solve2d_f32_ok(D)) {
+      p += f32_bytes(D);   // the workspace counts it; this call takes the general path
+    }
     I.tw_s = kTileCols * (32 / I.g[1]);
     I.tw_m = kTileCols * (32 / I.g[2]);
     const int rpw = 32 / I.g[0];   // rows a warp takes at once
@@ -915,12 +1327,13 @@ int launch_solve_2d(const PairDesc* d, int count, int in_f32, PairResult* result
   // the stride is 2 mod 16 and the tile's warps start in different banks
   const int line_ch = 32 * pp_max;
   const int line_stride = line_ch + (any_ext ? line_ch : line_ch / 2) + 2;
-  const size_t smem = sizeof(XF) * (size_t)kWarps2 * line_stride;
+  const size_t smem = f32 ? smem_f32 : sizeof(XF) * (size_t)kWarps2 * line_stride;
   Launch2D L{d_imgs, results, count, in_f32, d_row, d_col, d_tile, d_mid, d_midl, any3d, line_stride, line_ch,
              d_tab, d_bar, d_abort, spin_cap};
-  e = cudaFuncSetAttribute(fs1_solve2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const void* kfn = f32 ? (const void*)fs1_solve2d_kernel<true> : (const void*)fs1_solve2d_kernel<false>;
+  e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0, dev = 0, sms = 0;
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fs1_solve2d_kernel, kThreads2, smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, kThreads2, smem);
   if (e != cudaSuccess || per_sm < 1) {
     fprintf(stderr, "fs1: 2D kernel does not fit (%zu B shared memory): %s\n", smem, cudaGetErrorString(e));
     return FS1_EUNSUPPORTED;
@@ -929,7 +1342,7 @@ int launch_solve_2d(const PairDesc* d, int count, int in_f32, PairResult* result
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = per_sm * sms;
   void* args[] = {&L};
-  e = cudaLaunchCooperativeKernel((const void*)fs1_solve2d_kernel, dim3(grid), dim3(kThreads2), args, smem, st);
+  e = cudaLaunchCooperativeKernel(kfn, dim3(grid), dim3(kThreads2), args, smem, st);
   if (e != cudaSuccess) {
     fprintf(stderr, "fs1: 2D launch failed: %s\n", cudaGetErrorString(e));
     return FS1_ECUDA;
