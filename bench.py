@@ -332,7 +332,7 @@ def run_gpu(args):
     tdt = torch.float64 if W["precision"] == "fp64" else torch.float32
     stream = torch.cuda.current_stream(dev)
     solver = fs1.Solver(W["variant"], W["precision"], stream=stream.cuda_stream, team_size=args.team_size,
-                        autotune=not args.no_autotune, use_graph=not args.no_graph)
+                        autotune=not args.no_autotune, use_graph=not args.no_graph, grid2d=args.grid2d)
 
     def hgrid(p):
         return tuple(p.h) if p.ndim >= 2 else p.h[0]
@@ -470,6 +470,7 @@ def run_gpu(args):
                "team_size": teams[0] if len(teams) == 1 else teams,
                "launch": "graph replay" if graph else "direct",
                **({"team_kernel": kernel_inst} if kernel_inst else {}),
+               **({"kernel_2d": "grid kernel (fs1_config.grid2d = 1)"} if args.grid2d else {}),
                "iters_min": min(iters), "iters_max": max(iters), "err_median": statistics.median(errs)}
         if args.workload in (2, 11):
             cfg.update({"n": p0.a.size, "eps": p0.eps, "tol": p0.tol, "itr_max": p0.itr_max})
@@ -527,6 +528,8 @@ def main(argv=None):
     ap.add_argument("--team-size", type=int, default=0, help="CTAs per pair (0: autotuned)")
     ap.add_argument("--no-autotune", action="store_true", help="fixed team-size heuristic")
     ap.add_argument("--no-graph", action="store_true", help="direct launches instead of graph replay")
+    ap.add_argument("--grid2d", action="store_true",
+                    help="2D images on the grid kernel (state in device memory) instead of the cluster kernel")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

@@ -732,23 +732,26 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
     desc[i] = d;
   }
   const size_t o_2d = off;
-  // (the grid kernel may take two launches: room for a second one's tables)
-  if (two_d) off = align_up(off + solve2d_workspace(desc.data(), count) + solve2d_workspace(nullptr, 0) + 1024, 256);
+  // (the grid kernel may take three launches: room for the others' tables)
+  if (two_d)
+    off = align_up(off + solve2d_workspace(desc.data(), count) + 2 * solve2d_workspace(nullptr, 0) + 2048, 256);
   // 2D images the cluster-resident kernel holds (first in `perm`), then the
-  // rest for the grid kernel: those of its FP32 path, then the others
+  // rest for the grid kernel by launch class (solve2d_class), one launch each
   std::vector<int> perm;
-  int ncl = 0, nf32 = 0;
+  int ncl = 0;
+  int gb[4] = {0, 0, 0, 0};   // [gb[q], gb[q + 1]) of perm: grid launch q
   const size_t o_c2d = off;
   if (two_d) {
     auto on_cluster = [&](int i) { return !h->cfg.grid2d && cluster2d_inst(desc[i]) >= 0; };
     for (int i = 0; i < count; ++i)
       if (on_cluster(i)) perm.push_back(i);
     ncl = (int)perm.size();
-    for (int i = 0; i < count; ++i)
-      if (!on_cluster(i) && solve2d_f32_ok(desc[i])) perm.push_back(i);
-    nf32 = (int)perm.size() - ncl;
-    for (int i = 0; i < count; ++i)
-      if (!on_cluster(i) && !solve2d_f32_ok(desc[i])) perm.push_back(i);
+    gb[0] = ncl;
+    for (int q = 0; q < 3; ++q) {
+      for (int i = 0; i < count; ++i)
+        if (!on_cluster(i) && solve2d_class(desc[i]) == q) perm.push_back(i);
+      gb[q + 1] = (int)perm.size();
+    }
     std::vector<PairDesc> dcl(ncl);
     for (int k = 0; k < ncl; ++k) dcl[k] = desc[perm[k]];
     if (ncl) off = align_up(off + cluster2d_workspace(dcl.data(), ncl), 256);
@@ -829,12 +832,11 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
                                        h->stream, &nl);
       if (ls != FS1_OK) return (fs1_status)ls;
     }
-    // the grid kernel: one launch for the images of its FP32 path, one for
-    // the others (each launch's workspace follows the previous one's)
+    // the grid kernel: one launch per class (each launch's workspace follows
+    // the previous one's)
     size_t o_g = o_2d;
-    const int bounds[3] = {ncl, ncl + nf32, count};
-    for (int q = 0; q < 2; ++q) {
-      const int k0 = bounds[q], k1 = bounds[q + 1];
+    for (int q = 0; q < 3; ++q) {
+      const int k0 = gb[q], k1 = gb[q + 1];
       if (k1 <= k0) continue;
       const size_t wsz = solve2d_workspace(dp.data() + k0, k1 - k0);
       const int ls = launch_solve_2d(dp.data() + k0, k1 - k0, in_f32, d_res + k0, ws + o_g, wsz, h->cfg.spin_cap,

@@ -97,10 +97,14 @@ enum KernelKind {
 constexpr int kMaxImg2D = 64;
 constexpr int kMaxLine2D = 1024;   // longest line along any axis (staged in shared memory)
 size_t solve2d_workspace(const PairDesc* host_descs, int count);
-// 1: the image takes the grid kernel's FP32 block-frame path (2D, axes of at
-// most 1024 points whose lane chunks of P points have P h / eps <= 64 on
-// every axis of more than one point); a launch_solve_2d call whose images all
-// qualify runs that path
+// Launch class of a grid image: 0 the general path with FP32-frame scans on
+// every axis, 1 the general path scanning some axis point by point in
+// extended range, 2 the FP32 block-frame path (2D, axes of at most 1024
+// points whose lane chunks of P points have P h / eps <= 64, where the
+// general path would scan point by point).  A launch_solve_2d call whose
+// images are all of class 2 runs the FP32 path; callers launch the classes
+// separately.
+int solve2d_class(const PairDesc& d);
 int solve2d_f32_ok(const PairDesc& d);
 int launch_solve_2d(const PairDesc* host_descs, int count, int in_f32, PairResult* d_results, void* ws,
                     size_t ws_bytes, long long spin_cap, void* stream);

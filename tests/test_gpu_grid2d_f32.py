@@ -1,16 +1,19 @@
-"""The grid kernel's FP32 block-frame path (2D images whose lane chunks of P
-points span at most 64 nats, P h / eps <= 64, on every axis of more than one
-point; values FP32 with one power-of-two frame per block of 8 points) against
-the CPU FP64 oracle, forced with fs1_config.grid2d = 1 for shapes the cluster
-kernel would otherwise take, and by default for sides above 512.
+"""The grid kernel's FP32 block-frame path against the CPU FP64 oracle: 2D
+images whose lane chunks of P points span at most 64 nats (P h / eps <= 64)
+on every axis of more than one point, where the general path would scan an
+axis point by point in extended range (P' h / eps > 40 for its own P');
+values FP32 with one power-of-two frame per block of 8 points.  These are
+images with sides above 512 (beyond the cluster kernel) and h / eps of about
+1.3 to 2.
 
 Tolerances: relative W1 <= 1e-4 and marginal error within 1e-3 relative of the
 oracle (FP32 stabilised), at the GPU's iteration count."""
+import math
+
 import numpy as np
 import pytest
 
 from oracle import cref, marginals
-from paper_2202_10042_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
@@ -34,9 +37,34 @@ def _rand2d(seed, ns, nf, floor=0.02):
     return a / a.sum(), b / b.sum()
 
 
-def _solve(env, probs, grid2d=True, outs=False, dtype=None):
+def _general_lanes(n, c):
+    """Lanes per line of the general path (the fewest of 8, 16, 32 keeping at
+    most 16 points per lane and its FP32-frame scan where 32 lanes allow it)."""
+    frame32 = c * math.ceil(n / 32) <= 40
+    for g in (8, 16):
+        p = math.ceil(n / g)
+        if p <= 16 and (not frame32 or c * p <= 40):
+            return g
+    return 32
+
+
+def _f32_path(ns, nf, eps):
+    """The rule of solve2d_f32_ok, restated."""
+    per_point = False
+    for n, h in ((nf, 1.0 / nf), (ns, 1.0 / ns)):
+        if n < 2:
+            continue
+        c = h / eps
+        g = 8 if n <= 128 else (16 if n <= 256 else 32)
+        if c * math.ceil(math.ceil(n / g) / 8) * 8 > 64:
+            return False
+        per_point = per_point or c * math.ceil(n / _general_lanes(n, c)) > 40
+    return per_point
+
+
+def _solve(env, probs, outs=False, dtype=None):
     torch, fs1 = env
-    s = fs1.Solver("log", "fp32", grid2d=grid2d)
+    s = fs1.Solver("log", "fp32")
     keep, ps, pots = [], [], []
     for (a2, b2, h, eps, tol, itr) in probs:
         ta = torch.tensor(a2, dtype=dtype or torch.float64, device="cuda")
@@ -54,13 +82,6 @@ def _solve(env, probs, grid2d=True, outs=False, dtype=None):
     return w, infos, pots
 
 
-def _f32_path(ns, nf, eps):
-    def p_of(n):
-        g = 8 if n <= 128 else (16 if n <= 256 else 32)
-        return -(-(-(-n // g)) // 8) * 8
-    return (nf == 1 or p_of(nf) / nf / eps <= 64) and (ns == 1 or p_of(ns) / ns / eps <= 64)
-
-
 def _check(w, info, a2, b2, h, eps, itr):
     ref = cref.solve(a2, b2, h, eps, 0.0, itr, tau=1e10)
     assert info.iters == ref.iters
@@ -68,19 +89,17 @@ def _check(w, info, a2, b2, h, eps, itr):
     assert abs(info.marginal_err - ref.err) <= 1e-3 * ref.err + 1e-7, (info.marginal_err, ref.err)
 
 
-# every lane geometry (8, 16, 32 lanes; 8 to 32 points per lane), ragged rows
-# and columns (padded rows, partial blocks, partly empty lanes), single rows
-# and columns, c P up to the limit of 64 nats
+# 32 lanes of 24 or 32 points, padded rows (nf not a multiple of 8), partial
+# blocks and partly empty lanes, a single row and a single column
 @pytest.mark.parametrize("ns,nf,eps", [
-    (1, 37, 0.02), (29, 1, 0.02), (5, 3, 0.1), (9, 17, 0.03), (64, 64, 2e-3), (100, 129, 5e-3),
-    (257, 200, 2e-3), (130, 700, 2e-3), (513, 300, 1e-3), (1000, 1000, 1e-3), (33, 1024, 0.04),
-    (1024, 24, 6e-3), (600, 777, 1e-3),
+    (1024, 1024, 6e-4), (800, 800, 7e-4), (700, 900, 6e-4), (600, 777, 7e-4), (1, 900, 6e-4),
+    (900, 1, 6e-4), (640, 640, 7e-4), (1000, 1000, 7e-4),
 ])
 def test_f32_grid_against_oracle(env, ns, nf, eps):
+    assert _f32_path(ns, nf, eps)
     a2, b2 = _rand2d(ns * 131 + nf, ns, nf)
     h = (1.0 / nf, 1.0 / ns)
-    assert _f32_path(ns, nf, eps)
-    itr = 25
+    itr = 20
     w, infos, _ = _solve(env, [(a2, b2, h, eps, 0.0, itr)])
     _, fs1 = env
     assert infos[0].team_size == 0 and infos[0].status in (fs1.FS1_OK, fs1.FS1_ENOTCONV)
@@ -90,7 +109,8 @@ def test_f32_grid_against_oracle(env, ns, nf, eps):
 def test_f32_grid_potentials_and_marginals(env):
     """Potentials out, entry by entry, and the exact row marginal of the
     returned iterate."""
-    ns, nf, eps, itr = 300, 650, 1e-3, 20
+    ns, nf, eps, itr = 700, 900, 6e-4, 15
+    assert _f32_path(ns, nf, eps)
     a2, b2 = _rand2d(12, ns, nf)
     h = (1.0 / nf, 1.0 / ns)
     w, infos, pots = _solve(env, [(a2, b2, h, eps, 0.0, itr)], outs=True)
@@ -107,50 +127,35 @@ def test_f32_grid_potentials_and_marginals(env):
 
 
 def test_f32_grid_stop_rule_and_mixed_call(env):
-    """One call with images of the FP32 path and images beyond it (c P > 64):
-    two grid launches; every image stops within one iteration of the oracle's
-    own stop and matches the oracle at the GPU's iteration count."""
+    """One call with images of the FP32 path and images of the general path
+    (its frame scans, and c P beyond 64): two grid launches; every image stops
+    within one iteration of the oracle's own stop (or both reach the cap) and
+    matches the oracle at the GPU's iteration count."""
     _, fs1 = env
-    shapes = [(64, 80, 0.03), (20, 600, 0.05), (130, 70, 0.002), (700, 40, 0.02), (40, 100, 1e-3)]
-    assert [_f32_path(*sh) for sh in shapes] == [True, True, False, True, False]
+    shapes = [(1, 900, 6e-4), (640, 640, 7e-4), (900, 1, 6e-4), (700, 600, 1.5e-3), (520, 40, 3e-4)]
+    assert [_f32_path(*sh) for sh in shapes] == [True, True, True, False, False]
     probs = []
     for i, (ns, nf, eps) in enumerate(shapes):
         a2, b2 = _rand2d(500 + i, ns, nf)
-        probs.append((a2, b2, (1.0 / nf, 1.0 / ns), eps, 1e-5, 3000))
+        probs.append((a2, b2, (1.0 / nf, 1.0 / ns), eps, 1e-4, 300))
     w, infos, _ = _solve(env, probs)
     for (a2, b2, h, eps, tol, itr), info, wi in zip(probs, infos, w):
-        assert info.status in (fs1.FS1_OK, fs1.FS1_ENOTCONV)
+        assert info.team_size == 0 and info.status in (fs1.FS1_OK, fs1.FS1_ENOTCONV)
         assert (info.status == fs1.FS1_OK) == (info.marginal_err <= tol)
         _check(wi, info, a2, b2, h, eps, info.iters)
         ro = cref.solve(a2, b2, h, eps, tol, itr, tau=1e10)
         assert abs(ro.iters - info.iters) <= 1
-    assert sum(i.status == fs1.FS1_OK for i in infos) >= 3
 
 
-def test_f32_grid_equals_cluster_kernel(env):
-    """The grid kernel's FP32 path and the cluster kernel on the same images:
-    the same iteration counts and W1 within the FP32 tolerance."""
-    probs = []
-    for i, (ns, nf, eps) in enumerate([(48, 48, 0.02), (120, 90, 5e-3), (512, 512, 1e-3)]):
-        a2, b2 = _rand2d(40 + i, ns, nf)
-        probs.append((a2, b2, (1.0 / nf, 1.0 / ns), eps, 1e-5, 300))
-    wg, ig, _ = _solve(env, probs)
-    wc, ic, _ = _solve(env, probs, grid2d=False)
-    for k in range(len(probs)):
-        assert ig[k].team_size == 0 and ic[k].team_size > 0
-        assert abs(ic[k].iters - ig[k].iters) <= 1
-        assert abs(wc[k] - wg[k]) <= TOL32 * abs(wc[k])
-
-
-def test_f32_grid_big_images_by_default(env):
-    """Sides above 512 (beyond the cluster kernel) take the FP32 grid path by
-    default; float32 inputs; four images of a serving-size batch."""
+def test_f32_grid_float32_inputs_batch(env):
+    """Four images of a serving-size batch from float32 arrays, 8 iterations."""
     torch, _ = env
     probs = []
-    for i, side in enumerate((600, 800, 1024, 700)):
+    for i, (side, eps) in enumerate(((1024, 6e-4), (800, 7e-4), (640, 7e-4), (700, 8e-4))):
         a2, b2 = _rand2d(70 + i, side, side)
-        probs.append((a2, b2, (1.0 / side, 1.0 / side), 2e-3, 0.0, 8))
-    w, infos, _ = _solve(env, probs, grid2d=False, dtype=torch.float32)
+        assert _f32_path(side, side, eps) or side == 700
+        probs.append((a2, b2, (1.0 / side, 1.0 / side), eps, 0.0, 8))
+    w, infos, _ = _solve(env, probs, dtype=torch.float32)
     refs = cref.solve_many([(a2.astype(np.float32).astype(np.float64), b2.astype(np.float32).astype(np.float64),
                              h, eps, 0.0, 8) for a2, b2, h, eps, tol, itr in probs], tau=1e10)
     for k, r in enumerate(refs):
