@@ -221,9 +221,9 @@ class Clocks:
 # workload construction
 # ---------------------------------------------------------------------------
 
-def make_problems(workload, indices, itr_max=None, workers=16):
+def make_problems(workload, indices, itr_max=None, workers=16, **over):
     with cf.ThreadPoolExecutor(max_workers=workers) as ex:
-        return list(ex.map(lambda i: gen_problem(workload, i, itr_max=itr_max), indices))
+        return list(ex.map(lambda i: gen_problem(workload, i, itr_max=itr_max, **over), indices))
 
 
 def host_cores() -> int:
@@ -328,7 +328,8 @@ def run_gpu(args):
     W = WORKLOADS[args.workload]
     npairs = args.pairs or W["pairs"]
     idx = shard_pairs(npairs, rank)
-    host = make_problems(args.workload, idx, itr_max=args.itr_max)
+    over = {"side": args.side, "eps": args.eps} if args.workload == 4 else {}
+    host = make_problems(args.workload, idx, itr_max=args.itr_max, **over)
     tdt = torch.float64 if W["precision"] == "fp64" else torch.float32
     stream = torch.cuda.current_stream(dev)
     solver = fs1.Solver(W["variant"], W["precision"], stream=stream.cuda_stream, team_size=args.team_size,
@@ -474,6 +475,8 @@ def run_gpu(args):
                "iters_min": min(iters), "iters_max": max(iters), "err_median": statistics.median(errs)}
         if args.workload in (2, 11):
             cfg.update({"n": p0.a.size, "eps": p0.eps, "tol": p0.tol, "itr_max": p0.itr_max})
+        if over and (args.side or args.eps):
+            cfg["workload"] += " (overridden: side %d, eps %g)" % (p0.a.shape[0], p0.eps)
         line = {"metric": METRIC, "value": value, "unit": "N*iters/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
                 "higher_is_better": True, "scaling": "weak",
@@ -528,6 +531,8 @@ def main(argv=None):
     ap.add_argument("--team-size", type=int, default=0, help="CTAs per pair (0: autotuned)")
     ap.add_argument("--no-autotune", action="store_true", help="fixed team-size heuristic")
     ap.add_argument("--no-graph", action="store_true", help="direct launches instead of graph replay")
+    ap.add_argument("--side", type=int, default=None, help="workload 4: image side (default 512)")
+    ap.add_argument("--eps", type=float, default=None, help="workload 4: eps (default 1e-3)")
     ap.add_argument("--grid2d", action="store_true",
                     help="2D images on the grid kernel (state in device memory) instead of the cluster kernel")
     args = ap.parse_args(argv)
