@@ -97,9 +97,9 @@ typedef struct fs1_config {
                            h / eps <= 8); 1 always uses the grid kernel that keeps the
                            state in device memory (also 3D) */
   int units;            /* stabilised 1D batches of two or more pairs: 1 (default)
-                           solves each small pair (at most 32 points per thread on 4
-                           warps, within the frame cap of h / eps) on a unit of 4 warps
-                           or of one warp, 4 or 16 pairs side by side per CTA, after the
+                           solves each small pair (at most 32 points per thread on 8
+                           warps, within the frame cap of h / eps) on a unit of 8, 4 or
+                           one warp, 2, 4 or 16 pairs side by side per CTA, after the
                            pairs that need whole CTAs; 0 gives every pair whole CTAs.
                            Ignored when team_size > 0 */
 } fs1_config;

@@ -324,26 +324,27 @@ fs1_status choose_geometry(fs1_handle* h, int kind, const std::vector<const fs1_
 // divide each other (a class capped at the device's CTA count) fall back to a
 // static split of the CTAs over the classes in proportion to N * itr_max.
 //
-// Small stabilised pairs (at most 32 points per thread on 4 warps) go to the
-// kernel's units instead: after the teams' queues, every CTA runs 4 units of
-// 4 warps on one queue and then 16 single warps on another, a pair per unit
-// (classes nc and nc + 1 after the nc team classes); such a plan is always a
-// level schedule over all the device's CTAs.
+// Small stabilised pairs (at most 32 points per thread on 8 warps) go to the
+// kernel's units instead: after the teams' queues, every CTA runs 2 units of
+// 8 warps on one queue, then 4 of 4 warps on another and 16 single warps on a
+// third, a pair per unit (classes nc, nc + 1 and nc + 2 after the nc team
+// classes); such a plan is always a level schedule over all the device's CTAs.
 struct Plan {
   std::vector<int> cta_team, cta_rank, team_T, team_slot, team_class, class_off, order, class_T;
   std::vector<int> prob_T;    // team size of each problem (CTAs; 1 for a unit)
   std::vector<int> level_T;   // level schedule: team size per level (empty: static teams)
   int num_teams = 0, grid = 0, max_T = 1, slots = 0, tickets = 0;
-  int unit_class = -1;        // class of the 4-warp units' queue (-1: no units)
+  int unit_class = -1;        // class of the 8-warp units' queue (-1: no units)
 };
 
-// Warps of the unit that solves problem p (4 or 1), or 0 for a team of CTAs:
-// the fewest warps holding it at <= 32 points per thread within the frame cap
+// Warps of the unit that solves problem p (1, 4 or 8), or 0 for a team of
+// CTAs: the fewest warps holding it at <= 32 points per thread within the
+// frame cap
 int unit_warps(int kind, const fs1_problem& p) {
   if (kind != KK_LOG_F32 || p.ndim != 1) return 0;
   const int64_t cap = std::min(32, elems_cap_for(kind, p.h[0] / p.eps));
   const int64_t n = npoints(p);
-  return n <= 32 * cap ? 1 : (n <= 128 * cap ? 4 : 0);
+  return n <= 32 * cap ? 1 : (n <= 128 * cap ? 4 : (n <= 256 * cap ? 8 : 0));
 }
 
 // fewest CTAs that hold problem p on chip (0: more than fit)
@@ -405,7 +406,7 @@ fs1_status plan_teams(fs1_handle* h, int kind, const std::vector<const fs1_probl
     }
   }
   // classes by team size (a batch of unit pairs only keeps one empty class of
-  // teams of one CTA), then the units' two classes
+  // teams of one CTA), then the units' three classes
   std::vector<int> keys;
   for (int i = 0; i < n; ++i)
     if (uw[i] == 0) keys.push_back(tmin[i]);
@@ -413,12 +414,14 @@ fs1_status plan_teams(fs1_handle* h, int kind, const std::vector<const fs1_probl
   std::sort(keys.begin(), keys.end());
   keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
   const int nc = (int)keys.size();
-  const int nq = nc + (any_unit ? 2 : 0);   // queues
+  const int nq = nc + (any_unit ? 3 : 0);   // queues
   std::vector<double> W(nq, 0.0);
   std::vector<int> cnt(nq, 0), cls(n);
   for (int i = 0; i < n; ++i) {
-    cls[i] = uw[i] == 4 ? nc : (uw[i] == 1 ? nc + 1
-                                           : (int)(std::lower_bound(keys.begin(), keys.end(), tmin[i]) - keys.begin()));
+    cls[i] = uw[i] == 8   ? nc
+             : uw[i] == 4 ? nc + 1
+             : uw[i] == 1 ? nc + 2
+                          : (int)(std::lower_bound(keys.begin(), keys.end(), tmin[i]) - keys.begin());
     W[cls[i]] += cost[i];
     cnt[cls[i]] += 1;
   }

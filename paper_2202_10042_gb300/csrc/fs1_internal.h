@@ -74,9 +74,10 @@ struct TeamLaunch {
   int nlevel;
   const int* level_T;              // [nlevel]
   // Units (generic stabilised kernel, unit_queues = 1): after the teams'
-  // queues, every CTA solves small pairs as 4 units of 4 warps on the queue
-  // of class unit_class, each unit then as 4 single warps on the queue of
-  // class unit_class + 1 (a pair per unit, its points in the unit's threads).
+  // queues, every CTA solves small pairs as 2 units of 8 warps on the queue
+  // of class unit_class, each unit then as 2 units of 4 warps on the queue of
+  // class unit_class + 1 and each of those as 4 single warps on the queue of
+  // class unit_class + 2 (a pair per unit, its points in the unit's threads).
   int unit_queues;
   int unit_class;
   const int* valid;                // [num_pairs] 0: the pair failed the input check and is

@@ -83,7 +83,8 @@ struct DecayTables {
 // or, for pairs small enough to fit a few warps, 16 / GW independent units of
 // GW warps, each solving its own pair (a team of one unit).  A unit
 // synchronises its own warps only: __syncthreads for the whole CTA, the warp
-// barrier for one warp, a named barrier (id 1 + unit) otherwise.
+// barrier for one warp, a named barrier otherwise: ids 1-4 for units of 4
+// warps, 5-6 for units of 8 (both widths can run at once in one CTA).
 template <int GW>
 __device__ __forceinline__ void unit_sync() {
   if constexpr (GW == kWarps) {
@@ -91,7 +92,8 @@ __device__ __forceinline__ void unit_sync() {
   } else if constexpr (GW == 1) {
     __syncwarp();
   } else {
-    asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)(threadIdx.x / (32 * GW))), "n"(32 * GW) : "memory");
+    constexpr int base = GW == 8 ? 5 : 1;
+    asm volatile("bar.sync %0, %1;" ::"r"(base + (int)(threadIdx.x / (32 * GW))), "n"(32 * GW) : "memory");
   }
 }
 
@@ -578,7 +580,7 @@ __device__ __forceinline__ bool team_body(const TeamLaunch& L, int mode, unsigne
     tc.slot_base = 0;
     tc.abort = L.abort_flags;
     tc.ticket = 0;
-    cls = L.unit_class + (GW == 4 ? 0 : 1);
+    cls = L.unit_class + (GW == 8 ? 0 : (GW == 4 ? 1 : 2));
   } else if (kLevels && L.nlevel > 0) {
     level_ctx(L, 0, tc, cls);
   } else if (L.cta_team) {
@@ -970,19 +972,21 @@ __device__ __noinline__ bool unit_phase(const TeamLaunch& L, unsigned char* smem
 
 // The kernel: the pair loop of 16-warp units (team members); then, in the
 // generic stabilised instantiation and when the launch has units' queues,
-// units of 4 warps, each of which goes on as 4 units of one warp once its
-// queue is empty.  The 16-warp units' shared state is reused by the narrower
-// units after a block barrier; the units of 4 and of 1 warp have separate
-// shared state (a unit of 4 may still run while its neighbour has gone on as
-// single warps).
+// units of 8 warps, each of which goes on as 2 units of 4 once its queue is
+// empty, each of those as 4 units of one warp.  The 16-warp units' shared
+// state is reused by the narrower units after a block barrier; the units of
+// 8, 4 and 1 warps have separate shared state (a unit may still run while
+// its neighbour has gone on as narrower units).
 template <class V, class C, int E, int G>
 __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int mode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr bool kUnits = G < E && std::is_same<C, XF>::value;
   using S16 = UnitSmem<C, kWarps>;
+  using S8 = UnitSmem<C, 8>;
   using S4 = UnitSmem<C, 4>;
   using S1 = UnitSmem<C, 1>;
-  constexpr size_t kOff1 = (sizeof(S4) + 15) / 16 * 16;
+  constexpr size_t kOff4 = (sizeof(S8) + 15) / 16 * 16;
+  constexpr size_t kOff1 = kOff4 + (sizeof(S4) + 15) / 16 * 16;
   constexpr size_t kNarrow = kOff1 + sizeof(S1);
   constexpr size_t kStat = kUnits && kNarrow > sizeof(S16) ? kNarrow : sizeof(S16);
   __shared__ __align__(16) unsigned char stat[kStat];
@@ -990,7 +994,8 @@ __global__ void __launch_bounds__(kThreads, 1) fs1_team_kernel(TeamLaunch L, int
   if constexpr (kUnits) {
     if (!L.unit_queues || mode != 0) return;
     __syncthreads();
-    if (!unit_phase<V, C, E, G, 4>(L, smem_raw, reinterpret_cast<S4*>(stat))) return;
+    if (!unit_phase<V, C, E, G, 8>(L, smem_raw, reinterpret_cast<S8*>(stat))) return;
+    if (!unit_phase<V, C, E, G, 4>(L, smem_raw, reinterpret_cast<S4*>(stat + kOff4))) return;
     unit_phase<V, C, E, G, 1>(L, smem_raw, reinterpret_cast<S1*>(stat + kOff1));
   }
 }
