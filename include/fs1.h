@@ -196,6 +196,16 @@ fs1_status fs1_solve_batch(fs1_handle* h, const fs1_problem* probs, int64_t coun
 fs1_status fs1_kernel_apply_log(fs1_handle* h, const double* in, double* out, int64_t n,
                                 double hx, double eps);
 
+/* Test hook for the bounded device-side waits (the paper has no
+ * counterpart): one stabilised pair (a, b: device FP64 arrays of n points,
+ * 1024 <= n <= 32768) launched as a team of two CTAs of which only rank 0
+ * runs.  Its waits for the partner's exchange slot poll at most spin_cap
+ * times and give up, and the pair's result is FS1_ETIMEOUT (in *pair_status)
+ * with no fault and the handle still usable.  Returns FS1_OK when the launch
+ * ran, FS1_EINVAL for bad arguments or a handle of another variant. */
+fs1_status fs1_test_missing_partner(fs1_handle* h, const double* a, const double* b, int64_t n, double hx,
+                                    double eps, long long spin_cap, fs1_status* pair_status);
+
 /* Release the handle and its device memory. */
 void fs1_destroy(fs1_handle* h);
 

@@ -1433,6 +1433,61 @@ fs1_status fs1_kernel_apply_log(fs1_handle* h, const double* in, double* out, in
   return run_group(h, kind_of(h->cfg), 1, ps, r, geo, &ms, false);
 }
 
+fs1_status fs1_test_missing_partner(fs1_handle* h, const double* a, const double* b, int64_t n, double hx,
+                                    double eps, long long spin_cap, fs1_status* pair_status) {
+  const int thr = team_threads();
+  if (!h || !a || !b || !pair_status || n < 2 * thr || n > 2 * (int64_t)thr * team_elems_max(KK_LOG_F32) ||
+      !(hx > 0.0) || !(eps > 0.0) || spin_cap < 1 || h->cfg.variant != FS1_VARIANT_LOG)
+    return FS1_EINVAL;
+  // workspace: descriptor | result | [2 parities][2 ranks] generic slots |
+  // the same compact slots (one 128-byte line each) | counter | abort flag
+  const size_t o_desc = 0, o_res = 256, o_slot = 512;
+  const size_t o_cslot = o_slot + align_up(sizeof(Slot) * 4, 256);
+  const size_t o_ctr = o_cslot + 128 * 4, o_abt = o_ctr + 256, bytes = o_abt + 256;
+  fs1_status st;
+  if ((st = ensure_ws(h, bytes)) != FS1_OK) return st;
+  char* ws = (char*)h->ws;
+  PairDesc d{};
+  d.a = a;
+  d.b = b;
+  d.n = n;
+  d.n_fast = n;
+  d.n_mid = 1;
+  d.n_slow = 1;
+  d.h_fast = hx;
+  d.eps = eps;
+  d.tol = 0.0;
+  d.itr_max = 1;
+  const PairResult r0{NAN, NAN, 0, FS1_EINVAL, 0};
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(ws, 0, bytes, h->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(ws + o_desc, &d, sizeof d, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(ws + o_res, &r0, sizeof r0, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
+    return cuda_fail(e, "missing-partner setup");
+  TeamLaunch L{};
+  L.pairs = (const PairDesc*)(ws + o_desc);
+  L.results = (PairResult*)(ws + o_res);
+  L.num_pairs = 1;
+  L.team_size = 2;   // a team of two CTAs ...
+  L.num_teams = 1;
+  L.grid = 1;        // ... of which one is launched: its partner never publishes
+  L.in_f32 = 0;
+  L.slots = (Slot*)(ws + o_slot);
+  L.cslots = (unsigned long long*)(ws + o_cslot);
+  L.counters = (unsigned long long*)(ws + o_ctr);
+  L.abort_flags = (int*)(ws + o_abt);
+  L.spin_cap = spin_cap;
+  const int ls = launch_team_1d(KK_LOG_F32, L, h->stream, 0);
+  g_launches.fetch_add(1);
+  if (ls != FS1_OK) return (fs1_status)ls;
+  PairResult r;
+  if ((e = cudaMemcpyAsync(&r, ws + o_res, sizeof r, cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(h->stream)) != cudaSuccess)
+    return cuda_fail(e, "missing-partner result");
+  *pair_status = (fs1_status)r.status;
+  return FS1_OK;
+}
+
 const char* fs1_status_string(fs1_status s) {
   switch (s) {
     case FS1_OK: return "FS1_OK";

@@ -10,7 +10,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from ctypes import (POINTER, Structure, c_char_p, c_double, c_float, c_int, c_int64,
+from ctypes import (POINTER, Structure, byref, c_char_p, c_double, c_float, c_int, c_int64,
                     c_longlong, c_size_t, c_void_p)
 from typing import List, Optional, Sequence
 
@@ -51,7 +51,7 @@ class fs1_info(Structure):
 EXPORTED = ["fs1_config_default", "fs1_create", "fs1_w1", "fs1_solve_batch",
             "fs1_kernel_apply_log", "fs1_destroy", "fs1_status_string", "fs1_version",
             "fs1_launch_count", "fs1_w1_noalloc", "fs1_handle_stats",
-            "fs1_handle_launch_stats"]
+            "fs1_handle_launch_stats", "fs1_test_missing_partner"]
 
 _lib = None
 
@@ -76,6 +76,9 @@ def load(path: str = LIB_PATH):
     L.fs1_solve_batch.restype = c_int
     L.fs1_kernel_apply_log.argtypes = [c_void_p, c_void_p, c_void_p, c_int64, c_double, c_double]
     L.fs1_kernel_apply_log.restype = c_int
+    L.fs1_test_missing_partner.argtypes = [c_void_p, c_void_p, c_void_p, c_int64, c_double, c_double, c_longlong,
+                                           POINTER(c_int)]
+    L.fs1_test_missing_partner.restype = c_int
     L.fs1_destroy.argtypes = [c_void_p]
     L.fs1_destroy.restype = None
     L.fs1_status_string.argtypes = [c_int]
@@ -133,6 +136,15 @@ def fs1_solve_batch(h, probs: Sequence[fs1_problem]):
 def fs1_kernel_apply_log(h, in_ptr: int, out_ptr: int, n: int, hx: float, eps: float) -> int:
     return load().fs1_kernel_apply_log(h, c_void_p(in_ptr), c_void_p(out_ptr), int(n),
                                        float(hx), float(eps))
+
+
+def fs1_test_missing_partner(h, a_ptr: int, b_ptr: int, n: int, hx: float, eps: float, spin_cap: int):
+    """(status of the call, status of the pair): a pair on a team of two CTAs
+    of which only one runs gives up its bounded waits (FS1_ETIMEOUT)."""
+    ps = c_int(-1)
+    st = load().fs1_test_missing_partner(h, c_void_p(a_ptr), c_void_p(b_ptr), int(n), float(hx), float(eps),
+                                         int(spin_cap), byref(ps))
+    return st, ps.value
 
 
 def fs1_status_string(s: int) -> str:

@@ -135,3 +135,22 @@ def test_mixed_dimensions_and_invalid_in_one_batch(env):
         ref = cref.solve(a, b, h, eps, 0.0, itr, tau=1e10)
         assert infos[k].status == fs1.FS1_ENOTCONV and infos[k].iters == itr
         assert abs(w[k] - ref.w) <= TOL32 * abs(ref.w), (k, w[k], ref.w)
+
+
+def test_bounded_wait_gives_up_without_fault(env):
+    """A pair launched as a team of two CTAs of which only one runs: the
+    waits for the missing partner's exchange slot end at the spin cap, the
+    pair reports FS1_ETIMEOUT, and the handle then solves normally."""
+    torch, fs1 = env
+    n = 4000
+    a, b = inputs.random_pair_1d(11, n, floor=0.05)
+    ta = torch.tensor(a, dtype=torch.float64, device="cuda")
+    tb = torch.tensor(b, dtype=torch.float64, device="cuda")
+    s = fs1.Solver("log", "fp32", autotune=False)
+    st, pair_st = fs1.fs1_test_missing_partner(s.h, ta.data_ptr(), tb.data_ptr(), n, 1.0 / n, 0.05, 1 << 14)
+    assert st == fs1.FS1_OK and pair_st == fs1.FS1_ETIMEOUT
+    st2, w, infos = s.solve([fs1.Solver.problem(ta, tb, 1.0 / n, 0.05, 0.0, 20)])
+    s.close()
+    assert infos[0].status == fs1.FS1_ENOTCONV and infos[0].iters == 20
+    ref = cref.solve(a, b, 1.0 / n, 0.05, 0.0, 20, tau=1e10)
+    assert abs(w[0] - ref.w) <= TOL32 * abs(ref.w)
