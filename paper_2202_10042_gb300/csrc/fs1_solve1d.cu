@@ -63,7 +63,7 @@ int launch_team_1d(int kind, const TeamLaunch& L, void* stream, int exact_E) {
     switch (kind) {
       case KK_PLAIN_F64: e = launch_kind<double, double, 8, 2>(L, mode, st); break;
       case KK_PLAIN_F32: e = launch_kind<float, float, 32, 4>(L, mode, st); break;
-      case KK_LOG_F32: e = launch_kind<float, XF, 32, 4>(L, mode, st); break;
+      case KK_LOG_F32: e = launch_kind<float, XF, 32, 8>(L, mode, st); break;
       default: return FS1_EINVAL;
     }
   }
@@ -93,7 +93,7 @@ int max_coresident_ctas(int kind) {
   switch (kind & 0xff) {
     case KK_PLAIN_F64: return coresident<double, double, 8, 2>();
     case KK_PLAIN_F32: return coresident<float, float, 32, 4>();
-    case KK_LOG_F32: return coresident<float, XF, 32, 4>();
+    case KK_LOG_F32: return coresident<float, XF, 32, 8>();
   }
   return 0;
 }
