@@ -96,11 +96,12 @@ typedef struct fs1_config {
                            fits (2D grids of at most 512 x 512 points whose axes have
                            h / eps <= 8); 1 always uses the grid kernel that keeps the
                            state in device memory (also 3D) */
-  int units;            /* stabilised 1D batches of two or more pairs: 1 (default)
-                           solves each small pair (at most 32 points per thread on 8
-                           warps, within the frame cap of h / eps) on a unit of 8, 4 or
-                           one warp, 2, 4 or 16 pairs side by side per CTA, after the
-                           pairs that need whole CTAs; 0 gives every pair whole CTAs.
+  int units;            /* stabilised 1D batches: 1 (default) solves each small pair
+                           (at most 32 points per thread on 8 warps, within the frame
+                           cap of h / eps) on a unit of 8, 4 or one warp, 2, 4 or 16
+                           pairs side by side per CTA, after the pairs that need whole
+                           CTAs, when a batch has more such pairs than co-resident CTAs
+                           (fewer get a whole CTA each); 0 gives every pair whole CTAs.
                            Ignored when team_size > 0 */
 } fs1_config;
 

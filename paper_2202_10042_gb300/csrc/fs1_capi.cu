@@ -666,13 +666,17 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
   }
   const bool planned = !two_d && !paper && mode == 0;
   // small stabilised pairs of a batch on the kernel's units (no team-size
-  // tuning then); a lone pair keeps whole CTAs (its serial chains are
-  // shorter there, and fs1_w1 stays the same computation as fs1_w1_noalloc)
+  // tuning then), when they outnumber the co-resident CTAs: with fewer, a
+  // whole CTA each leaves no SM idle and runs each pair with shorter serial
+  // chains (100 pairs of 8000 points: 1.17e11 N*it/s on whole CTAs, 8.4e10
+  // on units of 8 warps that used a third of the SMs).  A lone pair keeps
+  // whole CTAs too, so that fs1_w1 stays the computation fs1_w1_noalloc
+  // repeats.
   bool units = planned && count > 1 && kind == KK_LOG_F32 && h->cfg.units && h->cfg.team_size <= 0 && !h->tuning;
   if (units) {
-    bool any = false;
-    for (auto* p : ps) any = any || unit_warps(kind, *p) > 0;
-    units = any;
+    int nu = 0;
+    for (auto* p : ps) nu += unit_warps(kind, *p) > 0 ? 1 : 0;
+    units = nu > max_coresident_ctas(kind);
   }
   if (planned && !units && h->cfg.autotune && h->cfg.team_size <= 0 && !h->tuning) {
     const int maxc = max_coresident_ctas(kind);
