@@ -5,12 +5,11 @@
 // with its state in device memory.  The grid is cut into chunks of 8192
 // points (one 512-thread CTA, 16 points per thread).  One half-step of
 // Algorithm 1 is ONE launch over the chunks:
-//   carries : every chunk forms its forward carry (the value at the point
-//             before it) and backward carry (at its last point) from the
-//             (decay, value) aggregates the previous launch stored for every
-//             chunk of its input: a decay-weighted sum over the other
-//             chunks, lam^{8192 d} from a table; the aggregates are complete
-//             when the launch starts, so no chunk waits for another;
+//   carries : every chunk reads its forward carry (the value at the point
+//             before it) and backward carry (at its last point) of the
+//             input, which the previous launch's last chunk formed by one
+//             scan over all chunks' (decay, value) aggregates; they are
+//             complete when the launch starts, so no chunk waits for another;
 //   half    : the chunk loads its input (128-bit, coalesced), forms the thread
 //             carries with the team kernel's in-CTA scan plus its chunk
 //             carries, runs the recurrences of Section 3, eq. "recursion",
@@ -19,8 +18,9 @@
 //             (v-half) the chunk's marginal-error partial;
 //   last    : the last chunk to finish (a ticket counter, no waiting) takes
 //             the while condition of Algorithm 1 after a v-half (the error
-//             partials summed in FP64 in chunk order) and advances the
-//             iteration count after a u-half.
+//             partials summed in FP64 in chunk order), advances the
+//             iteration count after a u-half, and scans the chunk aggregates
+//             of the launch's output into the carries the next launch reads.
 // Every launch first reads the stop flag and returns once the loop has
 // ended, so the host issues iterations in captured blocks and reads the flag
 // between blocks.  Up to kMaxStreamPairs pairs share the launches: the grid
@@ -46,8 +46,10 @@ namespace fs1 {
 
 namespace {
 
+constexpr int kST = 512;                 // threads of a chunk's CTA
+constexpr int kSW = kST / 32;            // its warps
 constexpr int kSE = 16;                  // points per thread per chunk
-constexpr int kChunk = kThreads * kSE;   // points per chunk (one CTA)
+constexpr int kChunk = kST * kSE;        // points per chunk (one CTA)
 
 struct StreamState {
   long long ell;   // completed iterations
@@ -73,10 +75,13 @@ struct StreamArgs {
   float* BW;
   float* U;              // [nch * kChunk] values relative to their run's frame
   float* V[2];
-  int* FU;               // [nch * kThreads] frames of the runs
+  int* FU;               // [nch * kST] frames of the runs
   int* FV[2];
   XF* agg_f[3];          // chunk aggregates of U, V[0], V[1]: forward (value at the chunk's
   XF* agg_b[3];          // last point) and backward (value at the point before its first)
+  XF* car_f[3];          // chunk carries of U, V[0], V[1]: forward (value at the point before
+  XF* car_b[3];          // the chunk, from the chunks before it) and backward (at its last point,
+                         // from the chunks after it)
   XF* dec;               // [nch] lam^{kChunk d}
   DecayTables<XF>* tabs; // the in-CTA decay tables (written once by the init kernel)
   float* errp;           // [2 nch] compensated error partials
@@ -121,7 +126,7 @@ __device__ __forceinline__ void ld_run(const float* X, int ch, int t, float (&x)
   const float4* p = reinterpret_cast<const float4*>(X + (size_t)ch * kChunk) + t;
 #pragma unroll
   for (int q = 0; q < kSE / 4; ++q) {
-    const float4 v = p[q * kThreads];
+    const float4 v = p[q * kST];
     x[4 * q] = v.x;
     x[4 * q + 1] = v.y;
     x[4 * q + 2] = v.z;
@@ -131,7 +136,7 @@ __device__ __forceinline__ void ld_run(const float* X, int ch, int t, float (&x)
 __device__ __forceinline__ void st_run(float* X, int ch, int t, const float (&x)[kSE]) {
   float4* p = reinterpret_cast<float4*>(X + (size_t)ch * kChunk) + t;
 #pragma unroll
-  for (int q = 0; q < kSE / 4; ++q) p[q * kThreads] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+  for (int q = 0; q < kSE / 4; ++q) p[q * kST] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
 }
 // values given relative to frame F, renormalised so that the largest lies in
 // [0.5, 1); returns the run's frame (kZeroExp for an all-zero run)
@@ -158,14 +163,14 @@ __device__ void cta_totals(typename Op::T af, typename Op::T ab, const DecayTabl
   const T wb = warp_sum_c(Op::prop(ab, tb.dt[lane], (float)(kSE * lane)));
   if (lane == 0) {
     sw[warp] = wf;
-    sw[kWarps + warp] = wb;
+    sw[kSW + warp] = wb;
   }
   __syncthreads();
   if (warp == 0) {
     T xf = Op::zero(), xb = Op::zero();
-    if (lane < kWarps) {
-      xf = Op::prop(sw[lane], tb.dw[kWarps - 1 - lane], (float)(32 * kSE * (kWarps - 1 - lane)));
-      xb = Op::prop(sw[kWarps + lane], tb.dw[lane], (float)(32 * kSE * lane));
+    if (lane < kSW) {
+      xf = Op::prop(sw[lane], tb.dw[kSW - 1 - lane], (float)(32 * kSE * (kSW - 1 - lane)));
+      xb = Op::prop(sw[kSW + lane], tb.dw[lane], (float)(32 * kSE * lane));
     }
     tf = warp_sum_c(xf);
     tbk = warp_sum_c(xb);
@@ -183,7 +188,7 @@ __device__ void cta_sum_pair(float& h, float& l, float* red) {
   __syncthreads();
   h = 0.f;
   l = 0.f;
-  for (int w = 0; w < kWarps; ++w) df_add(h, l, red[2 * w], red[2 * w + 1]);
+  for (int w = 0; w < kSW; ++w) df_add(h, l, red[2 * w], red[2 * w + 1]);
 }
 
 __device__ __forceinline__ XF xf_of_log(double x) {
@@ -210,11 +215,68 @@ __device__ __forceinline__ void run_aggregates(const float (&x)[kSE], float lam,
   }
 }
 
+// The carries of every chunk of array src from its chunk aggregates, by one
+// CTA: thread t takes the m consecutive chunks t m ..., the threads' block
+// aggregates are joined by the team kernel's in-CTA scan with decay
+// lam^{kChunk} per chunk (the tables tb are refilled for it), and each thread
+// sweeps its block:
+//   car_f[j] = lam^{kChunk} car_f[j - 1] + agg_f[j - 1],  car_f[0] = 0
+//   car_b[j] = lam^{kChunk} car_b[j + 1] + agg_b[j + 1],  car_b[nch - 1] = 0
+// (agg_f: the chunk's value at its last point; agg_b: at the point before
+// its first).  Every thread of the CTA calls; the aggregates were written by
+// other CTAs (read through L2).
+__device__ __forceinline__ XF ldcg_xf(const XF* p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return XF{v.x, __float_as_int(v.y)};
+}
+
+__device__ void chunk_carry_scan(const StreamArgs& A, int src, DecayTables<XF>& tb, XchgSmem<XF>& X) {
+  const int tid = threadIdx.x;
+  const int m = (A.nch + kST - 1) / kST;
+  const int j0 = tid * m;
+  const double cc = A.c * (double)kChunk;
+  const XF d1 = c_decay(1.0, cc, XF{});
+  const XF* AF = A.agg_f[src];
+  const XF* AB = A.agg_b[src];
+  __syncthreads();   // tb may still be read by the half-step's scans
+  fill_tables(tb, cc, m);
+  __syncthreads();
+  XF af = XF{0.f, kZeroExp}, ab = XF{0.f, kZeroExp};
+  for (int k = 0; k < m; ++k) af = c_add(c_mul(af, d1), j0 + k < A.nch ? ldcg_xf(AF + j0 + k) : XF{0.f, kZeroExp});
+  for (int k = m - 1; k >= 0; --k) ab = c_add(c_mul(ab, d1), j0 + k < A.nch ? ldcg_xf(AB + j0 + k) : XF{0.f, kZeroExp});
+  XF cf, cb;
+  {
+    TeamLaunch L{};
+    TeamCtx tc{0, 0, 1, 0, nullptr};
+    unsigned epoch = 0, xc = 0;
+    int dec;
+    exchange<OpPlain<XF>, XF, kSW>(L, tc, epoch, xc, af, ab, 0.f, m, tb, X, cf, cb, 0.f, 0.f, dec, nullptr, nullptr);
+  }
+  XF r = cf;
+  for (int k = 0; k < m && j0 + k < A.nch; ++k) {
+    A.car_f[src][j0 + k] = r;
+    r = c_add(c_mul(r, d1), ldcg_xf(AF + j0 + k));
+  }
+  XF t = cb;
+  for (int k = m - 1; k >= 0; --k) {
+    if (j0 + k < A.nch) A.car_b[src][j0 + k] = t;
+    if (j0 + k < A.nch) t = c_add(c_mul(t, d1), ldcg_xf(AB + j0 + k));
+  }
+}
+
+// the carries of u after the init kernel (one CTA per pair)
+__global__ void __launch_bounds__(kST, 1) stream_carry_kernel(StreamArgs A, int src) {
+  __shared__ DecayTables<XF> tb;
+  __shared__ XchgSmem<XF> X;
+  if (threadIdx.x == 0) X.ok = 1;
+  chunk_carry_scan(A, src, tb, X);
+}
+
 // masses in run order, u = v = 1/N (or the warm start), the chunk aggregates
 // of u, the chunk decay table and the loop state
-__global__ void __launch_bounds__(kThreads, 1) stream_init_kernel(StreamArgs A) {
+__global__ void __launch_bounds__(kST, 1) stream_init_kernel(StreamArgs A) {
   __shared__ DecayTables<XF> tb;
-  __shared__ XF sw[2 * kWarps];
+  __shared__ XF sw[2 * kSW];
   fill_tables(tb, A.c, kSE);
   __syncthreads();
   const int tid = threadIdx.x, ch = blockIdx.x;
@@ -252,8 +314,8 @@ __global__ void __launch_bounds__(kThreads, 1) stream_init_kernel(StreamArgs A) 
   }
   st_run(A.U, ch, tid, u);
   st_run(A.V[0], ch, tid, v);
-  A.FU[(size_t)ch * kThreads + tid] = fu;
-  A.FV[0][(size_t)ch * kThreads + tid] = fv;
+  A.FU[(size_t)ch * kST + tid] = fu;
+  A.FV[0][(size_t)ch * kST + tid] = fv;
   float af, ab;
   run_aggregates(u, A.lamf, af, ab);
   XF tf, tbk;
@@ -283,14 +345,14 @@ __device__ __forceinline__ void copy_tables(DecayTables<XF>& tb, const DecayTabl
 // memory by bulk copies issued at the start, so that they arrive while the
 // carries are formed; dynamic shared memory: kChunk floats per staged array.
 constexpr unsigned kStageBytes = kChunk * sizeof(float);
-__global__ void __launch_bounds__(kThreads, 2) stream_step_kernel(const __grid_constant__ StreamBatch B, int vhalf) {
+__global__ void __launch_bounds__(kST, 2) stream_step_kernel(const __grid_constant__ StreamBatch B, int vhalf) {
   extern __shared__ __align__(16) float4 s_stage[];   // [masses | accepted v], kChunk / 4 each
   __shared__ __align__(8) unsigned long long s_mbar;
   __shared__ DecayTables<XF> tb;
   __shared__ XchgSmem<XF> X;
-  __shared__ XF sw[2 * kWarps];
-  __shared__ float sred[2 * kWarps];
-  __shared__ double sdred[kWarps];
+  __shared__ XF sw[2 * kSW];
+  __shared__ float sred[2 * kSW];
+  __shared__ double sdred[kSW];
   __shared__ int sstop, spar, slast;
   int pr = 0;
   while (pr + 1 < B.npairs && B.choff[pr + 1] <= (int)blockIdx.x) ++pr;
@@ -320,34 +382,14 @@ __global__ void __launch_bounds__(kThreads, 2) stream_step_kernel(const __grid_c
   int* FZ = vhalf ? A.FV[par ^ 1] : A.FU;
   const int zsrc = vhalf ? 1 + (par ^ 1) : 0;
   const float lam = A.lamf;
-  const size_t run = (size_t)ch * kThreads + tid;
+  const size_t run = (size_t)ch * kST + tid;
   const XF zero = XF{0.f, kZeroExp};
 
   float x[kSE];
   ld_run(Xin, ch, tid, x);
   const int e = Fin[run];
-  // chunk carries of the input: decay-weighted sums of the other chunks'
-  // aggregates, each thread over chunks tid, tid + 512, ..., then the CTA
-  XF CF, CB;
-  {
-    const XF* AF = A.agg_f[src];
-    const XF* AB = A.agg_b[src];
-    XF tf = zero, tk = zero;
-    for (int j = tid; j < A.nch; j += kThreads) {
-      if (j < ch) tf = c_add(tf, c_mul(AF[j], A.dec[ch - 1 - j]));
-      if (j > ch) tk = c_add(tk, c_mul(AB[j], A.dec[j - ch - 1]));
-    }
-    tf = warp_sum_c(tf);
-    tk = warp_sum_c(tk);
-    if (lane == 0) {
-      sw[warp] = tf;
-      sw[kWarps + warp] = tk;
-    }
-    __syncthreads();
-    CF = warp_sum_c(lane < kWarps ? sw[lane] : zero);
-    CB = warp_sum_c(lane < kWarps ? sw[kWarps + lane] : zero);
-    __syncthreads();   // sw is reused below
-  }
+  // chunk carries of the input (formed by the previous launch's last chunk)
+  const XF CF = A.car_f[src][ch], CB = A.car_b[src][ch];
   // thread carries: the in-CTA scan, plus the chunk carries placed at the thread
   XF cf, cb;
   {
@@ -357,10 +399,10 @@ __global__ void __launch_bounds__(kThreads, 2) stream_step_kernel(const __grid_c
     TeamCtx tc{0, 0, 1, 0, nullptr};
     unsigned epoch = 0, xc = 0;
     int dec;
-    exchange<OpPlain<XF>, XF>(L, tc, epoch, xc, c_from(af, e, XF{}), c_from(ab, e, XF{}), 0.f, kSE, tb, X, cf,
+    exchange<OpPlain<XF>, XF, kSW>(L, tc, epoch, xc, c_from(af, e, XF{}), c_from(ab, e, XF{}), 0.f, kSE, tb, X, cf,
                               cb, 0.f, 0.f, dec, nullptr, nullptr);
     cf = c_add(cf, c_mul(CF, c_mul(tb.dt[lane], tb.dw[warp])));
-    cb = c_add(cb, c_mul(CB, c_mul(tb.dt[31 - lane], tb.dw[kWarps - 1 - warp])));
+    cb = c_add(cb, c_mul(CB, c_mul(tb.dt[31 - lane], tb.dw[kSW - 1 - warp])));
   }
   // the recurrences with the carries folded in, in frame F (as the team kernel)
   const int F = max(e + 5, max(c_exp(cf), c_exp(cb)) + 2);
@@ -388,9 +430,9 @@ __global__ void __launch_bounds__(kThreads, 2) stream_step_kernel(const __grid_c
   float s = c_to(cb, F), ep = 0.f;
 #pragma unroll
   for (int q = kSE / 4 - 1; q >= 0; --q) {
-    const float4 m4 = mq[q * kThreads];
+    const float4 m4 = mq[q * kST];
     float4 v4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (vhalf) v4 = vq[q * kThreads];
+    if (vhalf) v4 = vq[q * kST];
     const float mm[4] = {m4.x, m4.y, m4.z, m4.w};
     const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
@@ -441,14 +483,14 @@ __global__ void __launch_bounds__(kThreads, 2) stream_step_kernel(const __grid_c
     // the while condition of Algorithm 1: the chunks' error pairs summed in
     // FP64 (each thread over chunks tid, tid + 512, ..., then a fixed tree)
     double ev = 0.0;
-    for (int j = tid; j < A.nch; j += kThreads) ev += (double)__ldcg(A.errp + 2 * j) + (double)__ldcg(A.errp + 2 * j + 1);
+    for (int j = tid; j < A.nch; j += kST) ev += (double)__ldcg(A.errp + 2 * j) + (double)__ldcg(A.errp + 2 * j + 1);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
     if (lane == 0) sdred[warp] = ev;
     __syncthreads();
     if (tid == 0) {
       double err = 0.0;
-      for (int w = 0; w < kWarps; ++w) err += sdred[w];
+      for (int w = 0; w < kSW; ++w) err += sdred[w];
       StreamState* st = A.st;
       st->err = err;
       const int status = st->fail ? FS1_ETIMEOUT
@@ -463,6 +505,7 @@ __global__ void __launch_bounds__(kThreads, 2) stream_step_kernel(const __grid_c
         st->par = par ^ 1;   // accept v_new
       }
       st->done = 0u;
+      sstop = status >= 0;
     }
   } else if (tid == 0) {
     StreamState* st = A.st;
@@ -473,15 +516,19 @@ __global__ void __launch_bounds__(kThreads, 2) stream_step_kernel(const __grid_c
       atomicSub(B.nactive, 1);
     }
     st->done = 0u;
+    sstop = st->fail;
   }
+  // the carries of this launch's output for the next launch
+  __syncthreads();
+  if (!sstop) chunk_carry_scan(A, zsrc, tb, X);
 }
 
 
 // Cost phase 1: distance-weighted chunk aggregates of the accepted v.
-__global__ void __launch_bounds__(kThreads, 1) stream_cost_agg_kernel(StreamArgs A) {
+__global__ void __launch_bounds__(kST, 1) stream_cost_agg_kernel(StreamArgs A) {
   using DT = PairC<XF>;
   __shared__ DecayTables<XF> tb;
-  __shared__ DT sw[2 * kWarps];
+  __shared__ DT sw[2 * kSW];
   copy_tables(tb, A.tabs);
   __syncthreads();
   const int tid = threadIdx.x, ch = blockIdx.x;
@@ -489,7 +536,7 @@ __global__ void __launch_bounds__(kThreads, 1) stream_cost_agg_kernel(StreamArgs
   const float lam = A.lamf;
   float x[kSE];
   ld_run(A.V[par], ch, tid, x);
-  const int e = A.FV[par][(size_t)ch * kThreads + tid];
+  const int e = A.FV[par][(size_t)ch * kST + tid];
   float p = 0.f, Aa = 0.f;
 #pragma unroll
   for (int k = 0; k < kSE; ++k) {
@@ -533,18 +580,18 @@ __global__ void stream_cost_carry_kernel(StreamArgs A) {
 
 // Cost phase 3: per chunk, sum_k u_k (A_k + B_k) h in FP64, A / B the
 // distance-weighted forward / backward sums of v (as the team kernel).
-__global__ void __launch_bounds__(kThreads, 1) stream_cost_kernel(StreamArgs A) {
+__global__ void __launch_bounds__(kST, 1) stream_cost_kernel(StreamArgs A) {
   using DT = PairC<XF>;
   using OpD = OpDist<XF>;
   __shared__ DecayTables<XF> tb;
   __shared__ XchgSmem<DT> XD;
-  __shared__ double sred[kWarps];
+  __shared__ double sred[kSW];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, ch = blockIdx.x;
   if (tid == 0) XD.ok = 1;
   copy_tables(tb, A.tabs);
   __syncthreads();
   const int par = A.st->par;
-  const size_t run = (size_t)ch * kThreads + tid;
+  const size_t run = (size_t)ch * kST + tid;
   const float lam = A.lamf;
   float v[kSE], u[kSE];
   ld_run(A.V[par], ch, tid, v);
@@ -569,12 +616,12 @@ __global__ void __launch_bounds__(kThreads, 1) stream_cost_kernel(StreamArgs A) 
     TeamCtx tc{0, 0, 1, 0, nullptr};
     unsigned epoch = 0, xc = 0;
     int dec;
-    exchange<OpD, XF>(L, tc, epoch, xc, DT{c_from(p, fv, XF{}), c_from(Aa, fv, XF{})},
+    exchange<OpD, XF, kSW>(L, tc, epoch, xc, DT{c_from(p, fv, XF{}), c_from(Aa, fv, XF{})},
                       DT{c_from(s, fv, XF{}), c_from(Bb, fv, XF{})}, 0.f, kSE, tb, XD, dcf, dcb, 0.f, 0.f, dec,
                       nullptr, nullptr);
     dcf = OpD::add(dcf, OpD::prop(A.dcar_f[ch], c_mul(tb.dt[lane], tb.dw[warp]), (float)(kSE * tid)));
-    dcb = OpD::add(dcb, OpD::prop(A.dcar_b[ch], c_mul(tb.dt[31 - lane], tb.dw[kWarps - 1 - warp]),
-                                  (float)(kSE * (kThreads - 1 - tid))));
+    dcb = OpD::add(dcb, OpD::prop(A.dcar_b[ch], c_mul(tb.dt[31 - lane], tb.dw[kSW - 1 - warp]),
+                                  (float)(kSE * (kST - 1 - tid))));
   }
   int F = max(max(c_exp(dcf.p), c_exp(dcf.a)), max(c_exp(dcb.p), c_exp(dcb.a))) + 2;
   F = max(F, fv + 12);
@@ -601,7 +648,7 @@ __global__ void __launch_bounds__(kThreads, 1) stream_cost_kernel(StreamArgs A) 
   __syncthreads();
   if (tid == 0) {
     double t = 0.0;
-    for (int w = 0; w < kWarps; ++w) t += sred[w];
+    for (int w = 0; w < kSW; ++w) t += sred[w];
     A.costp[ch] = t;
   }
 }
@@ -626,8 +673,8 @@ __global__ void stream_final_kernel(StreamArgs A) {
       // point i = chunk ch, thread t, point k of the thread's run
       const int64_t ch = i / kChunk;
       const int r = (int)(i - ch * kChunk), t = r / kSE, k = r % kSE;
-      const size_t at = (size_t)ch * kChunk + (size_t)(k >> 2) * (4 * kThreads) + (size_t)t * 4 + (k & 3);
-      const size_t run = (size_t)ch * kThreads + t;
+      const size_t at = (size_t)ch * kChunk + (size_t)(k >> 2) * (4 * kST) + (size_t)t * 4 + (k & 3);
+      const size_t run = (size_t)ch * kST + t;
       if (A.f_out) A.f_out[i] = log_of(A.U[at], A.FU[run]);
       if (A.g_out) A.g_out[i] = log_of(A.V[par][at], A.FV[par][run]);
     }
@@ -641,7 +688,7 @@ size_t align256s(size_t x) { return (x + 255) / 256 * 256; }
 StreamArgs stream_args(const PairDesc& P, int in_f32, PairResult* d_result, char*& p) {
   const int nch = (int)((P.n + kChunk - 1) / kChunk);
   const size_t pts = (size_t)nch * kChunk;
-  const size_t runs = (size_t)nch * kThreads;
+  const size_t runs = (size_t)nch * kST;
   StreamArgs A{};
   A.a = P.a;
   A.b = P.b;
@@ -664,6 +711,8 @@ StreamArgs stream_args(const PairDesc& P, int in_f32, PairResult* d_result, char
   for (int i = 0; i < 3; ++i) {
     A.agg_f[i] = (XF*)p; p += align256s(sizeof(XF) * nch);
     A.agg_b[i] = (XF*)p; p += align256s(sizeof(XF) * nch);
+    A.car_f[i] = (XF*)p; p += align256s(sizeof(XF) * nch);
+    A.car_b[i] = (XF*)p; p += align256s(sizeof(XF) * nch);
   }
   A.dec = (XF*)p; p += align256s(sizeof(XF) * nch);
   A.tabs = (DecayTables<XF>*)p; p += align256s(sizeof(DecayTables<XF>));
@@ -705,8 +754,9 @@ int solve_stream_group(const PairDesc* P, const int* in_f32, int count, PairResu
     return FS1_ECUDA;
   }
   for (int i = 0; i < count; ++i) {
-    stream_init_kernel<<<B.A[i].nch, kThreads, 0, st>>>(B.A[i]);
-    ++nl;
+    stream_init_kernel<<<B.A[i].nch, kST, 0, st>>>(B.A[i]);
+    stream_carry_kernel<<<1, kST, 0, st>>>(B.A[i], 0);
+    nl += 2;
   }
   // Iterations in blocks of 16 (two launches each), captured once as a CUDA
   // graph (direct launches if capture is unavailable).  One block stays in
@@ -715,8 +765,8 @@ int solve_stream_group(const PairDesc* P, const int* in_f32, int count, PairResu
   const int block = 16;
   auto issue_block = [&]() {
     for (int i = 0; i < block; ++i) {
-      stream_step_kernel<<<grid, kThreads, 2 * kStageBytes, st>>>(B, 1);
-      stream_step_kernel<<<grid, kThreads, kStageBytes, st>>>(B, 0);
+      stream_step_kernel<<<grid, kST, 2 * kStageBytes, st>>>(B, 1);
+      stream_step_kernel<<<grid, kST, kStageBytes, st>>>(B, 0);
     }
   };
   if ((e = cudaFuncSetAttribute(stream_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -771,9 +821,9 @@ int solve_stream_group(const PairDesc* P, const int* in_f32, int count, PairResu
   }
   for (int i = 0; i < count; ++i) {
     const StreamArgs& A = B.A[i];
-    stream_cost_agg_kernel<<<A.nch, kThreads, 0, st>>>(A);
+    stream_cost_agg_kernel<<<A.nch, kST, 0, st>>>(A);
     stream_cost_carry_kernel<<<1, 32, 0, st>>>(A);
-    stream_cost_kernel<<<A.nch, kThreads, 0, st>>>(A);
+    stream_cost_kernel<<<A.nch, kST, 0, st>>>(A);
     stream_final_kernel<<<(A.f_out || A.g_out) ? 1024 : 1, 256, 0, st>>>(A);
     nl += 4;
   }
@@ -792,8 +842,8 @@ size_t stream_workspace(const int64_t* n, int count) {
     if (i % kMaxStreamPairs == 0) b += 256;   // a group's active count
     const size_t nch = (size_t)((n[i] + kChunk - 1) / kChunk);
     const size_t pts = nch * kChunk;
-    b += 5 * align256s(sizeof(float) * pts) + 3 * align256s(sizeof(int) * nch * kThreads) +
-         7 * align256s(sizeof(XF) * nch) + align256s(sizeof(DecayTables<XF>)) + align256s(sizeof(float) * 2 * nch) +
+    b += 5 * align256s(sizeof(float) * pts) + 3 * align256s(sizeof(int) * nch * kST) +
+         13 * align256s(sizeof(XF) * nch) + align256s(sizeof(DecayTables<XF>)) + align256s(sizeof(float) * 2 * nch) +
          4 * align256s(sizeof(PairC<XF>) * nch) + align256s(sizeof(double) * nch) + 256;
   }
   return b;
