@@ -91,11 +91,12 @@ typedef struct fs1_config {
                            input check, team kernel, result copy) is one replayed CUDA
                            graph; 0: direct launches */
   double tau;           /* absorption threshold of FS1_VARIANT_PAPER (default 1e10) */
-  int grid2d;           /* 2D solver: 0 (default) keeps an image resident in the shared
-                           memory of one thread-block cluster of 8 to 16 CTAs when it
-                           fits (2D grids of at most 512 x 512 points whose axes have
-                           h / eps <= 8); 1 always uses the grid kernel that keeps the
-                           state in device memory (also 3D) */
+  int grid2d;           /* 2D and 3D solver: 0 (default) keeps an image resident in the
+                           shared memory of one thread-block cluster of 8 to 16 CTAs
+                           when it fits (2D grids of at most 512 x 512 points, 3D grids
+                           of at most 64 points on the fast and middle axes and 128 on
+                           the slow one, every axis with h / eps <= 8); 1 always uses
+                           the grid kernel that keeps the state in device memory */
   int units;            /* stabilised 1D batches: 1 (default) solves each small pair
                            (at most 32 points per thread on 8 warps, within the frame
                            cap of h / eps) on a unit of 8, 4 or one warp, 2, 4 or 16

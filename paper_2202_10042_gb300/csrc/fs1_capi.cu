@@ -742,26 +742,43 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
   // (the grid kernel may take three launches: room for the others' tables)
   if (two_d)
     off = align_up(off + solve2d_workspace(desc.data(), count) + 2 * solve2d_workspace(nullptr, 0) + 2048, 256);
-  // 2D images the cluster-resident kernel holds (first in `perm`), then the
-  // rest for the grid kernel by launch class (solve2d_class), one launch each
+  // 2D images the cluster-resident kernel holds (first in `perm`), 3D grids
+  // its 3D variant holds (next), then the rest for the grid kernel by launch
+  // class (solve2d_class), one launch each.  The 3D grids' transport cost is
+  // one more grid-kernel launch (no iterations, warm-started from the final
+  // iterate) with its own workspace and results.
   std::vector<int> perm;
-  int ncl = 0;
+  int ncl = 0, ncl3 = 0;
   int gb[4] = {0, 0, 0, 0};   // [gb[q], gb[q + 1]) of perm: grid launch q
   const size_t o_c2d = off;
+  size_t o_c3d = off, o_cost = off, o_cres = off;
   if (two_d) {
     auto on_cluster = [&](int i) { return !h->cfg.grid2d && cluster2d_inst(desc[i]) >= 0; };
+    auto on_cluster3 = [&](int i) { return !h->cfg.grid2d && desc[i].n_mid > 1 && cluster3d_ok(desc[i]); };
     for (int i = 0; i < count; ++i)
       if (on_cluster(i)) perm.push_back(i);
     ncl = (int)perm.size();
-    gb[0] = ncl;
+    for (int i = 0; i < count; ++i)
+      if (on_cluster3(i)) perm.push_back(i);
+    ncl3 = (int)perm.size() - ncl;
+    gb[0] = ncl + ncl3;
     for (int q = 0; q < 3; ++q) {
       for (int i = 0; i < count; ++i)
-        if (!on_cluster(i) && solve2d_class(desc[i]) == q) perm.push_back(i);
+        if (!on_cluster(i) && !on_cluster3(i) && solve2d_class(desc[i]) == q) perm.push_back(i);
       gb[q + 1] = (int)perm.size();
     }
-    std::vector<PairDesc> dcl(ncl);
+    std::vector<PairDesc> dcl(ncl), d3(ncl3);
     for (int k = 0; k < ncl; ++k) dcl[k] = desc[perm[k]];
+    for (int k = 0; k < ncl3; ++k) d3[k] = desc[perm[ncl + k]];
     if (ncl) off = align_up(off + cluster2d_workspace(dcl.data(), ncl), 256);
+    o_c3d = off;
+    if (ncl3) {
+      off = align_up(off + cluster3d_workspace(d3.data(), ncl3), 256);
+      o_cost = off;
+      off = align_up(off + solve2d_workspace(d3.data(), ncl3) + 2048, 256);
+      o_cres = off;
+      off = align_up(off + sizeof(PairResult) * ncl3, 256);
+    }
   }
   // paper form: kPaperArrays FP64 arrays of N per pair
   std::vector<int64_t> poff(paper ? count : 0);
@@ -777,9 +794,9 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
   }
   if ((st = ensure_ws(h, off)) != FS1_OK) return st;
   if ((st = ensure_pinned(h, &h->hdr, &h->hdr_bytes, hdr)) != FS1_OK) return st;
-  if ((st = ensure_pinned(h, &h->hres, &h->hres_bytes, sizeof(PairResult) * count + sizeof(int) * count)) !=
-      FS1_OK)
-    return st;
+  // pinned results: [count] results, [count] input-check flags, [ncl3] 3D costs
+  const size_t o_hcost = sizeof(PairResult) * count + align_up(sizeof(int) * count, 16);
+  if ((st = ensure_pinned(h, &h->hres, &h->hres_bytes, o_hcost + sizeof(PairResult) * ncl3)) != FS1_OK) return st;
   char* ws = (char*)h->ws;
 
   // header image (nothing of ours is in flight: every call ends synchronised)
@@ -839,6 +856,16 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
                                        h->stream, &nl);
       if (ls != FS1_OK) return (fs1_status)ls;
     }
+    if (ncl3) {
+      std::vector<PairDesc> cost3(ncl3);
+      int ls = launch_cluster_3d(dp.data() + ncl, ncl3, in_f32, d_res + ncl, ws + o_c3d, o_cost - o_c3d, h->stream,
+                                 &nl, cost3.data());
+      if (ls != FS1_OK) return (fs1_status)ls;
+      ls = launch_solve_2d(cost3.data(), ncl3, in_f32, (PairResult*)(ws + o_cres), ws + o_cost, o_cres - o_cost,
+                           h->cfg.spin_cap, h->stream);
+      if (ls != FS1_OK) return (fs1_status)ls;
+      ++nl;
+    }
     // the grid kernel: one launch per class (each launch's workspace follows
     // the previous one's)
     size_t o_g = o_2d;
@@ -856,6 +883,9 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
     cudaEventRecord(h->ev1, h->stream);
     if ((e = cudaMemcpyAsync(hres, ws + o_res, sizeof(PairResult) * count, cudaMemcpyDeviceToHost, h->stream)) !=
         cudaSuccess)
+      return cuda_fail(e, "result copy");
+    if (ncl3 && (e = cudaMemcpyAsync((char*)hres + o_hcost, ws + o_cres, sizeof(PairResult) * ncl3,
+                                     cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
       return cuda_fail(e, "result copy");
   } else {
     TeamLaunch L{};
@@ -980,10 +1010,20 @@ fs1_status run_group(fs1_handle* h, int kind, int mode, const std::vector<const 
   if (two_d) {
     res.assign(count, PairResult{});
     for (int k = 0; k < count; ++k) res[perm[k]] = hres[k];
-    // an image whose scalings left the cluster kernel's exponent range is
+    // the 3D cluster kernel's grids take their cost from the cost launch
+    const PairResult* hcost = (const PairResult*)((const char*)hres + o_hcost);
+    for (int k = ncl; k < ncl + ncl3; ++k) {
+      PairResult& r = res[perm[k]];
+      if (r.status != FS1_OK && r.status != FS1_ENOTCONV) continue;
+      if (hcost[k - ncl].status == FS1_ETIMEOUT)
+        r.status = FS1_ETIMEOUT;
+      else
+        r.w = hcost[k - ncl].w;
+    }
+    // an image whose scalings left a cluster kernel's exponent range is
     // solved again by the grid kernel
     std::vector<int> again;
-    for (int k = 0; k < ncl; ++k)
+    for (int k = 0; k < ncl + ncl3; ++k)
       if (hres[k].status == FS1_EUNSUPPORTED) again.push_back(perm[k]);
     if (!again.empty()) {
       std::vector<PairDesc> dg(again.size());
