@@ -105,6 +105,8 @@ struct Tabs {
   XF subs[kSub + 1];     // lam_s^k
   XF ks[5];              // lam_f^{PF 2^lv}: the warp scan of the row pass
   XF lamR;               // lam_s^R: one CTA's rows
+  int exact;             // 1: blocks take a common frame by their largest value (gather_frame);
+                         // 0: by their largest frame (frame_max), exact enough while c <= 3
 };
 
 // ---------------------------------------------------------------------------
@@ -183,6 +185,43 @@ __device__ __forceinline__ short to16(int f, bool& bad) {
   return (short)max(-32767, min(32767, f));
 }
 
+// N values x[k] (>= 0) given relative to frames f[k], brought into one frame
+// set by the largest value (each value's own exponent counts, not only its
+// frame: a frame shared by many points can lie far above a given point, and a
+// common frame taken from the largest frame alone would push such points into
+// FP32's subnormal range, dropping real contributions where the scalings span
+// hundreds of binary orders within a few points).  The largest lands in
+// [0.5, 1); values more than 2^126 below it become zero (with c = h / eps <= 8
+// they are negligible in every output of the next sweep).  Returns the frame
+// (kZeroExp: all zero).
+template <int N>
+__device__ __forceinline__ int gather_frame(float (&x)[N], const int (&f)[N]) {
+  int e[N];
+  int emax = kZeroExp;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const int d = fexp(x[k]);   // kZeroExp for zero or subnormal
+    e[k] = d == kZeroExp ? kZeroExp : f[k] + d;
+    emax = max(emax, e[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < N; ++k) x[k] = e[k] == kZeroExp ? 0.f : x[k] * pow2f(f[k] - emax);
+  return emax;
+}
+
+// the same by the largest frame alone (cheaper; with c <= 3 on both axes a
+// point lies at most about 70 binary orders below the largest frame of the
+// blocks it is combined with, far from FP32's subnormal range)
+template <int N>
+__device__ __forceinline__ int frame_max(float (&x)[N], const int (&f)[N]) {
+  int emax = kZeroExp;
+#pragma unroll
+  for (int k = 0; k < N; ++k) emax = max(emax, f[k]);
+#pragma unroll
+  for (int k = 0; k < N; ++k) x[k] *= pow2f(f[k] - emax);
+  return emax;
+}
+
 template <int N>
 __device__ __forceinline__ int to_block(const XF (&v)[N], float (&x)[N]) {
   int em = kZeroExp;
@@ -211,18 +250,17 @@ __device__ __forceinline__ void row_pass_f(const float* im, const short* icf, fl
   int fe[NSB];
 #pragma unroll
   for (int s = 0; s < NSB; ++s) {
+    float xs[SUB];
     int f[SUB];
-    int emax = kZeroExp;
 #pragma unroll
     for (int k = 0; k < SUB; ++k) {
       const int slot = (s * SUB + k) * 32 + lane;
-      x[s * SUB + k] = im[slot];
+      xs[k] = im[slot];
       f[k] = fr16(icf[slot]);
-      emax = max(emax, f[k]);
     }
-    fe[s] = emax;
+    fe[s] = T.exact ? gather_frame(xs, f) : frame_max(xs, f);
 #pragma unroll
-    for (int k = 0; k < SUB; ++k) x[s * SUB + k] *= pow2f(f[k] - emax);
+    for (int k = 0; k < SUB; ++k) x[s * SUB + k] = xs[k];
   }
   const float lam = T.lamf;
   // sub-block aggregates: forward to the block's last point, backward from
@@ -364,20 +402,20 @@ __device__ __forceinline__ void colf_a(ColF<RS>& c, const float* ym, FR fr, int 
   XF A = XF{0.f, kZeroExp}, B = XF{0.f, kZeroExp};
 #pragma unroll
   for (int s = 0; s < NSB; ++s) {
+    float yv[kSub];
     int f[kSub];
-    int emax = kZeroExp;
 #pragma unroll
     for (int k = 0; k < kSub; ++k) {
       const int r = s * kSub + k;
-      c.y[r] = r < nr ? ym[r * SW + t] : 0.f;
+      yv[k] = r < nr ? ym[r * SW + t] : 0.f;
       f[k] = r < nr ? fr(r) : kZeroExp;
-      emax = max(emax, f[k]);
     }
+    const int emax = T.exact ? gather_frame(yv, f) : frame_max(yv, f);
     c.fe[s] = emax;
     float rr = 0.f, qq = 0.f;
 #pragma unroll
     for (int k = 0; k < kSub; ++k) {
-      c.y[s * kSub + k] *= pow2f(f[k] - emax);
+      c.y[s * kSub + k] = yv[k];
       rr = fmaf(!MASK || s * kSub + k < nr ? lam : 1.f, rr, c.y[s * kSub + k]);
     }
 #pragma unroll
@@ -628,6 +666,7 @@ __global__ void __launch_bounds__(kThr, 1) fs1_cluster2d_kernel(Launch L) {
       }
       for (int lv = 0; lv < 5; ++lv) T.ks[lv] = c_decay((double)(PF << lv), I.cf, XF{});
       T.lamR = c_decay((double)R, I.cs, XF{});
+      T.exact = (nf > 1 && I.cf > 3.0) || (ns > 1 && I.cs > 3.0);
     }
     // ---- a, b into slot order; u = v = 1 / N (Algorithm 2) or the warm start
     const XF init = xf_norm((float)(1.0 / ((double)nf * (double)ns)), 0);

@@ -61,6 +61,7 @@ using c2d::dsm_addr;
 using c2d::dsm_ld_f2;
 using c2d::dsm_ld_s32;
 using c2d::fr16;
+using c2d::gather_frame;
 using c2d::from_log;
 using c2d::kF16Zero;
 using c2d::kFrameC;
@@ -142,28 +143,6 @@ __device__ __forceinline__ XF shfl_up8(XF a, int o) {
 }
 __device__ __forceinline__ XF shfl_down8(XF a, int o) {
   return XF{__shfl_down_sync(0xffffffffu, a.m, o, 8), __shfl_down_sync(0xffffffffu, a.e, o, 8)};
-}
-
-// N values x[k] (>= 0) given relative to frames f[k], brought into one frame
-// set by the largest value (each value's own exponent counts, not only its
-// frame: a frame shared by many points can lie far above a given point, and a
-// common frame taken from the largest frame alone would push such points into
-// FP32's subnormal range).  The largest lands in [0.5, 1); values more than
-// 2^126 below it become zero (with c = h / eps <= 8 they are negligible in
-// every output of the next sweep).  Returns the frame (kZeroExp: all zero).
-template <int N>
-__device__ __forceinline__ int gather_frame(float (&x)[N], const int (&f)[N]) {
-  int e[N];
-  int emax = kZeroExp;
-#pragma unroll
-  for (int k = 0; k < N; ++k) {
-    const int d = fexp(x[k]);   // kZeroExp for zero or subnormal
-    e[k] = d == kZeroExp ? kZeroExp : f[k] + d;
-    emax = max(emax, e[k]);
-  }
-#pragma unroll
-  for (int k = 0; k < N; ++k) x[k] = e[k] == kZeroExp ? 0.f : x[k] * pow2f(f[k] - emax);
-  return emax;
 }
 
 // ---------------------------------------------------------------------------

@@ -183,3 +183,24 @@ def test_cluster_full_workload4_images(env):
         assert infos[i].iters == r.iters == 40
         assert abs(w[i] - r.w) <= TOL32 * abs(r.w)
         assert abs(infos[i].marginal_err - r.err) <= 1e-3 * r.err
+
+
+def test_cluster_blob_images_at_c_near_8(env):
+    """Blob images over a 1e-7 floor (the 2D benchmark's generator) at
+    c = h / eps = 7.8, the largest c the cluster kernel takes: the scalings
+    span hundreds of binary orders within a few points.  300 iterations stay on
+    the cluster kernel (no fall-back to the grid kernel) and agree with the
+    grid kernel: W, the marginal error, and the potentials point by point."""
+    import numpy as np
+    from paper_2202_10042_gb300 import inputs
+    ps = [inputs.workload4(i, side=256, eps=(1.0 / 256) / 7.8) for i in range(2)]
+    probs = [(p.a, p.b, tuple(p.h), p.eps, 0.0, 300) for p in ps]
+    wc, ic, pc = _solve(env, probs, outs=True)
+    wg, ig, pg = _solve(env, probs, grid2d=True, outs=True)
+    for k in range(len(probs)):
+        assert ic[k].team_size > 0 and ig[k].team_size == 0
+        assert ic[k].iters == ig[k].iters == 300
+        assert abs(wc[k] - wg[k]) <= TOL32 * abs(wg[k])
+        assert abs(ic[k].marginal_err - ig[k].marginal_err) <= 1e-3 * ig[k].marginal_err
+        (fc, gc), (fg, gg) = [(f.cpu().numpy(), g.cpu().numpy()) for f, g in (pc[k], pg[k])]
+        assert np.max(np.abs(fc - fg)) <= 1e-3 and np.max(np.abs(gc - gg)) <= 1e-3
