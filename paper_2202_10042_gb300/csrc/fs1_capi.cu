@@ -21,6 +21,7 @@
 
 #include "fs1.h"
 #include "fs1_internal.h"
+#include "fs1_cluster3d.h"
 
 using namespace fs1;
 

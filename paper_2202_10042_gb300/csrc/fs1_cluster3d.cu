@@ -50,6 +50,7 @@
 #include <vector>
 
 #include "fs1_cluster2d.cuh"
+#include "fs1_cluster3d.h"
 
 namespace fs1 {
 namespace c3d {

@@ -29,8 +29,8 @@ struct PairResult {
   double err;     // marginal L1 error of the final iterate
   int64_t iters;  // completed iterations
   int status;     // fs1_status value
-  int pad;        // CTAs that solved the problem: a 1D team, or the cluster of a 2D image or 3D grid
-                  // resident on chip (0: the grid kernel, the streamed path, the paper form)
+  int pad;        // CTAs that solved the problem: a 1D team, or the cluster of a 2D image resident on
+                  // chip (0: the 2D grid kernel, the streamed path, the paper form)
 };
 
 // Exchange slot of one CTA of a team (one per CTA and buffer parity): up to
@@ -120,19 +120,6 @@ int cluster2d_inst(const PairDesc& d);
 size_t cluster2d_workspace(const PairDesc* d, int count);
 int launch_cluster_2d(const PairDesc* d, int count, int in_f32, PairResult* results, const int* d_valid, void* ws,
                       size_t ws_bytes, void* stream, long long* launches);
-
-// Cluster-resident 3D solver (fs1_cluster3d.cu): a grid of at most 64 points
-// on the fast and middle axes (and c = h / eps <= 8 on every axis) in the
-// shared memory of one cluster of 8 to 16 CTAs.  launch_cluster_3d solves
-// d[0 .. count), all with cluster3d_ok; results[i].w is left NaN and cost[i]
-// (host) receives the descriptor of a grid-kernel launch of no iterations,
-// warm-started from the final iterate, whose result is that cost.  An image
-// whose scalings leave the kernel's exponent range ends with
-// FS1_EUNSUPPORTED (the caller solves it again with the grid kernel).
-int cluster3d_ok(const PairDesc& d);
-size_t cluster3d_workspace(const PairDesc* d, int count);
-int launch_cluster_3d(const PairDesc* d, int count, int in_f32, PairResult* results, void* ws, size_t ws_bytes,
-                      void* stream, long long* launches, PairDesc* cost);
 
 // Stabilised 1D solver with the state in device memory (fs1_stream.cu), for
 // pairs beyond the team kernel's on-chip capacity: workspace bytes for pairs
