@@ -47,6 +47,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
 #include <vector>
 
 #include "fs1_cluster2d.cuh"
@@ -661,7 +662,7 @@ cudaError_t prepare(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, int v, i
 
 // clusters of cs CTAs of kernel variant v with smem bytes of dynamic shared
 // memory that fit on the current device at once (0: none); queried once per
-// device and shape
+// device and shape (handles used from several host threads share the table)
 int clusters_of(int v, int cs, size_t smem) {
   struct Key {
     int dev, v, cs;
@@ -669,8 +670,10 @@ int clusters_of(int v, int cs, size_t smem) {
     int n;
   };
   static std::vector<Key> known;
+  static std::mutex mu;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  std::lock_guard<std::mutex> lock(mu);
   for (const Key& k : known)
     if (k.dev == dev && k.v == v && k.cs == cs && k.smem == smem) return k.n;
   cudaLaunchConfig_t cfg;
